@@ -1,0 +1,299 @@
+/*
+ * rapral.h -- C ABI of the GB300 (sm_103a) implementation of the RAPRAL hot
+ * path (arXiv 2604.11856): two-temperature populations, line-by-line spectral
+ * coefficients, the segment-wise RTE march and the wall radiative heat flux.
+ *
+ * Conventions (every entry point):
+ *  - Returns an int status: RAPRAL_OK or one of the codes below.  No call
+ *    aborts, traps or prints.  rapral_last_error() holds a message for the
+ *    last failure of a context.
+ *  - Array arguments are CALLER-OWNED DEVICE pointers (for example the
+ *    data_ptr() of CUDA tensors) unless a comment says "host".  The library
+ *    owns only the opaque context and its workspace (per-line constants, the
+ *    line-binning tables and a status word); it never frees caller memory.
+ *  - Work is enqueued asynchronously on the context's stream; outputs are
+ *    valid once that stream has synchronised (rapral_sync()).  Arguments that
+ *    can be checked on the host (sizes, ranges, null pointers) are checked
+ *    before anything is enqueued and fail with RAPRAL_EINVAL at once.
+ *    Checks of array CONTENTS (non-positive or non-finite temperatures,
+ *    negative densities, out-of-range cell or species indices, negative path
+ *    lengths) run on the device; a failure sets the context's sticky status,
+ *    turns every later kernel of the context into a no-op, and is reported
+ *    by rapral_sync() (and by the next call) as RAPRAL_EINVAL.
+ *  - Units: T in K; number densities in cm^-3; energies in cm^-1;
+ *    wavelengths in nm; path lengths in cm; kappa in cm^-1; j in
+ *    W/cm^3/sr/um; intensity in W/cm^2/sr/um; q_lambda in W/cm^2/um;
+ *    q in W/cm^2.  Physical constants are the paper's cgs values (Sec. 2.1).
+ *  - Row-major layouts; "[a][b]" means b varies fastest.
+ */
+#ifndef RAPRAL_H
+#define RAPRAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+enum {
+    RAPRAL_OK = 0,
+    RAPRAL_EINVAL = 1,     /* bad argument or out-of-range value            */
+    RAPRAL_ENOMEM = 2,     /* workspace or budget exceeded                  */
+    RAPRAL_ECUDA = 3,      /* a CUDA runtime call failed                    */
+    RAPRAL_ETIMEOUT = 4,   /* a bounded device wait gave up                 */
+    RAPRAL_ECANCELED = 5   /* work was cancelled                            */
+};
+
+/* Arithmetic of the spectral and transport steps.
+ * RAPRAL_FP64: every step in FP64 ("plain").
+ * RAPRAL_FP32: FP64 for the partition sums, the log-space part of the line
+ *   set-up and the wavelength-integrated flux; FP32 with compensated (Kahan)
+ *   sums for the line profiles and the march ("chosen"). */
+enum { RAPRAL_FP64 = 0, RAPRAL_FP32 = 1 };
+
+/* Kinds of radiating species. */
+enum { RAPRAL_ATOM = 0, RAPRAL_DIATOMIC = 1 };
+
+typedef struct rapral_ctx rapral_ctx;
+
+#if defined(__GNUC__)
+#define RAPRAL_API __attribute__((visibility("default")))
+#else
+#define RAPRAL_API
+#endif
+
+/* ------------------------------------------------------------ data model -- */
+
+/* Radiating-species database (Sec. 2.1; the paper's first layer).
+ * Atoms: a level list (E, g) per species.  Diatomics: electronic states
+ * (term energy E_i, degeneracy g_i, symmetry factor sigma, line-alternation
+ * factor for even / odd J) with a vibrational ladder E_V[V] and rotational
+ * ladders E_J[V][J] (J = 0 .. nj-1) per state. */
+typedef struct {
+    int32_t n_species;            /* S (<= RAPRAL_MAX_SPECIES)                */
+    const int32_t* kind;          /* [S] RAPRAL_ATOM / RAPRAL_DIATOMIC         */
+    const int32_t* density_col;   /* [S] column of the species in cells.n      */
+    const double* mass;           /* [S] molar mass, g/mol                     */
+    const int64_t* atom_off;      /* [S+1] level ranges into atom_E / atom_g   */
+    const double* atom_E;         /* [n_atom_levels] cm^-1                     */
+    const double* atom_g;         /* [n_atom_levels]                           */
+    const int64_t* st_off;        /* [S+1] state ranges                        */
+    const double* st_E;           /* [n_states] electronic term energy, cm^-1  */
+    const double* st_g;           /* [n_states]                                */
+    const double* st_sigma;       /* [n_states]                                */
+    const double* st_Lalt;        /* [n_states][2] even J, odd J               */
+    const int32_t* st_nv;         /* [n_states] vibrational levels             */
+    const int32_t* st_nj;         /* [n_states] rotational levels per V        */
+    const int64_t* st_vib_off;    /* [n_states] offset into vib_E              */
+    const int64_t* st_rot_off;    /* [n_states] offset into rot_E              */
+    const double* vib_E;          /* [n_vib] E_V, cm^-1                        */
+    const double* rot_E;          /* [n_rot] E_J(V), cm^-1, [V][J] per state   */
+    int64_t n_atom_levels, n_states, n_vib, n_rot;  /* sizes (bounds checks)  */
+} rapral_species;
+
+/* Line list (Sec. 2.2.1 atoms, Sec. 2.2.2 diatomics), sorted by lam0
+ * (ascending; an unsorted list still gives correct results, more slowly).
+ * Level energies are split into electronic, vibrational (both at T_ve) and
+ * rotational (at T_tr) parts; g is the statistical weight multiplying the
+ * level's Boltzmann factor (g_i S_multi (2J+1) L_alter / sigma for a
+ * rovibronic level). */
+typedef struct {
+    int64_t n_lines;
+    const double* lam0;     /* [L] centre, nm                                 */
+    const double* A;        /* [L] Einstein coefficient, s^-1                  */
+    const double* lamS0;    /* [L] Stark HWHM at N_e = 1e16, T = 1e4 K, nm     */
+    const int32_t* species; /* [L] radiating-species index                     */
+    const double *Eu_el, *Eu_v, *Eu_j, *gu;   /* [L] upper level               */
+    const double *El_el, *El_v, *El_j, *gl;   /* [L] lower level               */
+} rapral_lines;
+
+/* Cell states (cell-centred flowfield values, Sec. 2.3 first layer). */
+typedef struct {
+    int64_t n_cells;        /* C                                              */
+    const double* Ttr;      /* [C] translational-rotational temperature, K    */
+    const double* Tve;      /* [C] vibrational-electron-electronic temp., K   */
+    const double* n;        /* [C][n_cols] number densities, cm^-3            */
+    int32_t n_cols;
+    int32_t ne_col;         /* column of the electron density                 */
+    const double* lnpref;   /* [C][S] ln N_s - ln Z_s from rapral_populations  */
+} rapral_cells;
+
+/* Uniform wavelength grid: lam_k = lam_min + k h, h = (lam_max - lam_min) /
+ * (n - 1), k = 0 .. n-1 (end points included). */
+typedef struct {
+    double lam_min, lam_max;
+    int64_t n;
+} rapral_grid;
+
+/* Ray set.  A BUNDLE is a path through cells (segments listed from the far
+ * boundary to the surface point) shared by one or more DIRECTIONS; a
+ * direction scales every segment length (1/mu for a tangent-slab direction,
+ * 1 for a single line of sight) and carries its weight in the angular sum
+ * q_lambda[p] = sum_dir weight * I_dir (Sec. 2.2.3).  Bundles of surface
+ * point p are [point_off[p], point_off[p+1]).  The caller owns every array;
+ * rapral_slab_rays / rapral_axisym_rays fill them. */
+typedef struct {
+    int64_t n_bundles;          /* B                                          */
+    int64_t n_points;           /* P                                          */
+    int64_t n_segments;         /* seg_off[B]                                 */
+    int64_t n_dirs;             /* dir_off[B]                                 */
+    int32_t max_dirs;           /* max directions of a bundle (<= RAPRAL_MAX_DIRS) */
+    int32_t max_bundles_per_point;
+    const int64_t* point_off;   /* [P+1]                                      */
+    const int64_t* seg_off;     /* [B+1]                                      */
+    const int32_t* seg_cell;    /* [n_segments] cell index, far -> near       */
+    const double* seg_ds;       /* [n_segments] length, cm                    */
+    const int64_t* dir_off;     /* [B+1]                                      */
+    const double* dir_scale;    /* [n_dirs]                                   */
+    const double* dir_weight;   /* [n_dirs]                                   */
+    const int32_t* bundle_wall; /* [B] 1: the far end is a wall at T_wall     */
+    double T_wall;              /* K                                          */
+} rapral_rays;
+
+#define RAPRAL_MAX_SPECIES 32
+#define RAPRAL_MAX_DIRS 65
+
+/* ---------------------------------------------------------------- context -- */
+
+/* Creates a context on `device` that enqueues on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The caller owns the
+ * stream.  Errors: RAPRAL_EINVAL (bad device), RAPRAL_ECUDA. */
+RAPRAL_API int rapral_create(rapral_ctx** out, int device, void* cuda_stream);
+
+/* Frees the context and its workspace (after synchronising its stream). */
+RAPRAL_API void rapral_destroy(rapral_ctx* ctx);
+
+/* Message of the last failure of `ctx` (static storage of the context). */
+RAPRAL_API const char* rapral_last_error(const rapral_ctx* ctx);
+
+/* Re-targets the context to another stream (for example a worker's). */
+RAPRAL_API int rapral_set_stream(rapral_ctx* ctx, void* cuda_stream);
+
+/* Synchronises the context's stream and reports the sticky device status:
+ * RAPRAL_EINVAL if a device-side check failed since the last
+ * rapral_clear_status(), RAPRAL_ECUDA on a CUDA error, else RAPRAL_OK. */
+RAPRAL_API int rapral_sync(rapral_ctx* ctx);
+RAPRAL_API int rapral_clear_status(rapral_ctx* ctx);
+
+/* Physical constants: 0 = the paper's 4-digit cgs values (default),
+ * 1 = CODATA 2018. */
+RAPRAL_API int rapral_set_constants(rapral_ctx* ctx, int codata);
+
+/* Spectral tile width (grid points per line-sum tile; multiple of 128,
+ * 128 .. 8192) and cells per line-sum block (1, 2 or 4).  0 keeps the
+ * current value.  Used by the autotuner. */
+RAPRAL_API int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block);
+
+/* Device bytes the context's workspace needs for a solve of this size
+ * (lines L, spectral range nk); for admission control.  Host-only. */
+RAPRAL_API int rapral_workspace_bytes(int64_t n_lines, int64_t n_cells, int64_t nk, size_t* bytes);
+
+/* ---------------------------------------------------------- hot-path steps -- */
+
+/* Partition functions and log population prefactors (Sec. 2.1, Boltzmann
+ * distribution of atoms; molecular Boltzmann distribution with the
+ * rovibrational partition function Q_vr):
+ *   atoms:      Z_s = sum_levels g exp(-hcE / k T_ve)
+ *   diatomics:  Z_s = sum_i g_i exp(-hcE_i / k T_ve) Q_vr,i,
+ *               Q_vr,i = sum_V exp(-hcE_V / k T_ve) (1/sigma)
+ *                        sum_J (2J+1) L_alter exp(-hcE_J / k T_tr)
+ *   lnpref[c][s] = ln n_{c, density_col[s]} - ln Z_s   (-inf when n = 0).
+ * In: sp, cells (Ttr, Tve, n).  Out: lnpref [C][S] FP64 (device).
+ * Errors: EINVAL (sizes, S > RAPRAL_MAX_SPECIES; device: T <= 0 or not
+ * finite, n < 0). */
+RAPRAL_API int rapral_populations(rapral_ctx* ctx, const rapral_species* sp,
+                       const rapral_cells* cells, double* lnpref);
+
+/* Line-by-line emission and absorption coefficients (Sec. 2.2.1 / 2.2.2):
+ *   j(lam_k)     = sum_lines j0 phi(|lam_k - lam0|),
+ *   kappa(lam_k) = sum_lines kappa0 phi(|lam_k - lam0|),
+ *   j0 = 1e-7 (hc/4pi) N_u A / (lam0 1e-7), kappa0 = j0 / B(lam0) with B in
+ *   population form (Sec. 2.2), N from lnpref and the level data, phi the
+ *   Whiting Voigt shape with HWHMs Doppler(T_tr), Lorentz = natural +
+ *   Stark(T_ve, N_e) and the Voigt fit; a line adds to point k only when
+ *   |lam_k - lam0| <= 100 lamV.
+ * Computes grid points [k0, k0 + nk) for every cell.
+ * Out: kappa, emis [C][ld] (columns 0 .. nk-1 written), FP64 or FP32 per
+ * `precision`.  ld >= nk.  Lines are binned into spectral tiles on the
+ * device first (workspace).  Errors: EINVAL (k0 + nk > n, nk < 1, ld < nk,
+ * n < 2, lam_max <= lam_min; device: species index out of range, lam0 <= 0,
+ * g <= 0), ENOMEM (workspace), ECUDA. */
+RAPRAL_API int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp,
+                           const rapral_lines* lines, const rapral_cells* cells,
+                           const rapral_grid* grid, int64_t k0, int64_t nk,
+                           int precision, void* kappa, void* emis, int64_t ld);
+
+/* Ray march and angular reduction (Sec. 2.2.3).  For each bundle and grid
+ * point, nodes sit on cell faces (end nodes take the adjacent cell's value,
+ * interior nodes the mean of the two adjacent cells); over each segment
+ * kappa is the far node's value and j is linear:
+ *   I <- I e^{-dtau} + a j_far + b j_near,  dtau = kappa_far ds scale,
+ *   a = (f - e^{-dtau}) / kappa_far,  b = (1 - f) / kappa_far,
+ *   f = (1 - e^{-dtau}) / dtau,
+ * with three-term series of a and b when |dtau| < 4e-4 (FP64) / 5e-2 (FP32).
+ * The march starts from 0 (far field) or the Planck intensity at T_wall.
+ * Then q_lambda[p][k] = sum over the point's directions of weight * I.
+ * In: kappa, emis [C][ld] for grid points [k0, k0+nk) (as written by
+ * rapral_spectral_coeffs with the same precision).  Out: q_lambda [P][nk]
+ * (FP64 or FP32); I_out [n_dirs][nk] or NULL.  Errors: EINVAL (sizes,
+ * max_dirs > RAPRAL_MAX_DIRS; device: seg_cell not in [0, n_cells),
+ * seg_ds < 0). */
+RAPRAL_API int rapral_trace_rays(rapral_ctx* ctx, const rapral_rays* rays, int64_t n_cells,
+                      const void* kappa, const void* emis, int64_t ld,
+                      const rapral_grid* grid, int64_t k0, int64_t nk, int precision,
+                      void* q_lambda, void* I_out);
+
+/* Spectral integral of the wall flux (Sec. 2.2.3): q[p] += sum_k w_k
+ * q_lambda[p][k] h 1e-3 (lam in um), w_k the trapezoid weights of the whole
+ * grid (1/2 at k = 0 and k = n-1), so the chunks of one grid add up.  FP64
+ * accumulation.  The caller zeroes q before the first chunk.
+ * In: q_lambda [P][nk] FP64/FP32.  In/out: q [P] FP64. */
+RAPRAL_API int rapral_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision,
+                     const rapral_grid* grid, int64_t k0, int64_t nk, int64_t n_points,
+                     double* q);
+
+/* ------------------------------------------------------------ ray builders -- */
+
+/* Tangent slab (plane-parallel layers): one bundle through `n_layers` cells
+ * cell_order[0] (far boundary) .. cell_order[m-1] (wall), thickness dx[i];
+ * directions mu[m] with weight 2 pi wmu[m] mu[m] and path scale 1/mu[m];
+ * with `normal_ray` a first direction mu = 1 of weight 0 (intensity output
+ * only).  Inputs are device arrays; outputs are caller-owned device arrays
+ * sized: point_off[2], seg_off[2], seg_cell[m], seg_ds[m], dir_off[2],
+ * dir_scale/dir_weight[n_mu + normal_ray], bundle_wall[1].  Fills `rays`
+ * (host struct) with those pointers and sizes. */
+RAPRAL_API int rapral_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx,
+                     int32_t n_layers, const double* mu, const double* wmu, int32_t n_mu,
+                     int32_t normal_ray, int32_t wall_start, double T_wall,
+                     int64_t* point_off, int64_t* seg_off, int32_t* seg_cell, double* seg_ds,
+                     int64_t* dir_off, double* dir_scale, double* dir_weight,
+                     int32_t* bundle_wall, rapral_rays* rays);
+
+/* Axisymmetric rays (Sec. 2.2.3 lines of sight, on a rectilinear (x, r) grid
+ * around a body of radius r_body = rf[0]): from each surface point
+ * (surf_x[p], r_body) a ray per (mu_m, azimuth a) with mu = cos of the angle
+ * to the outward normal and azimuths at (a + 1/2) 2 pi / n_phi; each ray is a
+ * bundle of one direction (scale 1, weight wmu[m] mu_m 2 pi / n_phi).
+ * Cells are numbered ix * nr + jr.  Segments run from the far boundary to
+ * the point; zero-length pieces are dropped.
+ * Two calls: with seg_cell == NULL the call counts segments, writes seg_off
+ * [B+1] (B = P n_mu n_phi) and returns the total in *n_segments (host; the
+ * call synchronises the stream); a second call with seg_cell / seg_ds
+ * (device, n_segments entries) fills them and the remaining arrays
+ * (point_off[P+1], dir_off[B+1], dir_scale[B], dir_weight[B],
+ * bundle_wall[B]) and `rays`.  Geometry arrays (xf[nx+1], rf[nr+1],
+ * surf_x[P], mu, wmu) are device arrays. */
+RAPRAL_API int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf,
+                       int32_t nr, const double* surf_x, int32_t n_points,
+                       const double* mu, const double* wmu, int32_t n_mu, int32_t n_phi,
+                       int64_t* seg_off, int64_t* n_segments, int32_t* seg_cell, double* seg_ds,
+                       int64_t* point_off, int64_t* dir_off, double* dir_scale,
+                       double* dir_weight, int32_t* bundle_wall, rapral_rays* rays);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAPRAL_H */

@@ -1,0 +1,386 @@
+// C ABI of librapral: context, errors, host-side checks, workspace, and the
+// orchestration of the hot-path kernels on the context's stream.
+#include <cstdarg>
+#include <new>
+
+#include "rapral_internal.cuh"
+
+int set_error(rapral_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_status(rapral_ctx* ctx, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return RAPRAL_OK;
+    return set_error(ctx, RAPRAL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ws_reserve(rapral_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return RAPRAL_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "workspace sync");
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    size_t grow = bytes + bytes / 4 + (1u << 20);
+    e = cudaMalloc(&ctx->ws, grow);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, RAPRAL_ENOMEM, "workspace of %zu bytes: %s", grow, cudaGetErrorString(e));
+    }
+    ctx->ws_bytes = grow;
+    return RAPRAL_OK;
+}
+
+static const char* check_name(int c) {
+    switch (c) {
+        case CHK_CELL_T: return "cell temperature not positive and finite";
+        case CHK_CELL_N: return "cell number density negative or not finite";
+        case CHK_LINE_SPECIES: return "line species index out of range";
+        case CHK_LINE_LAM: return "line centre or Stark width invalid";
+        case CHK_LINE_G: return "line level weight not positive";
+        case CHK_LINE_A: return "Einstein coefficient negative or not finite";
+        case CHK_SEG_CELL: return "segment cell index out of range";
+        case CHK_SEG_DS: return "segment length negative or not finite";
+        case CHK_DIR: return "direction scale not positive";
+        case CHK_TIMEOUT: return "bounded device wait expired";
+        default: return "device check";
+    }
+}
+
+// Reads the sticky status (synchronises the stream).
+static int read_status(rapral_ctx* ctx) {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "status read-back");
+    const int code = ctx->h_pinned[ST_CODE];
+    if (code != RAPRAL_OK)
+        return set_error(ctx, code, "%s (index %d)", check_name(ctx->h_pinned[ST_CHECK]), ctx->h_pinned[ST_INDEX]);
+    return RAPRAL_OK;
+}
+
+extern "C" {
+
+int rapral_create(rapral_ctx** out, int device, void* cuda_stream) {
+    if (!out) return RAPRAL_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return RAPRAL_EINVAL;
+    }
+    rapral_ctx* ctx = new (std::nothrow) rapral_ctx();
+    if (!ctx) return RAPRAL_ENOMEM;
+    ctx->device = device;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 16 * sizeof(int64_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return RAPRAL_ECUDA;
+    }
+    *out = ctx;
+    return RAPRAL_OK;
+}
+
+void rapral_destroy(rapral_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+const char* rapral_last_error(const rapral_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+int rapral_set_stream(rapral_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return RAPRAL_EINVAL;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    return RAPRAL_OK;
+}
+
+int rapral_sync(rapral_ctx* ctx) {
+    if (!ctx) return RAPRAL_EINVAL;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(ctx, e, "pending CUDA error");
+    return read_status(ctx);
+}
+
+int rapral_clear_status(rapral_ctx* ctx) {
+    if (!ctx) return RAPRAL_EINVAL;
+    return cuda_status(ctx, cudaMemsetAsync(ctx->d_status, 0, 8 * sizeof(int), ctx->stream), "status clear");
+}
+
+int rapral_set_constants(rapral_ctx* ctx, int codata) {
+    if (!ctx || (codata != 0 && codata != 1)) return RAPRAL_EINVAL;
+    ctx->codata = codata;
+    return RAPRAL_OK;
+}
+
+int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (tile_width != 0) {
+        if (tile_width != 128 && tile_width != 256 && tile_width != 512 && tile_width != 1024 &&
+            tile_width != 2048 && tile_width != 4096 && tile_width != 8192)
+            return set_error(ctx, RAPRAL_EINVAL, "tile width %d not a power of two in 128..8192", tile_width);
+        ctx->tile_w = tile_width;
+    }
+    if (cells_per_block != 0) {
+        if (cells_per_block != 1 && cells_per_block != 2 && cells_per_block != 4)
+            return set_error(ctx, RAPRAL_EINVAL, "cells per block %d not 1, 2 or 4", cells_per_block);
+        ctx->cells_per_block = cells_per_block;
+    }
+    return RAPRAL_OK;
+}
+
+int rapral_workspace_bytes(int64_t n_lines, int64_t n_cells, int64_t nk, size_t* bytes) {
+    if (!bytes || n_lines < 0 || n_cells < 0 || nk < 0) return RAPRAL_EINVAL;
+    // per-line records + tile ranges, per-cell records, tile offsets, and a
+    // tile-list estimate of three tiles per line
+    const int64_t tiles = nk / 128 + 2;
+    size_t b = 0;
+    b = arena_need(b, (size_t)n_lines * sizeof(LinePrep));
+    b = arena_need(b, (size_t)n_lines * sizeof(int2));
+    b = arena_need(b, (size_t)n_cells * sizeof(CellPrep));
+    b = arena_need(b, (size_t)(tiles + 1) * sizeof(int));
+    b = arena_need(b, 64);
+    b = arena_need(b, (size_t)(3 * n_lines + tiles) * sizeof(int));
+    *bytes = b + b / 4 + (1u << 20);
+    return RAPRAL_OK;
+}
+
+int rapral_populations(rapral_ctx* ctx, const rapral_species* sp, const rapral_cells* cells, double* lnpref) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!sp || !cells || !lnpref) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (sp->n_species < 1 || sp->n_species > RAPRAL_MAX_SPECIES)
+        return set_error(ctx, RAPRAL_EINVAL, "species count %d not in 1..%d", sp->n_species, RAPRAL_MAX_SPECIES);
+    if (cells->n_cells < 0 || cells->n_cols < 1 || cells->ne_col < 0 || cells->ne_col >= cells->n_cols)
+        return set_error(ctx, RAPRAL_EINVAL, "cell array sizes");
+    if (cells->n_cells == 0) return RAPRAL_OK;
+    if (!cells->Ttr || !cells->Tve || !cells->n || !sp->kind || !sp->density_col)
+        return set_error(ctx, RAPRAL_EINVAL, "null cell or species array");
+    cudaSetDevice(ctx->device);
+    const Phys ph = make_phys(ctx->codata);
+    cudaError_t e = launch_validate_cells(ctx, cells);
+    if (e == cudaSuccess) e = launch_populations(ctx, sp, cells, lnpref, ph);
+    return cuda_status(ctx, e, "populations");
+}
+
+static int check_grid(rapral_ctx* ctx, const rapral_grid* g, int64_t k0, int64_t nk) {
+    if (!g) return set_error(ctx, RAPRAL_EINVAL, "null grid");
+    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || !std::isfinite(g->lam_max))
+        return set_error(ctx, RAPRAL_EINVAL, "grid needs n >= 2 and 0 < lam_min < lam_max");
+    if (k0 < 0 || nk < 1 || k0 + nk > g->n)
+        return set_error(ctx, RAPRAL_EINVAL, "range [%lld, %lld) outside the grid of %lld points", (long long)k0,
+                         (long long)(k0 + nk), (long long)g->n);
+    return RAPRAL_OK;
+}
+
+static double grid_h(const rapral_grid* g) { return (g->lam_max - g->lam_min) / (double)(g->n - 1); }
+
+int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
+                           const rapral_cells* cells, const rapral_grid* g, int64_t k0, int64_t nk, int precision,
+                           void* kappa, void* emis, int64_t ld) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!sp || !ln || !cells || !kappa || !emis) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    int st = check_grid(ctx, g, k0, nk);
+    if (st) return st;
+    if (precision != RAPRAL_FP64 && precision != RAPRAL_FP32)
+        return set_error(ctx, RAPRAL_EINVAL, "precision %d", precision);
+    if (ld < nk) return set_error(ctx, RAPRAL_EINVAL, "ld %lld < nk %lld", (long long)ld, (long long)nk);
+    if (ln->n_lines < 0 || ln->n_lines > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "line count");
+    if (cells->n_cells < 0 || cells->n_cols < 1 || cells->ne_col < 0 || cells->ne_col >= cells->n_cols)
+        return set_error(ctx, RAPRAL_EINVAL, "cell array sizes");
+    if (sp->n_species < 1 || sp->n_species > RAPRAL_MAX_SPECIES) return set_error(ctx, RAPRAL_EINVAL, "species count");
+    if (cells->n_cells > 0 && !cells->lnpref) return set_error(ctx, RAPRAL_EINVAL, "cells.lnpref is null");
+    cudaSetDevice(ctx->device);
+    const int64_t C = cells->n_cells, L = ln->n_lines;
+    const size_t esz = precision == RAPRAL_FP64 ? 8 : 4;
+    cudaError_t e = cudaSuccess;
+    if (C == 0) return RAPRAL_OK;
+    if (L == 0) {
+        e = cudaMemset2DAsync(kappa, ld * esz, 0, nk * esz, C, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemset2DAsync(emis, ld * esz, 0, nk * esz, C, ctx->stream);
+        return cuda_status(ctx, e, "zero coefficients");
+    }
+    const int W = ctx->tile_w;
+    if (precision == RAPRAL_FP64 && W > 512)
+        return set_error(ctx, RAPRAL_EINVAL, "FP64 line sum supports tile widths 128..512 (got %d)", W);
+    const int64_t T = (nk + W - 1) / W;
+    if (T > 65535) return set_error(ctx, RAPRAL_EINVAL, "range of %lld points needs more than 65535 tiles", (long long)nk);
+    const double h = grid_h(g);
+    const Phys ph = make_phys(ctx->codata);
+
+    // phase 1: per-line and per-cell records, tile ranges, tile counts
+    size_t need = 0;
+    need = arena_need(need, L * sizeof(LinePrep));
+    need = arena_need(need, C * sizeof(CellPrep));
+    need = arena_need(need, L * sizeof(int2));
+    need = arena_need(need, (T + 1) * sizeof(int));
+    need = arena_need(need, 4 * sizeof(unsigned long long));
+    need = arena_need(need, 4 * sizeof(int));
+    const size_t phase1 = need;
+    need = arena_need(need, (size_t)(3 * L + T) * sizeof(int));   // first guess of the tile lists
+    st = ws_reserve(ctx, need);
+    if (st) return st;
+    Arena ar{ctx->ws, ctx->ws_bytes};
+    LinePrep* lp = ar.take<LinePrep>(L);
+    CellPrep* cp = ar.take<CellPrep>(C);
+    BinPlan plan;
+    plan.k0 = k0; plan.nk = nk; plan.tile_w = W; plan.n_tiles = T;
+    plan.line_tiles = ar.take<int2>(L);
+    plan.tile_off = ar.take<int>(T + 1);
+    unsigned long long* dmax = ar.take<unsigned long long>(4);
+    plan.wmax = dmax + 2;
+    plan.sorted_flag = ar.take<int>(4);
+    const int one = 1;
+    e = cudaMemcpyAsync(plan.sorted_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan.wmax, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = launch_validate_cells(ctx, cells);
+    if (e == cudaSuccess) e = launch_validate_lines(ctx, ln, sp->n_species);
+    if (e == cudaSuccess) e = launch_line_prep(ctx, sp, ln, g->lam_min, h, ph, lp, plan.sorted_flag);
+    if (e == cudaSuccess) e = launch_cell_prep(ctx, cells, ph, cp, dmax);
+    if (e == cudaSuccess) e = launch_bin_bounds(ctx, ln, lp, cp, dmax, h, &plan);
+    if (e == cudaSuccess) e = launch_bin_count(ctx, ln, g, h, &plan);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->h_pinned, plan.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "line binning");
+    const int64_t total = ctx->h_pinned[0];
+    // phase 2: tile lists
+    need = arena_need(phase1, (size_t)(total + 1) * sizeof(int));
+    if (need > ctx->ws_bytes) {
+        // the arena moves: records must be rebuilt in the new one
+        st = ws_reserve(ctx, need + (size_t)(3 * L + T) * sizeof(int));
+        if (st) return st;
+        return rapral_spectral_coeffs(ctx, sp, ln, cells, g, k0, nk, precision, kappa, emis, ld);
+    }
+    ar.used = phase1;
+    plan.tile_lines = ar.take<int>(total + 1);
+    e = launch_bin_fill(ctx, ln, g, h, &plan);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "line binning");
+
+    LineSumArgs a;
+    a.lp = lp; a.cp = cp; a.lnpref = cells->lnpref; a.S = sp->n_species; a.C = C;
+    a.tile_off = plan.tile_off; a.tile_lines = plan.tile_lines;
+    a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk; a.ld = ld; a.tile_w = W;
+    a.kappa = kappa; a.emis = emis; a.status = ctx->d_status;
+    e = launch_line_sum(ctx, a, precision, T);
+    return cuda_status(ctx, e, "line sum");
+}
+
+int rapral_trace_rays(rapral_ctx* ctx, const rapral_rays* rays, int64_t n_cells, const void* kappa, const void* emis,
+                      int64_t ld, const rapral_grid* g, int64_t k0, int64_t nk, int precision, void* q_lambda,
+                      void* I_out) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!rays || !kappa || !emis || !q_lambda) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    int st = check_grid(ctx, g, k0, nk);
+    if (st) return st;
+    if (precision != RAPRAL_FP64 && precision != RAPRAL_FP32)
+        return set_error(ctx, RAPRAL_EINVAL, "precision %d", precision);
+    if (ld < nk) return set_error(ctx, RAPRAL_EINVAL, "ld < nk");
+    if (rays->n_points < 0 || rays->n_bundles < 0 || rays->n_segments < 0 || rays->n_dirs < 0)
+        return set_error(ctx, RAPRAL_EINVAL, "ray set sizes");
+    if (rays->max_dirs < 0 || rays->max_dirs > RAPRAL_MAX_DIRS)
+        return set_error(ctx, RAPRAL_EINVAL, "max_dirs %d not in 0..%d", rays->max_dirs, RAPRAL_MAX_DIRS);
+    if (rays->n_points > 65535) return set_error(ctx, RAPRAL_EINVAL, "more than 65535 surface points");
+    if (rays->n_points == 0) return RAPRAL_OK;
+    if (!rays->point_off || !rays->seg_off || !rays->dir_off || !rays->dir_scale || !rays->dir_weight ||
+        !rays->bundle_wall || (rays->n_segments > 0 && (!rays->seg_cell || !rays->seg_ds)))
+        return set_error(ctx, RAPRAL_EINVAL, "null ray array");
+    if (rays->bundle_wall && !(rays->T_wall >= 0.0)) return set_error(ctx, RAPRAL_EINVAL, "T_wall");
+    cudaSetDevice(ctx->device);
+    const Phys ph = make_phys(ctx->codata);
+    cudaError_t e = launch_validate_rays(ctx, rays, n_cells);
+    if (e == cudaSuccess) e = launch_march(ctx, rays, kappa, emis, ld, g, grid_h(g), k0, nk, precision, q_lambda, I_out, ph);
+    return cuda_status(ctx, e, "ray march");
+}
+
+int rapral_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const rapral_grid* g, int64_t k0,
+                     int64_t nk, int64_t n_points, double* q) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!q_lambda || !q) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    int st = check_grid(ctx, g, k0, nk);
+    if (st) return st;
+    if (precision != RAPRAL_FP64 && precision != RAPRAL_FP32)
+        return set_error(ctx, RAPRAL_EINVAL, "precision %d", precision);
+    if (n_points < 0 || n_points > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "n_points");
+    cudaSetDevice(ctx->device);
+    return cuda_status(ctx, launch_wall_flux(ctx, q_lambda, precision, g, grid_h(g), k0, nk, n_points, q), "wall flux");
+}
+
+int rapral_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx, int32_t n_layers, const double* mu,
+                     const double* wmu, int32_t n_mu, int32_t normal_ray, int32_t wall_start, double T_wall,
+                     int64_t* point_off, int64_t* seg_off, int32_t* seg_cell, double* seg_ds, int64_t* dir_off,
+                     double* dir_scale, double* dir_weight, int32_t* bundle_wall, rapral_rays* rays) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!rays || !point_off || !seg_off || !dir_off || !dir_scale || !dir_weight || !bundle_wall)
+        return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (n_layers < 0 || (n_layers > 0 && (!cell_order || !dx || !seg_cell || !seg_ds)))
+        return set_error(ctx, RAPRAL_EINVAL, "layers");
+    const int nd = n_mu + (normal_ray ? 1 : 0);
+    if (n_mu < 0 || nd < 1 || nd > RAPRAL_MAX_DIRS || (n_mu > 0 && (!mu || !wmu)))
+        return set_error(ctx, RAPRAL_EINVAL, "direction count %d not in 1..%d", nd, RAPRAL_MAX_DIRS);
+    if (wall_start && !(T_wall > 0.0)) return set_error(ctx, RAPRAL_EINVAL, "T_wall must be positive for a wall start");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_slab_rays(ctx, cell_order, dx, n_layers, mu, wmu, n_mu, normal_ray, wall_start, point_off,
+                                     seg_off, seg_cell, seg_ds, dir_off, dir_scale, dir_weight, bundle_wall);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "slab rays");
+    rays->n_bundles = 1; rays->n_points = 1; rays->n_segments = n_layers; rays->n_dirs = nd;
+    rays->max_dirs = nd; rays->max_bundles_per_point = 1;
+    rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
+    rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
+    rays->bundle_wall = bundle_wall; rays->T_wall = T_wall;
+    return RAPRAL_OK;
+}
+
+int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                       const double* surf_x, int32_t n_points, const double* mu, const double* wmu, int32_t n_mu,
+                       int32_t n_phi, int64_t* seg_off, int64_t* n_segments, int32_t* seg_cell, double* seg_ds,
+                       int64_t* point_off, int64_t* dir_off, double* dir_scale, double* dir_weight,
+                       int32_t* bundle_wall, rapral_rays* rays) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!xf || !rf || !surf_x || !mu || !wmu || !seg_off || !n_segments)
+        return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (nx < 1 || nr < 1 || n_points < 0 || n_mu < 1 || n_phi < 1)
+        return set_error(ctx, RAPRAL_EINVAL, "grid or direction counts");
+    if ((int64_t)nx * nr > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "too many cells");
+    cudaSetDevice(ctx->device);
+    const int64_t B = (int64_t)n_points * n_mu * n_phi;
+    cudaError_t e;
+    if (!seg_cell) {
+        e = launch_axisym_count(ctx, xf, nx, rf, nr, surf_x, n_points, mu, n_mu, n_phi, seg_off, nullptr);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_pinned, seg_off + B, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_status(ctx, e, "axisymmetric ray count");
+        *n_segments = reinterpret_cast<int64_t*>(ctx->h_pinned)[0];
+        return RAPRAL_OK;
+    }
+    if (!seg_ds || !point_off || !dir_off || !dir_scale || !dir_weight || !bundle_wall || !rays)
+        return set_error(ctx, RAPRAL_EINVAL, "null output array");
+    e = launch_axisym_fill(ctx, xf, nx, rf, nr, surf_x, n_points, mu, wmu, n_mu, n_phi, seg_off, seg_cell, seg_ds,
+                           point_off, dir_off, dir_scale, dir_weight, bundle_wall);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "axisymmetric rays");
+    rays->n_bundles = B; rays->n_points = n_points; rays->n_segments = *n_segments; rays->n_dirs = B;
+    rays->max_dirs = 1;
+    rays->max_bundles_per_point = n_mu * n_phi;
+    rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
+    rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
+    rays->bundle_wall = bundle_wall; rays->T_wall = 0.0;
+    return RAPRAL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,375 @@
+// Line preparation, spectral-tile binning and the line-by-line sum
+// (Sec. 2.2.1 atoms, Sec. 2.2.2 diatomics).
+//
+// Binning (deterministic, ordered by line index):
+//   k_bin_bounds   per line, the tiles its window can touch in any cell of the
+//                  request, from a conservative width: lamV <= lamL + lamG
+//                  with both widths at their largest over the cells
+//   k_bin_count    one block per tile: scan the lines whose centre lies within
+//                  the widest window of the tile, count those that reach it
+//   scan           exclusive prefix of the counts -> CSR offsets
+//   k_bin_fill     same scan, ordered compaction of the line indices
+//
+// Line sum: one block per (tile, cell).  Threads own consecutive grid points
+// of the tile.  Lines of the tile are processed in batches of blockDim: each
+// thread sets up one (line, cell) pair -- populations in log space, strengths,
+// Doppler / Stark / Voigt widths, profile normalisation and the window --
+// into shared memory; then every thread evaluates the Whiting profile of each
+// staged pair at its own points inside that pair's window and accumulates
+// kappa and j.  Results are written once, coalesced.
+#include "rapral_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double voigt_hwhm(double lamL, double lamG) {
+    const double d = (lamL - lamG) / (lamL + lamG);
+    return (1.0 - 0.18121 * (1.0 - d * d) - (0.023665 * exp(0.6 * d) + 0.00418 * exp(-1.9 * d)) * sin(M_PI * d)) *
+           (lamL + lamG);
+}
+
+__global__ void k_validate_lines(rapral_lines ln, int32_t S, int* status) {
+    int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= ln.n_lines) return;
+    const int s = ln.species[l];
+    if (s < 0 || s >= S) fail(status, CHK_LINE_SPECIES, l);
+    const double lam = ln.lam0[l];
+    if (!(lam > 0.0) || !isfinite(lam) || !(ln.lamS0[l] >= 0.0) || !isfinite(ln.lamS0[l]))
+        fail(status, CHK_LINE_LAM, l);
+    if (!(ln.gu[l] > 0.0) || !(ln.gl[l] > 0.0) || !isfinite(ln.gu[l]) || !isfinite(ln.gl[l]))
+        fail(status, CHK_LINE_G, l);
+    if (!(ln.A[l] >= 0.0) || !isfinite(ln.A[l])) fail(status, CHK_LINE_A, l);
+}
+
+__global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, double lam_min, double h, Phys ph,
+                            LinePrep* __restrict__ out, int* sorted_flag, const int* status) {
+    if (*status) return;
+    int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= ln.n_lines) return;
+    LinePrep p;
+    const double lam0 = ln.lam0[l];
+    const double lcm = lam0 * 1e-7;
+    const double A = ln.A[l];
+    const int s = ln.species[l];
+    p.lam0 = lam0;
+    p.lnAj = log(1e-7 * (ph.h * ph.c / (4.0 * M_PI)) * A / lcm);
+    p.lnAk = log(1e4 * A * (lcm * lcm) * (lcm * lcm) / (8.0 * M_PI * ph.c));
+    p.Eve_u = ln.Eu_el[l] + ln.Eu_v[l];
+    p.Er_u = ln.Eu_j[l];
+    p.lngu = log(ln.gu[l]);
+    p.dEve = (ln.Eu_el[l] + ln.Eu_v[l]) - (ln.El_el[l] + ln.El_v[l]);
+    p.dEr = ln.Eu_j[l] - ln.El_j[l];
+    p.cD = RAPRAL_DOPPLER_HALF * lam0 / sqrt(mass[s]);
+    p.lamS0 = ln.lamS0[l];
+    p.tpos = (lam0 - lam_min) / h;
+    p.species = s;
+    p.pad = 0;
+    out[l] = p;
+    if (l + 1 < ln.n_lines && ln.lam0[l + 1] < lam0) *sorted_flag = 0;
+}
+
+// Conservative window per line: lamV <= lamL + lamG (the Voigt fit's factor
+// never exceeds 1), both at their largest over the request's cells.
+__global__ void k_bin_bounds(const LinePrep* __restrict__ lp, int64_t L, const unsigned long long* __restrict__ dmax,
+                             double h, int64_t k0, int64_t nk, int tile_w, int2* __restrict__ line_tiles,
+                             unsigned long long* wmax, const int* status) {
+    if (*status) return;
+    int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    const double sqrtTmax = __longlong_as_double((long long)dmax[0]);
+    const double stcmax = __longlong_as_double((long long)dmax[1]);
+    const LinePrep p = lp[l];
+    const double lamG = p.cD * sqrtTmax;
+    const double lamL = RAPRAL_LAM_NATURAL + p.lamS0 * stcmax;
+    const double w = RAPRAL_WINDOW * (lamL + lamG) * (1.0 + 1e-9) / h + 2.0;   // grid points
+    atomicMax(wmax, (unsigned long long)__double_as_longlong(w));
+    const double lo = fmax(ceil(p.tpos - w), (double)k0);
+    const double hi = fmin(floor(p.tpos + w), (double)(k0 + nk - 1));
+    int2 t;
+    if (lo > hi) {
+        t.x = 1; t.y = 0;
+    } else {
+        t.x = (int)(((int64_t)lo - k0) / tile_w);
+        t.y = (int)(((int64_t)hi - k0) / tile_w);
+    }
+    line_tiles[l] = t;
+}
+
+// Lines whose centre can reach tile t: lam0 within the widest window of the
+// tile's wavelength span (binary search when lam0 is sorted, else all).
+__device__ void tile_candidates(const double* lam0, int64_t L, int sorted, double wmax, double lam_min, double h,
+                                int64_t kt0, int64_t kt1, int64_t* b0, int64_t* b1) {
+    if (!sorted) { *b0 = 0; *b1 = L; return; }
+    const double lo = lam_min + ((double)kt0 - wmax - 2.0) * h;
+    const double hi = lam_min + ((double)kt1 + wmax + 2.0) * h;
+    int64_t a = 0, b = L;
+    while (a < b) { int64_t m = (a + b) >> 1; if (lam0[m] < lo) a = m + 1; else b = m; }
+    *b0 = a;
+    b = L;
+    while (a < b) { int64_t m = (a + b) >> 1; if (lam0[m] <= hi) a = m + 1; else b = m; }
+    *b1 = a;
+}
+
+__global__ void __launch_bounds__(256) k_bin_count(const double* __restrict__ lam0, int64_t L,
+                                                   const int2* __restrict__ line_tiles, const int* sorted_flag,
+                                                   const unsigned long long* wmaxp, double lam_min, double h,
+                                                   int64_t k0, int64_t nk, int tile_w, int* __restrict__ counts,
+                                                   const int* status) {
+    if (*status) return;
+    const int t = blockIdx.x;
+    const int64_t kt0 = k0 + (int64_t)t * tile_w;
+    const int64_t kt1 = min(kt0 + tile_w, k0 + nk) - 1;
+    int64_t b0, b1;
+    tile_candidates(lam0, L, *sorted_flag, __longlong_as_double((long long)*wmaxp), lam_min, h, kt0, kt1, &b0, &b1);
+    int cnt = 0;
+    for (int64_t l = b0 + threadIdx.x; l < b1; l += blockDim.x) {
+        const int2 r = line_tiles[l];
+        cnt += (r.x <= t && t <= r.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    __shared__ int ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += ws[i];
+        counts[t] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bin_fill(const double* __restrict__ lam0, int64_t L,
+                                                  const int2* __restrict__ line_tiles, const int* sorted_flag,
+                                                  const unsigned long long* wmaxp, double lam_min, double h,
+                                                  int64_t k0, int64_t nk, int tile_w, const int* __restrict__ off,
+                                                  int* __restrict__ out, const int* status) {
+    if (*status) return;
+    const int t = blockIdx.x;
+    const int64_t kt0 = k0 + (int64_t)t * tile_w;
+    const int64_t kt1 = min(kt0 + tile_w, k0 + nk) - 1;
+    int64_t b0, b1;
+    tile_candidates(lam0, L, *sorted_flag, __longlong_as_double((long long)*wmaxp), lam_min, h, kt0, kt1, &b0, &b1);
+    __shared__ int wsum[8];
+    __shared__ int base_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int base = off[t];
+    for (int64_t r0 = b0; r0 < b1; r0 += blockDim.x) {
+        const int64_t l = r0 + threadIdx.x;
+        bool in = false;
+        if (l < b1) { const int2 r = line_tiles[l]; in = (r.x <= t && t <= r.y); }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int i = 0; i < nw; ++i) { int v = wsum[i]; wsum[i] = s; s += v; }
+            base_s = s;
+        }
+        __syncthreads();
+        if (in) out[base + wsum[warp] + __popc(m & ((1u << lane) - 1u))] = (int)l;
+        base += base_s;
+        __syncthreads();
+    }
+}
+
+// Single-block exclusive scan over n entries; data[n] receives the total.
+template <class T>
+__global__ void __launch_bounds__(1024) k_scan(T* data, int64_t n) {
+    __shared__ T part[32];
+    __shared__ T carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int64_t i = c0 + threadIdx.x;
+        T v = (i < n) ? data[i] : T(0);
+        T x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) part[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            T p = (lane < (int)(blockDim.x >> 5)) ? part[lane] : T(0);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                T y = __shfl_up_sync(0xffffffffu, p, o);
+                if (lane >= o) p += y;
+            }
+            part[lane] = p;
+        }
+        __syncthreads();
+        const T carry = carry_s;
+        const T incl = x + (warp > 0 ? part[warp - 1] : T(0));
+        if (i < n) data[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry_s = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) data[n] = carry_s;
+}
+
+// ------------------------------------------------------------ line sum FP64
+
+struct __align__(16) PairF64 {
+    double lam0, w100, inv2V, r, omr, c16, aj, ak;
+    int klo, khi, pad0, pad1;
+};
+
+template <int PPT>
+__global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
+    if (*a.status) return;
+    const int W = 128 * PPT;
+    const int t = blockIdx.y;
+    const int64_t c = blockIdx.x;
+    const int64_t kt0 = a.k0 + (int64_t)t * W;
+    const int64_t kend = min(kt0 + W, a.k0 + a.nk);   // exclusive
+    const int64_t kp = kt0 + (int64_t)threadIdx.x * PPT;
+    __shared__ PairF64 pr[128];
+    double acck[PPT], accj[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) { acck[i] = 0.0; accj[i] = 0.0; }
+    const CellPrep cp = a.cp[c];
+    const int beg = a.tile_off[t], end = a.tile_off[t + 1];
+    for (int b = beg; b < end; b += 128) {
+        const int nb = min(128, end - b);
+        if ((int)threadIdx.x < nb) {
+            const int l = a.tile_lines[b + threadIdx.x];
+            const LinePrep L = a.lp[l];
+            PairF64 P;
+            P.klo = 1; P.khi = 0;
+            const double lnNu = a.lnpref[c * a.S + L.species] + L.lngu - (L.Eve_u * cp.bve + L.Er_u * cp.btr);
+            const double Sj = exp(L.lnAj + lnNu);
+            if (Sj > 0.0) {
+                const double x = L.dEve * cp.bve + L.dEr * cp.btr;
+                const double Sk = exp(L.lnAk + lnNu) * expm1(x);
+                const double lamG = L.cD * cp.sqrtT;
+                const double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
+                const double lamV = voigt_hwhm(lamL, lamG);
+                const double r = lamL / lamV;
+                const double pre = 1e3 / (2.0 * lamV * (1.065 + 0.447 * r + 0.058 * r * r));
+                P.lam0 = L.lam0;
+                P.w100 = RAPRAL_WINDOW * lamV;
+                P.inv2V = 0.5 / lamV;
+                P.r = r;
+                P.omr = 1.0 - r;
+                P.c16 = 0.016 * r * (1.0 - r);
+                P.aj = Sj * pre;
+                P.ak = Sk * pre;
+                const double lo = ceil((L.lam0 - P.w100 - a.lam_min) / a.h) - 1.0;
+                const double hi = floor((L.lam0 + P.w100 - a.lam_min) / a.h) + 1.0;
+                P.klo = (int)fmax(lo, (double)kt0);
+                P.khi = (int)fmin(hi, (double)(kend - 1));
+            }
+            pr[threadIdx.x] = P;
+        }
+        __syncthreads();
+        for (int q = 0; q < nb; ++q) {
+            const int klo = pr[q].klo, khi = pr[q].khi;
+            if (khi < kp || klo > kp + PPT - 1) continue;
+            const PairF64 P = pr[q];
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                const int64_t k = kp + i;
+                if (k < klo || k > khi) continue;
+                const double lk = __dadd_rn(a.lam_min, __dmul_rn((double)k, a.h));
+                const double dl = fabs(lk - P.lam0);
+                if (!(dl <= P.w100)) continue;
+                const double u = dl * P.inv2V;
+                const double u2 = u * u;
+                const double ga = 2.772 * u2;
+                const double g = ga < 745.5 ? exp(-ga) : 0.0;
+                const double v = u2 * sqrt(sqrt(u));
+                const double ea = 0.4 * v;
+                const double e2 = ea < 745.5 ? exp(-ea) : 0.0;
+                const double qd = 1.0 + 4.0 * u2;
+                const double pd = 1.0 + 0.1 * v;
+                const double br = P.omr * g + (P.r * pd - P.c16 * qd) / (qd * pd) + P.c16 * e2;
+                accj[i] += P.aj * br;
+                acck[i] += P.ak * br;
+            }
+        }
+        __syncthreads();
+    }
+    double* K = reinterpret_cast<double*>(a.kappa) + c * a.ld - a.k0;
+    double* J = reinterpret_cast<double*>(a.emis) + c * a.ld - a.k0;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int64_t k = kp + i;
+        if (k < kend) { K[k] = acck[i]; J[k] = accj[i]; }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_validate_lines(rapral_ctx* ctx, const rapral_lines* ln, int32_t n_species) {
+    if (ln->n_lines == 0) return cudaSuccess;
+    k_validate_lines<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(*ln, n_species, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_prep(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
+                             double lam_min, double h, const Phys& ph, LinePrep* out, int* sorted_flag) {
+    if (ln->n_lines == 0) return cudaSuccess;
+    k_line_prep<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(*ln, sp->mass, lam_min, h, ph, out, sorted_flag,
+                                                                   ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_bounds(rapral_ctx* ctx, const rapral_lines* ln, const LinePrep* lp, const CellPrep* cp,
+                              const unsigned long long* d_max, double h, BinPlan* plan) {
+    (void)cp;
+    if (ln->n_lines == 0) return cudaSuccess;
+    k_bin_bounds<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(lp, ln->n_lines, d_max, h, plan->k0, plan->nk,
+                                                                    plan->tile_w, plan->line_tiles, plan->wmax,
+                                                                    ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_count(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
+                             BinPlan* plan) {
+    k_bin_count<<<(unsigned)plan->n_tiles, 256, 0, ctx->stream>>>(ln->lam0, ln->n_lines, plan->line_tiles,
+                                                                  plan->sorted_flag, plan->wmax, g->lam_min, h,
+                                                                  plan->k0, plan->nk, plan->tile_w, plan->tile_off,
+                                                                  ctx->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_scan_i32(ctx, plan->tile_off, plan->n_tiles);
+}
+
+cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
+                            BinPlan* plan) {
+    k_bin_fill<<<(unsigned)plan->n_tiles, 256, 0, ctx->stream>>>(ln->lam0, ln->n_lines, plan->line_tiles,
+                                                                 plan->sorted_flag, plan->wmax, g->lam_min, h,
+                                                                 plan->k0, plan->nk, plan->tile_w, plan->tile_off,
+                                                                 plan->tile_lines, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n) {
+    k_scan<int><<<1, 1024, 0, ctx->stream>>>(data, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n) {
+    k_scan<long long><<<1, 1024, 0, ctx->stream>>>(reinterpret_cast<long long*>(data), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles) {
+    if (n_tiles == 0 || a.C == 0) return cudaSuccess;
+    // cells along x (up to 2^31 - 1), tiles along y (<= 65535): consecutive
+    // blocks share a tile's line list in L2
+    dim3 grid((unsigned)a.C, (unsigned)n_tiles);
+    if (precision == RAPRAL_FP64) {
+        switch (a.tile_w) {
+            case 128: k_line_sum_f64<1><<<grid, 128, 0, ctx->stream>>>(a); break;
+            case 256: k_line_sum_f64<2><<<grid, 128, 0, ctx->stream>>>(a); break;
+            case 512: k_line_sum_f64<4><<<grid, 128, 0, ctx->stream>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}

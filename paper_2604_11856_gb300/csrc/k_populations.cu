@@ -1,0 +1,110 @@
+// Populations (Sec. 2.1) and per-cell preparation.
+//
+// k_populations: one warp per (cell, species).  Atoms: lanes stride over the
+// level list and sum g exp(-c2 E / T_ve).  Diatomics: lanes stride over the
+// rotational ladder of each (state, V) and add
+//   g_i exp(-c2 E_i / T_ve) exp(-c2 E_V / T_ve) / sigma (2J+1) L_alter exp(-c2 E_J / T_tr),
+// which is the product form of g_i exp(-c2E_i/T_ee) Q_vr,i.  One fixed-order
+// warp reduction per (cell, species) keeps the result deterministic.  FP64
+// throughout (partition sums are FP64 in both precisions).
+#include "rapral_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void k_validate_cells(const double* Ttr, const double* Tve, const double* n, int64_t C,
+                                 int32_t ncol, int* status) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const double a = Ttr[i], b = Tve[i];
+    if (!(a > 0.0) || !(b > 0.0) || !isfinite(a) || !isfinite(b)) fail(status, CHK_CELL_T, i);
+    for (int j = 0; j < ncol; ++j) {
+        const double v = n[i * ncol + j];
+        if (!(v >= 0.0) || !isfinite(v)) { fail(status, CHK_CELL_N, i); break; }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_populations(rapral_species sp, const double* __restrict__ Ttr,
+                                                     const double* __restrict__ Tve, const double* __restrict__ n,
+                                                     int32_t ncol, int64_t C, double c2, double* __restrict__ lnpref,
+                                                     const int* status) {
+    if (*status) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int S = sp.n_species;
+    if (w >= C * S) return;
+    const int64_t c = w / S;
+    const int s = (int)(w - c * S);
+    const double bve = c2 / Tve[c], btr = c2 / Ttr[c];
+    const double N = n[c * ncol + sp.density_col[s]];
+    double z = 0.0;
+    if (sp.kind[s] == RAPRAL_ATOM) {
+        const int64_t a = sp.atom_off[s], b = sp.atom_off[s + 1];
+        for (int64_t l = a + lane; l < b; l += 32) z += sp.atom_g[l] * exp(-bve * sp.atom_E[l]);
+    } else {
+        const int64_t a = sp.st_off[s], b = sp.st_off[s + 1];
+        for (int64_t i = a; i < b; ++i) {
+            const double pre = sp.st_g[i] * exp(-bve * sp.st_E[i]) / sp.st_sigma[i];
+            const int nv = sp.st_nv[i], nj = sp.st_nj[i];
+            const double La = sp.st_Lalt[2 * i], Lb = sp.st_Lalt[2 * i + 1];
+            const double* rot = sp.rot_E + sp.st_rot_off[i];
+            const double* vib = sp.vib_E + sp.st_vib_off[i];
+            for (int v = 0; v < nv; ++v) {
+                const double pv = pre * exp(-bve * vib[v]);
+                for (int J = lane; J < nj; J += 32)
+                    z += pv * ((2.0 * J + 1.0) * ((J & 1) ? Lb : La) * exp(-btr * rot[(int64_t)v * nj + J]));
+            }
+        }
+    }
+    z = warp_sum(z);
+    if (lane == 0) lnpref[c * S + s] = (N > 0.0) ? log(N) - log(z) : -INFINITY;
+}
+
+__global__ void k_cell_prep(const double* __restrict__ Ttr, const double* __restrict__ Tve,
+                            const double* __restrict__ n, int32_t ncol, int32_t ne_col, int64_t C, double c2,
+                            CellPrep* __restrict__ out, unsigned long long* dmax, const int* status) {
+    if (*status) return;
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    CellPrep p;
+    const double tt = Ttr[c], tv = Tve[c];
+    p.bve = c2 / tv;
+    p.btr = c2 / tt;
+    p.sqrtT = sqrt(tt);
+    p.stc = pow(tv / 10000.0, 0.33) * (n[c * ncol + ne_col] / 1e16);
+    out[c] = p;
+    // positive doubles order like their bit patterns
+    atomicMax(&dmax[0], (unsigned long long)__double_as_longlong(p.sqrtT));
+    atomicMax(&dmax[1], (unsigned long long)__double_as_longlong(p.stc));
+}
+
+}  // namespace
+
+cudaError_t launch_validate_cells(rapral_ctx* ctx, const rapral_cells* cells) {
+    k_validate_cells<<<div_up(cells->n_cells, 256), 256, 0, ctx->stream>>>(
+        cells->Ttr, cells->Tve, cells->n, cells->n_cells, cells->n_cols, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_populations(rapral_ctx* ctx, const rapral_species* sp, const rapral_cells* cells,
+                               double* lnpref, const Phys& ph) {
+    const int64_t warps = cells->n_cells * sp->n_species;
+    k_populations<<<div_up(warps * 32, 256), 256, 0, ctx->stream>>>(
+        *sp, cells->Ttr, cells->Tve, cells->n, cells->n_cols, cells->n_cells, ph.c2, lnpref, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_prep(rapral_ctx* ctx, const rapral_cells* cells, const Phys& ph, CellPrep* out,
+                             unsigned long long* d_max) {
+    cudaError_t e = cudaMemsetAsync(d_max, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return e;
+    k_cell_prep<<<div_up(cells->n_cells, 256), 256, 0, ctx->stream>>>(
+        cells->Ttr, cells->Tve, cells->n, cells->n_cols, cells->ne_col, cells->n_cells, ph.c2, out, d_max,
+        ctx->d_status);
+    return cudaGetLastError();
+}

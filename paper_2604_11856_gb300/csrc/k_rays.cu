@@ -1,0 +1,381 @@
+// Rays: builders (tangent slab, axisymmetric lines of sight), the segment
+// march with the angular reduction, and the spectral flux integral
+// (Sec. 2.2.3).
+//
+// k_march: one block per (surface point, wavelength tile).  Threads are
+// (wavelength lane, bundle slice): lanes run over consecutive grid points so
+// every kappa / j gather of a segment is a coalesced row read; slices take the
+// point's bundles round-robin.  Per bundle the kernel walks the segments from
+// the far boundary, keeps the node values of the current face in registers,
+// and advances the intensity of every direction of the bundle (up to MAXD in
+// registers) with the far/near coefficients of the linear-emission integral.
+// The weighted directions are summed per thread; slices are combined in
+// shared memory in a fixed order, so results do not depend on timing.
+#include "rapral_internal.cuh"
+
+namespace {
+
+template <class T> struct Real;
+template <> struct Real<double> {
+    static __device__ __forceinline__ double em1(double x) { return expm1(x); }
+    static constexpr double thin = RAPRAL_THIN_F64;
+};
+template <> struct Real<float> {
+    static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
+    static constexpr float thin = (float)RAPRAL_THIN_F32;
+};
+
+__global__ void k_validate_rays(const int32_t* seg_cell, const double* seg_ds, int64_t nseg, int64_t C,
+                                const double* dir_scale, int64_t ndir, int* status) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nseg) {
+        const int c = seg_cell[i];
+        if (c < 0 || c >= C) fail(status, CHK_SEG_CELL, i);
+        const double d = seg_ds[i];
+        if (!(d >= 0.0) || !isfinite(d)) fail(status, CHK_SEG_DS, i);
+    }
+    if (i < ndir) {
+        const double s = dir_scale[i];
+        if (!(s > 0.0) || !isfinite(s)) fail(status, CHK_DIR, i);
+    }
+}
+
+struct MarchArgs {
+    const int64_t* point_off;
+    const int64_t* seg_off;
+    const int32_t* seg_cell;
+    const double* seg_ds;
+    const int64_t* dir_off;
+    const double* dir_scale;
+    const double* dir_weight;
+    const int32_t* bundle_wall;
+    double T_wall;
+    const void* kappa;
+    const void* emis;
+    int64_t ld;
+    double lam_min, h;
+    int64_t k0, nk;
+    void* q_lambda;
+    void* I_out;
+    Phys ph;
+    const int* status;
+};
+
+// Planck intensity, temperature form (Sec. 2.2), W/cm^2/sr/um.
+__device__ __forceinline__ double planck(double lam_nm, double T, const Phys& ph) {
+    const double lcm = lam_nm * 1e-7;
+    const double l2 = lcm * lcm;
+    return 1e-7 * 2.0 * ph.h * ph.c * ph.c / (1e4 * l2 * l2 * lcm * expm1(ph.h * ph.c / (lcm * ph.kB * T)));
+}
+
+template <class T, int MAXD, int SL>
+__global__ void __launch_bounds__(256) k_march(MarchArgs a) {
+    if (*a.status) return;
+    constexpr int LW = 256 / SL;        // wavelength lanes per block
+    const int lane = threadIdx.x % LW;
+    const int slice = threadIdx.x / LW;
+    const int64_t p = blockIdx.y;
+    const int64_t kk = (int64_t)blockIdx.x * LW + lane;     // column within the range
+    const bool active = kk < a.nk;
+    const int64_t kcol = active ? kk : a.nk - 1;
+    const T* Kt = reinterpret_cast<const T*>(a.kappa) + kcol;
+    const T* Jt = reinterpret_cast<const T*>(a.emis) + kcol;
+    const T thin = Real<T>::thin;
+    T acc = T(0), comp = T(0);
+    for (int64_t b = a.point_off[p] + slice; b < a.point_off[p + 1]; b += SL) {
+        const int64_t d0 = a.dir_off[b];
+        const int nd = (int)(a.dir_off[b + 1] - d0);
+        T I[MAXD];
+        T I0 = T(0);
+        if (a.bundle_wall[b]) I0 = (T)planck(a.lam_min + (double)(a.k0 + kcol) * a.h, a.T_wall, a.ph);
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) I[d] = I0;
+        const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
+        if (s1 > s0) {
+            int c = a.seg_cell[s0];
+            T kc = Kt[(int64_t)c * a.ld], jc = Jt[(int64_t)c * a.ld];   // current cell
+            T kf = kc, jf = jc;                                          // far node of the segment
+            for (int64_t i = s0; i < s1; ++i) {
+                T kn, jn;                 // near node
+                T kx = T(0), jx = T(0);   // next cell
+                if (i + 1 < s1) {
+                    const int cn = a.seg_cell[i + 1];
+                    kx = Kt[(int64_t)cn * a.ld];
+                    jx = Jt[(int64_t)cn * a.ld];
+                    kn = T(0.5) * (kc + kx);
+                    jn = T(0.5) * (jc + jx);
+                } else {
+                    kn = kc; jn = jc;
+                }
+                const T ds = (T)a.seg_ds[i];
+                const T inv_k = T(1) / kf;
+#pragma unroll
+                for (int d = 0; d < MAXD; ++d) {
+                    if (d < nd) {
+                        const T s = ds * (T)a.dir_scale[d0 + d];
+                        const T dtau = kf * s;
+                        const T em1 = Real<T>::em1(-dtau);     // e^{-dtau} - 1
+                        const T e = T(1) + em1;
+                        T ca, cb;
+                        if (fabs(dtau) < thin) {
+                            ca = s * (T(0.5) - dtau * (T(1) / T(3)) + dtau * dtau * T(0.125));
+                            cb = s * (T(0.5) - dtau * (T(1) / T(6)) + dtau * dtau * (T(1) / T(24)));
+                        } else {
+                            const T f = -em1 / dtau;
+                            ca = (f - e) * inv_k;
+                            cb = (T(1) - f) * inv_k;
+                        }
+                        I[d] = I[d] * e + ca * jf + cb * jn;
+                    }
+                }
+                kf = kn; jf = jn;
+                kc = kx; jc = jx;
+            }
+        }
+        T part = T(0);
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+            if (d < nd) {
+                part += (T)a.dir_weight[d0 + d] * I[d];
+                if (a.I_out && active) reinterpret_cast<T*>(a.I_out)[(d0 + d) * a.nk + kk] = I[d];
+            }
+        }
+        // compensated sum over the point's bundles
+        const T y = part - comp;
+        const T tt = acc + y;
+        comp = (tt - acc) - y;
+        acc = tt;
+    }
+    if (SL == 1) {
+        if (active) reinterpret_cast<T*>(a.q_lambda)[p * a.nk + kk] = acc;
+        return;
+    }
+    __shared__ T red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (slice == 0 && active) {
+        T s = red[lane];
+        for (int q = 1; q < SL; ++q) s += red[q * LW + lane];
+        reinterpret_cast<T*>(a.q_lambda)[p * a.nk + kk] = s;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_wall_flux(const T* __restrict__ qlam, int64_t nk, int64_t k0, int64_t n,
+                                                   double h_um, double* __restrict__ q, const int* status) {
+    if (*status) return;
+    const int64_t p = blockIdx.x;
+    double s = 0.0, c = 0.0;
+    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) {
+        const int64_t kg = k0 + k;
+        const double w = (kg == 0 || kg == n - 1) ? 0.5 : 1.0;
+        const double x = w * (double)qlam[p * nk + k] * h_um;
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+        s = t;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s + c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) q[p] += red[0];
+}
+
+__global__ void k_slab_rays(const int32_t* cell_order, const double* dx, int32_t m, const double* mu,
+                            const double* wmu, int32_t n_mu, int32_t normal_ray, int32_t wall_start,
+                            int64_t* point_off, int64_t* seg_off, int32_t* seg_cell, double* seg_ds,
+                            int64_t* dir_off, double* dir_scale, double* dir_weight, int32_t* bundle_wall) {
+    const int nd = n_mu + (normal_ray ? 1 : 0);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) { seg_cell[i] = cell_order[i]; seg_ds[i] = dx[i]; }
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        if (normal_ray && d == 0) { dir_scale[0] = 1.0; dir_weight[0] = 0.0; continue; }
+        const int mm = d - (normal_ray ? 1 : 0);
+        dir_scale[d] = 1.0 / mu[mm];
+        dir_weight[d] = 2.0 * M_PI * wmu[mm] * mu[mm];
+    }
+    if (threadIdx.x == 0) {
+        point_off[0] = 0; point_off[1] = 1;
+        seg_off[0] = 0; seg_off[1] = m;
+        dir_off[0] = 0; dir_off[1] = nd;
+        bundle_wall[0] = wall_start;
+    }
+}
+
+// Ray from the surface point (x0, rb): position x = x0 + t dx, radius
+// sqrt((rb + t dn)^2 + (t dt)^2) (non-decreasing for dn > 0).  Walks the
+// rectilinear (x, r) cells from the point outward, stepping to whichever face
+// (x or r) comes first; emits (cell, length) for every piece of positive
+// length.  With out_cell != nullptr the pieces are written backwards from
+// out_end - 1 (so the list runs from the far boundary to the point).
+__device__ int64_t walk_ray(const double* xf, int nx, const double* rf, int nr, double x0, double rb, double dx,
+                            double dn, double dt, int32_t* out_cell, double* out_ds, int64_t out_end) {
+    if (!(x0 >= xf[0] && x0 <= xf[nx])) return 0;
+    int lo = 0, hi = nx;   // largest ix with xf[ix] <= x0
+    while (hi - lo > 1) { int m = (lo + hi) >> 1; if (xf[m] <= x0) lo = m; else hi = m; }
+    int ix = lo;
+    if (x0 == xf[ix] && dx < 0.0) ix -= 1;
+    if (ix >= nx) ix = nx - 1;
+    int jr = 0;
+    const double A = dn * dn + dt * dt, B = 2.0 * rb * dn;
+    double t = 0.0;
+    int64_t n = 0;
+    const int guard = 2 * (nx + nr) + 8;
+    for (int it = 0; it < guard && ix >= 0 && ix < nx && jr < nr; ++it) {
+        double tx = INFINITY;
+        if (dx > 0.0) tx = (xf[ix + 1] - x0) / dx;
+        else if (dx < 0.0) tx = (xf[ix] - x0) / dx;
+        double tr = INFINITY;
+        if (A > 0.0) {
+            const double rr = rf[jr + 1];
+            const double cq = rb * rb - rr * rr;                 // <= 0
+            tr = (-2.0 * cq) / (B + sqrt(B * B - 4.0 * A * cq));  // cancellation-free root
+        }
+        const double tn = fmin(tx, tr);
+        const double len = tn - t;
+        if (len > 0.0) {
+            if (out_cell) { out_cell[out_end - 1 - n] = ix * nr + jr; out_ds[out_end - 1 - n] = len; }
+            ++n;
+            t = tn;
+        }
+        if (tx <= tr) ix += (dx > 0.0) ? 1 : -1;
+        if (tr <= tx) jr += 1;
+    }
+    return n;
+}
+
+__device__ __forceinline__ void ray_dir(int64_t b, int32_t n_mu, int32_t n_phi, const double* mu, int64_t* p,
+                                        int* m, double* dx, double* dn, double* dt) {
+    const int64_t per = (int64_t)n_mu * n_phi;
+    *p = b / per;
+    const int64_t rem = b - *p * per;
+    *m = (int)(rem / n_phi);
+    const int a = (int)(rem - (int64_t)(*m) * n_phi);
+    const double mm = mu[*m];
+    const double st = sqrt(1.0 - mm * mm);
+    const double psi = (a + 0.5) * (2.0 * M_PI / n_phi);
+    *dx = st * cos(psi);
+    *dn = mm;
+    *dt = st * sin(psi);
+}
+
+__global__ void k_axisym_count(const double* xf, int32_t nx, const double* rf, int32_t nr, const double* surf_x,
+                               int32_t P, const double* mu, int32_t n_mu, int32_t n_phi, int64_t* counts) {
+    const int64_t B = (int64_t)P * n_mu * n_phi;
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    int64_t p; int m; double dx, dn, dt;
+    ray_dir(b, n_mu, n_phi, mu, &p, &m, &dx, &dn, &dt);
+    counts[b] = walk_ray(xf, nx, rf, nr, surf_x[p], rf[0], dx, dn, dt, nullptr, nullptr, 0);
+}
+
+__global__ void k_axisym_fill(const double* xf, int32_t nx, const double* rf, int32_t nr, const double* surf_x,
+                              int32_t P, const double* mu, const double* wmu, int32_t n_mu, int32_t n_phi,
+                              const int64_t* seg_off, int32_t* seg_cell, double* seg_ds, int64_t* point_off,
+                              int64_t* dir_off, double* dir_scale, double* dir_weight, int32_t* bundle_wall) {
+    const int64_t B = (int64_t)P * n_mu * n_phi;
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b > B) return;
+    dir_off[b] = b;
+    if (b <= P) point_off[b] = b * (int64_t)n_mu * n_phi;
+    if (b == B) return;
+    int64_t p; int m; double dx, dn, dt;
+    ray_dir(b, n_mu, n_phi, mu, &p, &m, &dx, &dn, &dt);
+    walk_ray(xf, nx, rf, nr, surf_x[p], rf[0], dx, dn, dt, seg_cell, seg_ds, seg_off[b + 1]);
+    dir_scale[b] = 1.0;
+    dir_weight[b] = wmu[m] * mu[m] * (2.0 * M_PI / n_phi);
+    bundle_wall[b] = 0;
+}
+
+template <class T, int MAXD>
+cudaError_t march_sl(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxb) {
+    if (maxb >= 8) {
+        dim3 g(div_up(nk, 32), (unsigned)P);
+        k_march<T, MAXD, 8><<<g, 256, 0, ctx->stream>>>(a);
+    } else {
+        dim3 g(div_up(nk, 256), (unsigned)P);
+        k_march<T, MAXD, 1><<<g, 256, 0, ctx->stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t march_t(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxd, int maxb) {
+    if (maxd <= 1) return march_sl<T, 1>(ctx, a, P, nk, maxb);
+    if (maxd <= 17) return march_sl<T, 17>(ctx, a, P, nk, maxb);
+    return march_sl<T, RAPRAL_MAX_DIRS>(ctx, a, P, nk, maxb);
+}
+
+}  // namespace
+
+cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells) {
+    const int64_t n = r->n_segments > r->n_dirs ? r->n_segments : r->n_dirs;
+    if (n == 0) return cudaSuccess;
+    k_validate_rays<<<div_up(n, 256), 256, 0, ctx->stream>>>(r->seg_cell, r->seg_ds, r->n_segments, n_cells,
+                                                            r->dir_scale, r->n_dirs, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis, int64_t ld,
+                         const rapral_grid* g, double h, int64_t k0, int64_t nk, int precision, void* q_lambda,
+                         void* I_out, const Phys& ph) {
+    MarchArgs a;
+    a.point_off = r->point_off; a.seg_off = r->seg_off; a.seg_cell = r->seg_cell; a.seg_ds = r->seg_ds;
+    a.dir_off = r->dir_off; a.dir_scale = r->dir_scale; a.dir_weight = r->dir_weight;
+    a.bundle_wall = r->bundle_wall; a.T_wall = r->T_wall;
+    a.kappa = kappa; a.emis = emis; a.ld = ld;
+    a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk;
+    a.q_lambda = q_lambda; a.I_out = I_out; a.ph = ph; a.status = ctx->d_status;
+    if (precision == RAPRAL_FP64)
+        return march_t<double>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
+    return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
+}
+
+cudaError_t launch_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const rapral_grid* g, double h,
+                             int64_t k0, int64_t nk, int64_t n_points, double* q) {
+    if (n_points == 0) return cudaSuccess;
+    const double h_um = h * 1e-3;
+    if (precision == RAPRAL_FP64)
+        k_wall_flux<double><<<(unsigned)n_points, 256, 0, ctx->stream>>>(
+            reinterpret_cast<const double*>(q_lambda), nk, k0, g->n, h_um, q, ctx->d_status);
+    else
+        k_wall_flux<float><<<(unsigned)n_points, 256, 0, ctx->stream>>>(
+            reinterpret_cast<const float*>(q_lambda), nk, k0, g->n, h_um, q, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx, int32_t m,
+                             const double* mu, const double* wmu, int32_t n_mu, int32_t normal_ray,
+                             int32_t wall_start, int64_t* point_off, int64_t* seg_off, int32_t* seg_cell,
+                             double* seg_ds, int64_t* dir_off, double* dir_scale, double* dir_weight,
+                             int32_t* bundle_wall) {
+    k_slab_rays<<<1, 256, 0, ctx->stream>>>(cell_order, dx, m, mu, wmu, n_mu, normal_ray, wall_start, point_off,
+                                           seg_off, seg_cell, seg_ds, dir_off, dir_scale, dir_weight, bundle_wall);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axisym_count(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                                const double* surf_x, int32_t P, const double* mu, int32_t n_mu, int32_t n_phi,
+                                int64_t* seg_off, int64_t* scan_tmp) {
+    (void)scan_tmp;
+    const int64_t B = (int64_t)P * n_mu * n_phi;
+    if (B == 0) return cudaSuccess;
+    k_axisym_count<<<div_up(B, 128), 128, 0, ctx->stream>>>(xf, nx, rf, nr, surf_x, P, mu, n_mu, n_phi, seg_off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_scan_i64(ctx, seg_off, B);
+}
+
+cudaError_t launch_axisym_fill(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                               const double* surf_x, int32_t P, const double* mu, const double* wmu, int32_t n_mu,
+                               int32_t n_phi, const int64_t* seg_off, int32_t* seg_cell, double* seg_ds,
+                               int64_t* point_off, int64_t* dir_off, double* dir_scale, double* dir_weight,
+                               int32_t* bundle_wall) {
+    const int64_t B = (int64_t)P * n_mu * n_phi;
+    k_axisym_fill<<<div_up(B + 1, 128), 128, 0, ctx->stream>>>(xf, nx, rf, nr, surf_x, P, mu, wmu, n_mu, n_phi,
+                                                               seg_off, seg_cell, seg_ds, point_off, dir_off,
+                                                               dir_scale, dir_weight, bundle_wall);
+    return cudaGetLastError();
+}

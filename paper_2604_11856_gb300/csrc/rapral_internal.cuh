@@ -1,0 +1,190 @@
+// Internal declarations of librapral: context, workspace arena, status word,
+// per-line and per-cell preparation records, and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#include "rapral.h"
+
+// ------------------------------------------------------------- constants ----
+
+// Physical constants in cgs (Sec. 2.1 prints k, c, h with four digits).
+struct Phys {
+    double kB, c, h;
+    double c2;        // h c / k, cm K
+};
+
+inline Phys make_phys(int codata) {
+    Phys p;
+    if (codata) { p.kB = 1.380649e-16; p.c = 2.99792458e10; p.h = 6.62607015e-27; }
+    else        { p.kB = 1.380e-16;    p.c = 2.998e10;      p.h = 6.626e-27; }
+    p.c2 = p.h * p.c / p.kB;
+    return p;
+}
+
+// Sec. 2.2.1 constants.
+#define RAPRAL_LAM_NATURAL 5.9e-6        // natural HWHM, nm
+#define RAPRAL_DOPPLER_HALF (7.16233e-7 / 2.0)
+#define RAPRAL_WINDOW 100.0              // lines reach |dlam| <= 100 lamV
+#define RAPRAL_THIN_F64 4e-4             // |dtau| below which the series is used
+#define RAPRAL_THIN_F32 5e-2
+
+// Status word layout (device int[8]).
+enum { ST_CODE = 0, ST_CHECK = 1, ST_INDEX = 2 };
+enum {
+    CHK_NONE = 0, CHK_CELL_T, CHK_CELL_N, CHK_LINE_SPECIES, CHK_LINE_LAM, CHK_LINE_G,
+    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT
+};
+
+// ------------------------------------------------------------- records ----
+
+// Per-line constants, independent of the cell (FP64).
+struct __align__(16) LinePrep {
+    double lam0;     // nm
+    double lnAj;     // ln(1e-7 (hc/4pi) A / (lam0 1e-7))       ln S_j = lnAj + ln N_u
+    double lnAk;     // ln(1e4 A (lam0 1e-7)^4 / (8 pi c))        S_k = e^{lnAk + ln N_u} expm1(x)
+    double Eve_u;    // E_el + E_V of the upper level (at T_ve)
+    double Er_u;     // E_J of the upper level (at T_tr)
+    double lngu;     // ln g_u
+    double dEve;     // (E_el + E_V)_u - (E_el + E_V)_l
+    double dEr;      // E_J,u - E_J,l
+    double cD;       // Doppler: lamG = cD sqrt(T_tr)
+    double lamS0;    // Stark HWHM at the reference state
+    double tpos;     // (lam0 - lam_min) / h, grid units
+    int32_t species;
+    int32_t pad;
+};
+
+// Per-cell constants (FP64).
+struct __align__(16) CellPrep {
+    double bve;      // c2 / T_ve
+    double btr;      // c2 / T_tr
+    double sqrtT;    // sqrt(T_tr)
+    double stc;      // (T_ve/1e4)^0.33 (N_e/1e16)
+};
+
+// ---------------------------------------------------------------- context ----
+
+struct rapral_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int codata = 0;
+    int tile_w = 512;          // grid points per line-sum tile
+    int cells_per_block = 1;
+    // workspace arena (grown on demand; all users are stream-ordered)
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    // status word (device) and a pinned host mirror
+    int* d_status = nullptr;
+    int* h_pinned = nullptr;    // [16] pinned scratch for small read-backs
+    char err[512] = {0};
+};
+
+// Records `msg` as the context's last error and returns `code`.
+int set_error(rapral_ctx* ctx, int code, const char* fmt, ...);
+// Wraps a CUDA call result.
+int cuda_status(rapral_ctx* ctx, cudaError_t e, const char* what);
+// Ensures the arena holds `bytes`; may synchronise the stream.
+int ws_reserve(rapral_ctx* ctx, size_t bytes);
+
+// Bump allocator over the arena (256-byte aligned slices).
+struct Arena {
+    char* base;
+    size_t cap, used = 0;
+    template <class T>
+    T* take(size_t n) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + n * sizeof(T);
+        return reinterpret_cast<T*>(base + off);
+    }
+};
+inline size_t arena_need(size_t cur, size_t bytes) { return ((cur + 255) & ~size_t(255)) + bytes; }
+
+// Grid launch helper.
+inline unsigned div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Device-side failure: first check wins.
+__device__ __forceinline__ void fail(int* status, int check, long long index) {
+    if (atomicCAS(&status[ST_CODE], 0, RAPRAL_EINVAL) == 0) {
+        status[ST_CHECK] = check;
+        status[ST_INDEX] = (int)(index > 2147483647LL ? 2147483647LL : index);
+    }
+}
+
+// ------------------------------------------------------ kernel launchers ----
+// (defined in the .cu files; all enqueue on ctx->stream)
+
+cudaError_t launch_validate_cells(rapral_ctx* ctx, const rapral_cells* cells);
+cudaError_t launch_populations(rapral_ctx* ctx, const rapral_species* sp, const rapral_cells* cells,
+                               double* lnpref, const Phys& ph);
+cudaError_t launch_validate_lines(rapral_ctx* ctx, const rapral_lines* ln, int32_t n_species);
+cudaError_t launch_line_prep(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
+                             double lam_min, double h, const Phys& ph, LinePrep* out, int* sorted_flag);
+cudaError_t launch_cell_prep(rapral_ctx* ctx, const rapral_cells* cells, const Phys& ph, CellPrep* out,
+                             unsigned long long* d_max /*[2]*/);
+
+// Binning of lines into spectral tiles of the range [k0, k0 + nk).
+struct BinPlan {
+    int64_t k0, nk;
+    int tile_w;
+    int64_t n_tiles;
+    int2* line_tiles;            // [L] first / last tile a line may touch (first > last: none)
+    int* tile_off;               // [T+1]
+    int* tile_lines;             // [tile_off[T]]
+    int* sorted_flag;            // [1] 1 while lam0 is non-decreasing
+    unsigned long long* wmax;    // [1] largest window half-width, grid points (double bits)
+};
+cudaError_t launch_bin_bounds(rapral_ctx* ctx, const rapral_lines* ln, const LinePrep* lp, const CellPrep* cp,
+                              const unsigned long long* d_max, double h, BinPlan* plan);
+cudaError_t launch_bin_count(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
+                             BinPlan* plan);
+cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
+                            BinPlan* plan);
+
+struct LineSumArgs {
+    const LinePrep* lp;
+    const CellPrep* cp;
+    const double* lnpref;     // [C][S]
+    int32_t S;
+    int64_t C;
+    const int* tile_off;
+    const int* tile_lines;
+    double lam_min, h;
+    int64_t k0, nk, ld;
+    int tile_w;
+    void* kappa;
+    void* emis;
+    const int* status;
+};
+cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles);
+
+// Rays
+cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells);
+cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis,
+                         int64_t ld, const rapral_grid* g, double h, int64_t k0, int64_t nk, int precision,
+                         void* q_lambda, void* I_out, const Phys& ph);
+cudaError_t launch_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const rapral_grid* g,
+                             double h, int64_t k0, int64_t nk, int64_t n_points, double* q);
+cudaError_t launch_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx, int32_t m,
+                             const double* mu, const double* wmu, int32_t n_mu, int32_t normal_ray,
+                             int32_t wall_start, int64_t* point_off, int64_t* seg_off, int32_t* seg_cell,
+                             double* seg_ds, int64_t* dir_off, double* dir_scale, double* dir_weight,
+                             int32_t* bundle_wall);
+cudaError_t launch_axisym_count(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                                const double* surf_x, int32_t P, const double* mu, int32_t n_mu,
+                                int32_t n_phi, int64_t* seg_off, int64_t* scan_tmp);
+cudaError_t launch_axisym_fill(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                               const double* surf_x, int32_t P, const double* mu, const double* wmu,
+                               int32_t n_mu, int32_t n_phi, const int64_t* seg_off, int32_t* seg_cell,
+                               double* seg_ds, int64_t* point_off, int64_t* dir_off, double* dir_scale,
+                               double* dir_weight, int32_t* bundle_wall);
+
+// Exclusive scan of int64 counts in place over [0, n] (n + 1 entries; the
+// last entry receives the total); single block.
+cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n);
+cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n);

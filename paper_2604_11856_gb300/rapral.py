@@ -1,0 +1,349 @@
+"""Thin ctypes binding of librapral (include/rapral.h).
+
+Argument marshalling only: device memory and streams come from PyTorch, every
+step of the path runs in the library's CUDA kernels.  Functions carry the
+C-ABI names without the `rapral_` prefix.  There is no CPU fallback: without
+the built library or a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECANCELED = range(6)
+FP64, FP32 = 0, 1
+MAX_DIRS = 65
+_ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ECANCELED: "ECANCELED"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class RapralError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Species(ct.Structure):
+    _fields_ = [("n_species", ct.c_int32), ("kind", ct.c_void_p), ("density_col", ct.c_void_p),
+                ("mass", ct.c_void_p), ("atom_off", ct.c_void_p), ("atom_E", ct.c_void_p),
+                ("atom_g", ct.c_void_p), ("st_off", ct.c_void_p), ("st_E", ct.c_void_p), ("st_g", ct.c_void_p),
+                ("st_sigma", ct.c_void_p), ("st_Lalt", ct.c_void_p), ("st_nv", ct.c_void_p),
+                ("st_nj", ct.c_void_p), ("st_vib_off", ct.c_void_p), ("st_rot_off", ct.c_void_p),
+                ("vib_E", ct.c_void_p), ("rot_E", ct.c_void_p), ("n_atom_levels", ct.c_int64),
+                ("n_states", ct.c_int64), ("n_vib", ct.c_int64), ("n_rot", ct.c_int64)]
+
+
+class Lines(ct.Structure):
+    _fields_ = [("n_lines", ct.c_int64)] + [(k, ct.c_void_p) for k in
+                                             ["lam0", "A", "lamS0", "species", "Eu_el", "Eu_v", "Eu_j", "gu",
+                                              "El_el", "El_v", "El_j", "gl"]]
+
+
+class Cells(ct.Structure):
+    _fields_ = [("n_cells", ct.c_int64), ("Ttr", ct.c_void_p), ("Tve", ct.c_void_p), ("n", ct.c_void_p),
+                ("n_cols", ct.c_int32), ("ne_col", ct.c_int32), ("lnpref", ct.c_void_p)]
+
+
+class Grid(ct.Structure):
+    _fields_ = [("lam_min", ct.c_double), ("lam_max", ct.c_double), ("n", ct.c_int64)]
+
+
+class Rays(ct.Structure):
+    _fields_ = [("n_bundles", ct.c_int64), ("n_points", ct.c_int64), ("n_segments", ct.c_int64),
+                ("n_dirs", ct.c_int64), ("max_dirs", ct.c_int32), ("max_bundles_per_point", ct.c_int32),
+                ("point_off", ct.c_void_p), ("seg_off", ct.c_void_p), ("seg_cell", ct.c_void_p),
+                ("seg_ds", ct.c_void_p), ("dir_off", ct.c_void_p), ("dir_scale", ct.c_void_p),
+                ("dir_weight", ct.c_void_p), ("bundle_wall", ct.c_void_p), ("T_wall", ct.c_double)]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Loads librapral.so (building it with nvcc when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"librapral.so is not built ({path}); run __graft_entry__.build()")
+        L = ct.CDLL(path)
+        i, i32, i64, vp, d = ct.c_int, ct.c_int32, ct.c_int64, ct.c_void_p, ct.c_double
+        P = ct.POINTER
+        sig = {
+            "rapral_create": (i, [P(vp), i, vp]),
+            "rapral_destroy": (None, [vp]),
+            "rapral_last_error": (ct.c_char_p, [vp]),
+            "rapral_set_stream": (i, [vp, vp]),
+            "rapral_sync": (i, [vp]),
+            "rapral_clear_status": (i, [vp]),
+            "rapral_set_constants": (i, [vp, i]),
+            "rapral_set_tiling": (i, [vp, i, i]),
+            "rapral_workspace_bytes": (i, [i64, i64, i64, P(ct.c_size_t)]),
+            "rapral_populations": (i, [vp, P(Species), P(Cells), vp]),
+            "rapral_spectral_coeffs": (i, [vp, P(Species), P(Lines), P(Cells), P(Grid), i64, i64, i, vp, vp, i64]),
+            "rapral_trace_rays": (i, [vp, P(Rays), i64, vp, vp, i64, P(Grid), i64, i64, i, vp, vp]),
+            "rapral_wall_flux": (i, [vp, vp, i, P(Grid), i64, i64, i64, vp]),
+            "rapral_slab_rays": (i, [vp, vp, vp, i32, vp, vp, i32, i32, i32, d, vp, vp, vp, vp, vp, vp, vp, vp,
+                                     P(Rays)]),
+            "rapral_axisym_rays": (i, [vp, vp, i32, vp, i32, vp, i32, vp, vp, i32, i32, vp, P(i64), vp, vp, vp,
+                                       vp, vp, vp, vp, P(Rays)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Context:
+    """A librapral context bound to a CUDA device and stream."""
+
+    def __init__(self, device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("librapral needs a CUDA device; there is no CPU fallback")
+        self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ct.c_void_p()
+        rc = self.lib.rapral_create(ct.byref(h), self.device.index, ct.c_void_p(self.stream.cuda_stream))
+        if rc != OK:
+            raise RapralError(rc, "rapral_create failed")
+        self.h = h
+
+    def check(self, rc):
+        if rc != OK:
+            raise RapralError(rc, self.lib.rapral_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self.check(self.lib.rapral_set_stream(self.h, ct.c_void_p(stream.cuda_stream)))
+
+    def sync(self):
+        self.check(self.lib.rapral_sync(self.h))
+
+    def clear_status(self):
+        self.check(self.lib.rapral_clear_status(self.h))
+
+    def set_tiling(self, tile_width=0, cells_per_block=0):
+        self.check(self.lib.rapral_set_tiling(self.h, tile_width, cells_per_block))
+
+    def set_constants(self, codata):
+        self.check(self.lib.rapral_set_constants(self.h, int(codata)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rapral_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def workspace_bytes(n_lines, n_cells, nk):
+    out = ct.c_size_t()
+    rc = load().rapral_workspace_bytes(int(n_lines), int(n_cells), int(nk), ct.byref(out))
+    if rc != OK:
+        raise RapralError(rc, "rapral_workspace_bytes")
+    return out.value
+
+
+# ----------------------------------------------------------------------------
+# device-resident inputs
+# ----------------------------------------------------------------------------
+
+def _t(a, dtype, device):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).to(device, non_blocking=True)
+
+
+class DeviceSpecies:
+    """Species database on the device plus its rapral_species struct."""
+
+    def __init__(self, sp, device):
+        f8, i4, i8 = np.float64, np.int32, np.int64
+        self.t = dict(kind=_t(sp.kind, i4, device), density_col=_t(sp.density_col, i4, device),
+                      mass=_t(sp.mass, f8, device), atom_off=_t(sp.atom_off, i8, device),
+                      atom_E=_t(sp.atom_E, f8, device), atom_g=_t(sp.atom_g, f8, device),
+                      st_off=_t(sp.st_off, i8, device), st_E=_t(sp.st_E, f8, device), st_g=_t(sp.st_g, f8, device),
+                      st_sigma=_t(sp.st_sigma, f8, device), st_Lalt=_t(sp.st_Lalt, f8, device),
+                      st_nv=_t(sp.st_nv, i4, device), st_nj=_t(sp.st_nj, i4, device),
+                      st_vib_off=_t(sp.st_vib_off, i8, device), st_rot_off=_t(sp.st_rot_off, i8, device),
+                      vib_E=_t(sp.vib_E, f8, device), rot_E=_t(sp.rot_E, f8, device))
+        s = Species()
+        s.n_species = len(sp.names)
+        for k, v in self.t.items():
+            setattr(s, k, v.data_ptr() if v.numel() else None)
+        s.n_atom_levels = int(sp.atom_E.shape[0]); s.n_states = int(sp.st_E.shape[0])
+        s.n_vib = int(sp.vib_E.shape[0]); s.n_rot = int(sp.rot_E.shape[0])
+        self.struct = s
+        self.S = s.n_species
+
+
+LINE_KEYS = ["lam0", "A", "lamS0", "Eu_el", "Eu_v", "Eu_j", "gu", "El_el", "El_v", "El_j", "gl"]
+
+
+class DeviceLines:
+    def __init__(self, ln, device, tensors=None):
+        if tensors is None:
+            tensors = {k: _t(getattr(ln, k), np.float64, device) for k in LINE_KEYS}
+            tensors["species"] = _t(ln.species, np.int32, device)
+        self.t = tensors
+        s = Lines()
+        s.n_lines = int(tensors["lam0"].shape[0])
+        for k, v in tensors.items():
+            setattr(s, k, v.data_ptr() if v.numel() else None)
+        self.struct = s
+        self.L = s.n_lines
+
+
+class DeviceCells:
+    def __init__(self, cells, S, device, tensors=None):
+        if tensors is None:
+            tensors = dict(Ttr=_t(cells.Ttr, np.float64, device), Tve=_t(cells.Tve, np.float64, device),
+                           n=_t(cells.n, np.float64, device))
+        self.t = tensors
+        C = int(tensors["Ttr"].shape[0])
+        self.lnpref = torch.empty((C, S), dtype=torch.float64, device=device)
+        s = Cells()
+        s.n_cells = C
+        s.Ttr, s.Tve, s.n = tensors["Ttr"].data_ptr(), tensors["Tve"].data_ptr(), tensors["n"].data_ptr()
+        s.n_cols = int(tensors["n"].shape[1])
+        s.ne_col = int(getattr(cells, "ne_col", 10)) if cells is not None else 10
+        s.lnpref = self.lnpref.data_ptr()
+        self.struct = s
+        self.C = C
+
+
+def grid_struct(g):
+    s = Grid()
+    s.lam_min, s.lam_max, s.n = float(g.lam_min), float(g.lam_max), int(g.n)
+    return s
+
+
+# ----------------------------------------------------------------------------
+# the C-ABI calls
+# ----------------------------------------------------------------------------
+
+def populations(ctx, dsp, dcells):
+    ctx.check(ctx.lib.rapral_populations(ctx.h, ct.byref(dsp.struct), ct.byref(dcells.struct),
+                                         _ptr(dcells.lnpref)))
+    return dcells.lnpref
+
+
+def spectral_coeffs(ctx, dsp, dlines, dcells, grid, k0, nk, precision, kappa, emis):
+    """kappa, emis: [C, ld] tensors of the precision's dtype (written columns 0..nk-1)."""
+    ld = kappa.shape[1]
+    assert emis.shape[1] == ld and kappa.is_contiguous() and emis.is_contiguous()
+    g = grid_struct(grid)
+    ctx.check(ctx.lib.rapral_spectral_coeffs(ctx.h, ct.byref(dsp.struct), ct.byref(dlines.struct),
+                                             ct.byref(dcells.struct), ct.byref(g), int(k0), int(nk),
+                                             int(precision), _ptr(kappa), _ptr(emis), int(ld)))
+
+
+def trace_rays(ctx, rays, n_cells, kappa, emis, grid, k0, nk, precision, q_lambda, I_out=None):
+    g = grid_struct(grid)
+    ctx.check(ctx.lib.rapral_trace_rays(ctx.h, ct.byref(rays.struct), int(n_cells), _ptr(kappa), _ptr(emis),
+                                        int(kappa.shape[1]), ct.byref(g), int(k0), int(nk), int(precision),
+                                        _ptr(q_lambda), _ptr(I_out)))
+
+
+def wall_flux(ctx, q_lambda, precision, grid, k0, nk, n_points, q):
+    g = grid_struct(grid)
+    ctx.check(ctx.lib.rapral_wall_flux(ctx.h, _ptr(q_lambda), int(precision), ct.byref(g), int(k0), int(nk),
+                                       int(n_points), _ptr(q)))
+
+
+class DeviceRays:
+    """Caller-owned ray arrays (torch tensors) and their rapral_rays struct."""
+
+    def __init__(self):
+        self.t = {}
+        self.struct = Rays()
+
+    @property
+    def n_points(self):
+        return self.struct.n_points
+
+    @property
+    def n_dirs(self):
+        return self.struct.n_dirs
+
+
+def slab_rays(ctx, geo, device):
+    """Tangent-slab bundle (rapral_slab_rays) from a SlabGeometry."""
+    r = DeviceRays()
+    m = int(len(geo.cell_order))
+    n_mu = int(len(geo.mu))
+    nd = n_mu + (1 if geo.normal_ray else 0)
+    i32, i64, f8 = torch.int32, torch.int64, torch.float64
+    t = r.t
+    t["cell_order"] = _t(geo.cell_order, np.int32, device)
+    t["dx"] = _t(geo.dx, np.float64, device)
+    t["mu"] = _t(geo.mu, np.float64, device)
+    t["wmu"] = _t(geo.wmu, np.float64, device)
+    t["point_off"] = torch.empty(2, dtype=i64, device=device)
+    t["seg_off"] = torch.empty(2, dtype=i64, device=device)
+    t["seg_cell"] = torch.empty(max(m, 1), dtype=i32, device=device)
+    t["seg_ds"] = torch.empty(max(m, 1), dtype=f8, device=device)
+    t["dir_off"] = torch.empty(2, dtype=i64, device=device)
+    t["dir_scale"] = torch.empty(nd, dtype=f8, device=device)
+    t["dir_weight"] = torch.empty(nd, dtype=f8, device=device)
+    t["bundle_wall"] = torch.empty(1, dtype=i32, device=device)
+    ctx.check(ctx.lib.rapral_slab_rays(ctx.h, _ptr(t["cell_order"]), _ptr(t["dx"]), m, _ptr(t["mu"]),
+                                       _ptr(t["wmu"]), n_mu, int(bool(geo.normal_ray)), int(bool(geo.wall_start)),
+                                       float(geo.T_wall), _ptr(t["point_off"]), _ptr(t["seg_off"]),
+                                       _ptr(t["seg_cell"]), _ptr(t["seg_ds"]), _ptr(t["dir_off"]),
+                                       _ptr(t["dir_scale"]), _ptr(t["dir_weight"]), _ptr(t["bundle_wall"]),
+                                       ct.byref(r.struct)))
+    return r
+
+
+def axisym_rays(ctx, geo, device, points=None):
+    """Axisymmetric lines of sight (rapral_axisym_rays) from an AxisymGeometry;
+    `points` selects a subset of the surface points."""
+    r = DeviceRays()
+    t = r.t
+    sx = np.asarray(geo.surf_x) if points is None else np.asarray(geo.surf_x)[np.asarray(points)]
+    P = int(len(sx)); n_mu = int(len(geo.mu)); n_phi = int(geo.n_phi)
+    B = P * n_mu * n_phi
+    nx, nr = len(geo.xf) - 1, len(geo.rf) - 1
+    t["xf"] = _t(geo.xf, np.float64, device); t["rf"] = _t(geo.rf, np.float64, device)
+    t["surf_x"] = _t(sx, np.float64, device)
+    t["mu"] = _t(geo.mu, np.float64, device); t["wmu"] = _t(geo.wmu, np.float64, device)
+    t["seg_off"] = torch.empty(B + 1, dtype=torch.int64, device=device)
+    nseg = ct.c_int64()
+    args0 = [ctx.h, _ptr(t["xf"]), nx, _ptr(t["rf"]), nr, _ptr(t["surf_x"]), P, _ptr(t["mu"]), _ptr(t["wmu"]),
+             n_mu, n_phi, _ptr(t["seg_off"]), ct.byref(nseg)]
+    ctx.check(ctx.lib.rapral_axisym_rays(*args0, None, None, None, None, None, None, None, None))
+    n = int(nseg.value)
+    t["seg_cell"] = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    t["seg_ds"] = torch.empty(max(n, 1), dtype=torch.float64, device=device)
+    t["point_off"] = torch.empty(P + 1, dtype=torch.int64, device=device)
+    t["dir_off"] = torch.empty(B + 1, dtype=torch.int64, device=device)
+    t["dir_scale"] = torch.empty(B, dtype=torch.float64, device=device)
+    t["dir_weight"] = torch.empty(B, dtype=torch.float64, device=device)
+    t["bundle_wall"] = torch.empty(B, dtype=torch.int32, device=device)
+    ctx.check(ctx.lib.rapral_axisym_rays(*args0, _ptr(t["seg_cell"]), _ptr(t["seg_ds"]), _ptr(t["point_off"]),
+                                         _ptr(t["dir_off"]), _ptr(t["dir_scale"]), _ptr(t["dir_weight"]),
+                                         _ptr(t["bundle_wall"]), ct.byref(r.struct)))
+    return r

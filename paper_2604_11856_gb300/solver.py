@@ -1,0 +1,153 @@
+"""Whole solves over the C-ABI: populations -> spectral coefficients (per
+spectral chunk) -> ray march -> wall flux.
+
+`DeviceProblem` holds a problem's inputs resident on the device; `solve`
+runs the path on them (optionally in spectral chunks, with the line sum of
+chunk k+1 overlapping the march of chunk k on a second stream);
+`solve_host` is the end-to-end call that starts from host arrays, copies
+them in, and returns the wall flux on the host.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import rapral as R
+from . import synth
+
+
+class DeviceProblem:
+    """A problem's species, lines, cells, rays and grid on one device."""
+
+    def __init__(self, problem, ctx, points=None, lines=None, species=None):
+        dev = ctx.device
+        self.problem = problem
+        self.grid = problem.grid
+        self.species = species if species is not None else R.DeviceSpecies(problem.species, dev)
+        self.lines = lines if lines is not None else R.DeviceLines(problem.lines, dev)
+        self.cells = R.DeviceCells(problem.cells, self.species.S, dev)
+        geo = problem.geometry
+        if isinstance(geo, synth.SlabGeometry):
+            self.rays = R.slab_rays(ctx, geo, dev)
+        elif isinstance(geo, synth.AxisymGeometry):
+            self.rays = R.axisym_rays(ctx, geo, dev, points=points)
+        else:
+            raise TypeError(f"unknown geometry {type(geo)}")
+        self.C = self.cells.C
+        self.P = self.rays.n_points
+
+
+def _dtype(precision):
+    return torch.float64 if precision == R.FP64 else torch.float32
+
+
+def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensity=False, ctx2=None,
+          buffers=None):
+    """Runs the whole path on device-resident inputs.  Returns a dict with
+    q [P] (FP64, device) and, on request, kappa / emis [C, n] and
+    q_lambda [P, n] / I [n_dirs, n] for the whole grid (single chunk only).
+    With ctx2 (a second context on another stream) chunk k+1's line sum
+    overlaps chunk k's march."""
+    n = dp.grid.n
+    chunk = n if not chunk else min(chunk, n)
+    dev = ctx.device
+    dt = _dtype(precision)
+    C, P = dp.C, dp.P
+    q = torch.zeros(P, dtype=torch.float64, device=dev)
+    R.populations(ctx, dp.species, dp.cells)
+    nbuf = 2 if ctx2 is not None else 1
+    if buffers is None:
+        buffers = [(torch.empty((C, chunk), dtype=dt, device=dev), torch.empty((C, chunk), dtype=dt, device=dev))
+                   for _ in range(nbuf)]
+    qlam = torch.empty((P, chunk), dtype=dt, device=dev)
+    out = {}
+    I = None
+    if keep_intensity:
+        I = torch.empty((dp.rays.n_dirs, chunk), dtype=dt, device=dev)
+    starts = list(range(0, n, chunk))
+    if ctx2 is None:
+        for k0 in starts:
+            nk = min(chunk, n - k0)
+            kap, em = buffers[0]
+            R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
+            R.trace_rays(ctx, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)
+            R.wall_flux(ctx, qlam, precision, dp.grid, k0, nk, P, q)
+    else:
+        # two streams: coefficients of chunk i on ctx (stream A), march + flux on ctx2 (stream B)
+        sa, sb = ctx.stream, ctx2.stream
+        ready = [torch.cuda.Event() for _ in starts]
+        free = [torch.cuda.Event() for _ in range(nbuf)]
+        used = [False] * nbuf
+        ev_pop = torch.cuda.Event()
+        ev_pop.record(sa)
+        sb.wait_event(ev_pop)
+        for i, k0 in enumerate(starts):
+            nk = min(chunk, n - k0)
+            kap, em = buffers[i % nbuf]
+            if used[i % nbuf]:
+                sa.wait_event(free[i % nbuf])
+            R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
+            ready[i].record(sa)
+            sb.wait_event(ready[i])
+            R.trace_rays(ctx2, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)
+            R.wall_flux(ctx2, qlam, precision, dp.grid, k0, nk, P, q)
+            free[i % nbuf].record(sb)
+            used[i % nbuf] = True
+        done = torch.cuda.Event()
+        done.record(sb)
+        sa.wait_event(done)
+    out["q"] = q
+    if len(starts) == 1:
+        if keep_coeffs:
+            out["kappa"], out["emis"] = buffers[0]
+        out["q_lambda"] = qlam
+        if keep_intensity:
+            out["I"] = I
+    return out
+
+
+def solve_host(problem, precision=R.FP64, chunk=None, ctx=None, device=None):
+    """End-to-end: host arrays in, wall flux out.  Inputs are staged through
+    pinned host memory and copied on the context's stream; the result is
+    read back to the host.  Returns (q numpy array, bytes in, bytes out)."""
+    if ctx is None:
+        ctx = R.Context(device)
+    dev = ctx.device
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+    with torch.cuda.stream(ctx.stream):
+        sp = problem.species
+        hs = dict(kind=pin(sp.kind, np.int32), density_col=pin(sp.density_col, np.int32), mass=pin(sp.mass, np.float64),
+                  atom_off=pin(sp.atom_off, np.int64), atom_E=pin(sp.atom_E, np.float64),
+                  atom_g=pin(sp.atom_g, np.float64), st_off=pin(sp.st_off, np.int64), st_E=pin(sp.st_E, np.float64),
+                  st_g=pin(sp.st_g, np.float64), st_sigma=pin(sp.st_sigma, np.float64),
+                  st_Lalt=pin(sp.st_Lalt, np.float64), st_nv=pin(sp.st_nv, np.int32), st_nj=pin(sp.st_nj, np.int32),
+                  st_vib_off=pin(sp.st_vib_off, np.int64), st_rot_off=pin(sp.st_rot_off, np.int64),
+                  vib_E=pin(sp.vib_E, np.float64), rot_E=pin(sp.rot_E, np.float64))
+        hl = {k: pin(getattr(problem.lines, k), np.float64) for k in R.LINE_KEYS}
+        hl["species"] = pin(problem.lines.species, np.int32)
+        hc = dict(Ttr=pin(problem.cells.Ttr, np.float64), Tve=pin(problem.cells.Tve, np.float64),
+                  n=pin(problem.cells.n, np.float64))
+        nbytes = sum(t.numel() * t.element_size() for d in (hs, hl, hc) for t in d.values())
+        dl = {k: v.to(dev, non_blocking=True) for k, v in hl.items()}
+        dc = {k: v.to(dev, non_blocking=True) for k, v in hc.items()}
+        dsp = R.DeviceSpecies.__new__(R.DeviceSpecies)
+        dsp.t = {k: v.to(dev, non_blocking=True) for k, v in hs.items()}
+        s = R.Species()
+        s.n_species = len(sp.names)
+        for k, v in dsp.t.items():
+            setattr(s, k, v.data_ptr() if v.numel() else None)
+        s.n_atom_levels, s.n_states = int(sp.atom_E.shape[0]), int(sp.st_E.shape[0])
+        s.n_vib, s.n_rot = int(sp.vib_E.shape[0]), int(sp.rot_E.shape[0])
+        dsp.struct, dsp.S = s, s.n_species
+        dp = DeviceProblem.__new__(DeviceProblem)
+        dp.problem, dp.grid, dp.species = problem, problem.grid, dsp
+        dp.lines = R.DeviceLines(None, dev, tensors=dl)
+        dp.cells = R.DeviceCells(problem.cells, dsp.S, dev, tensors=dc)
+        geo = problem.geometry
+        dp.rays = R.slab_rays(ctx, geo, dev) if isinstance(geo, synth.SlabGeometry) else R.axisym_rays(ctx, geo, dev)
+        dp.C, dp.P = dp.cells.C, dp.rays.n_points
+        res = solve(dp, ctx, precision, chunk)
+        q_host = torch.empty(res["q"].shape, dtype=torch.float64).pin_memory()
+        q_host.copy_(res["q"], non_blocking=True)
+    ctx.sync()
+    return q_host.numpy().copy(), nbytes, q_host.numel() * 8
