@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the RAPRAL hot path on GB300.
+
+A step is one whole solve of the stagnation-line workload (200 two-temperature
+cells, 20,000 atomic + 300,000 molecular lines, 1,000,000-point grid over
+50-2000 nm, 16-direction tangent slab plus the normal ray): populations ->
+line binning -> line-by-line kappa / j -> ray march -> wall flux, with inputs
+resident in HBM.  The FP32-chosen arithmetic is the headline; the FP64-plain
+path on the same workload is measured beside it.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "cell·λ coeff points/s and ray·λ segments/s; served q_rad p50/p99 vs FP64 plain"
+WORKLOAD = "stagnation line: 200 cells, 20k atomic + 300k molecular lines, 1e6-point grid 50-2000 nm, 16-mu tangent slab"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["rapral", "reference"], default="rapral")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain side measurement")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--cells", type=int, default=200,
+                    help="cells of the stagnation line (fewer only for profiler captures)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def cpu_baseline(problem, seconds, precision_note="f64"):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    workload: every line, the whole grid, a few cells (one per thread), for
+    about `seconds`; reported as coefficient cell*lambda points per second."""
+    import oracle
+    from paper_2604_11856_gb300 import synth
+    threads = oracle.lib().orc_num_threads()
+    p = problem
+    # first estimate with one cell per thread on a 1/20 slice of the grid
+    n_cells = max(1, threads)
+    idx = np.linspace(0, len(p.cells) - 1, n_cells).round().astype(int)
+    cells = synth.Cells(Ttr=p.cells.Ttr[idx], Tve=p.cells.Tve[idx], n=p.cells.n[idx])
+    sub = synth.Problem(p.name, p.species, p.lines, cells, p.grid, p.geometry)
+    lnp = oracle.lnpref(sub)
+    nk = p.grid.n // 20
+    t0 = time.perf_counter()
+    oracle.spectral_coeffs(sub, lnp, 0, nk)
+    dt = time.perf_counter() - t0
+    # grow the slice towards the time budget
+    nk2 = int(min(p.grid.n, nk * max(1.0, seconds / max(dt, 1e-3))))
+    k0 = (p.grid.n - nk2) // 2
+    t0 = time.perf_counter()
+    oracle.spectral_coeffs(sub, lnp, k0, nk2)
+    dt2 = time.perf_counter() - t0
+    return {"value": n_cells * nk2 / dt2, "unit": "cell·λ points/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_cells} of {len(p.cells)} cells x {nk2} of {p.grid.n} grid points, all "
+                      f"{len(p.lines)} lines, kappa and j in FP64 ({dt2:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, bounded samples of the
+    bench workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2604_11856_gb300 import synth
+    p = synth.stagnation_line()
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(p, per_step / 4)
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(p, per_step)
+        vals.append(last["value"])
+    v = float(np.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": "cell·λ points/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": last["sample"]},
+            "cpu_baseline": {**last, "value": v},
+            "e2e": {"value": v, "unit": "cell·λ points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    precision = R.FP32 if args.precision == "fp32" else R.FP64
+
+    p = synth.stagnation_line(n_cells=args.cells)
+    ctx = R.Context(local)
+    if args.tile:
+        ctx.set_tiling(tile_width=args.tile)
+    dp = solver.DeviceProblem(p, ctx)
+    C, K = dp.C, p.grid.n
+    n_dirs = dp.rays.n_dirs
+    seg_lambda = C * n_dirs * K          # segments x directions x wavelengths per step
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    dt = torch.float32 if precision == R.FP32 else torch.float64
+    bufs = [(torch.empty((C, K), dtype=dt, device=dev), torch.empty((C, K), dtype=dt, device=dev))]
+    stream = ctx.stream
+
+    def step(ev_pair=None):
+        if ev_pair is not None:
+            ctx.set_profile_events(*ev_pair)
+        out = solver.solve(dp, ctx, precision, buffers=bufs)
+        if ev_pair is not None:
+            ctx.set_profile_events(None, None)
+        return out
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    ctx.reset_stats()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in k3:   # materialise the events before handing them to the library
+        a.record(stream); b.record(stream)
+    barrier()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))              # evict L2 between steps (outside the timed window)
+            starts[i].record(stream)
+            step(k3[i])
+            ends[i].record(stream)
+        barrier()
+    t_wall = time.perf_counter() - t_wall
+    ctx.sync()
+    step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+    k3_ms = [k3[i][0].elapsed_time(k3[i][1]) for i in range(args.steps)]
+    stats = ctx.get_stats()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * C * K / (ms_per_step * 1e-3)
+    evals_per_step = stats["evaluations"] / args.steps
+    k3_mean = float(np.mean(k3_ms))
+
+    # roofline of the line sum: transcendental (XU / MUFU) work the FP32
+    # profile needs: rcp + 2 rsqrt per evaluation, + ex2 for the Gaussian core
+    # and + ex2 for the correction term where they do not underflow
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    if precision == R.FP32:
+        xu_ops = (3 * stats["evaluations"] + stats["gauss_terms"] + stats["correction_terms"]) / args.steps
+        peak = n_sm * 16 * sm_max / 1e9               # Gop/s: 16 XU lanes per SM per clock
+        achieved = xu_ops / (k3_mean * 1e-3) / 1e9
+        roof = {"bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)", "achieved": achieved, "peak": peak,
+                "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "k_line_sum_f32", "kernel_ms": k3_mean, "evaluations": evals_per_step,
+                "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"}
+    else:
+        # FP64: ~40 FP64 operations per evaluation, 2 FP64 FMA lanes per SM per clock
+        fp64_ops = 40.0 * evals_per_step
+        peak = n_sm * 2 * 2 * sm_max / 1e9
+        achieved = fp64_ops / (k3_mean * 1e-3) / 1e9
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_line_sum_f64", "kernel_ms": k3_mean,
+                "evaluations": evals_per_step}
+
+    out = {"metric": METRIC, "value": value, "unit": "cell·λ points/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if precision == R.FP32 else "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": args.precision + ("-chosen" if precision == R.FP32 else "-plain"),
+                      "cells": C, "lines": len(p.lines), "grid_points": K, "directions": n_dirs,
+                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+           "secondary": {"ray_lambda_segments_per_s": world * seg_lambda / (ms_per_step * 1e-3),
+                         "profile_evaluations_per_s": world * evals_per_step / (ms_per_step * 1e-3),
+                         "line_sum_ms": k3_mean, "wall_s": t_wall},
+           "roofline": roof, "clocks": clk.summary(), "gpu_launches": None}
+    # launches per step: validate x2, line prep, cell prep, bounds, count, scan, fill, line sum,
+    # populations + its validation, march + its validation, flux, slab rays are built once
+    out["gpu_launches"] = 14 * args.steps
+
+    if not args.no_fp64 and precision == R.FP32:
+        bufs64 = [(torch.empty((C, K), dtype=torch.float64, device=dev),
+                   torch.empty((C, K), dtype=torch.float64, device=dev))]
+        r64 = solver.solve(dp, ctx, R.FP64, buffers=bufs64)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        r64 = solver.solve(dp, ctx, R.FP64, buffers=bufs64)
+        e1.record(stream)
+        ctx.sync()
+        ms64 = e0.elapsed_time(e1)
+        r32 = step()
+        ctx.sync()
+        q32, q64 = float(r32["q"].item()), float(r64["q"].item())
+        out["fp64_plain"] = {"value": C * K / (ms64 * 1e-3), "ms_per_step": ms64, "q_W_cm2": q64,
+                             "fp32_q_W_cm2": q32, "fp32_q_rel_err": abs(q32 / q64 - 1)}
+        del bufs64
+
+    if not args.no_e2e:
+        # end to end through the public API: host arrays -> pinned staging -> device -> q on the host
+        ectx = R.Context(local)
+        solver.solve_host(p, precision, ctx=ectx)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(3, args.steps))
+        for _ in range(n_e2e):
+            qh, bi, bo = solver.solve_host(p, precision, ctx=ectx)
+        te = (time.perf_counter() - t0) / n_e2e
+        out["e2e"] = {"value": world * C * K / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
+                      "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3}
+        ectx.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -181,10 +181,31 @@ RAPRAL_API int rapral_clear_status(rapral_ctx* ctx);
  * 1 = CODATA 2018. */
 RAPRAL_API int rapral_set_constants(rapral_ctx* ctx, int codata);
 
-/* Spectral tile width (grid points per line-sum tile; multiple of 128,
- * 128 .. 8192) and cells per line-sum block (1, 2 or 4).  0 keeps the
- * current value.  Used by the autotuner. */
+/* Spectral tile width (grid points per line-sum tile: 128, 256, 512 or
+ * 1024; FP64 up to 512) and cells per line-sum block (1, 2 or 4).  0 keeps
+ * the current value.  Used by the autotuner. */
 RAPRAL_API int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block);
+
+/* Work counters of the line sum, accumulated over rapral_spectral_coeffs
+ * calls since the last reset: in-window (line, cell, grid point) profile
+ * evaluations, how many of them needed the Gaussian core term and the
+ * exponential correction term in the chosen arithmetic (the others underflow
+ * to zero), and (line, cell, tile) pairs set up. */
+typedef struct {
+    int64_t evaluations;
+    int64_t gauss_terms;
+    int64_t correction_terms;
+    int64_t pairs;
+} rapral_stats;
+
+/* Reads the counters (synchronises the stream). */
+RAPRAL_API int rapral_get_stats(rapral_ctx* ctx, rapral_stats* out);
+RAPRAL_API int rapral_reset_stats(rapral_ctx* ctx);
+
+/* Records the CUDA events `before` / `after` (cudaEvent_t, caller-owned) on
+ * the context's stream immediately around every line-sum kernel launch, so a
+ * caller can time that kernel alone.  NULL, NULL turns it off. */
+RAPRAL_API int rapral_set_profile_events(rapral_ctx* ctx, void* before, void* after);
 
 /* Device bytes the context's workspace needs for a solve of this size
  * (lines L, spectral range nk); for admission control.  Host-only. */

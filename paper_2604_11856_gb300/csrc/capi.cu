@@ -83,6 +83,8 @@ int rapral_create(rapral_ctx** out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 16 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
@@ -99,8 +101,38 @@ void rapral_destroy(rapral_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_stats) cudaFree(ctx->d_stats);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
+}
+
+int rapral_get_stats(rapral_ctx* ctx, rapral_stats* out) {
+    if (!ctx || !out) return RAPRAL_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_stats, 4 * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "stats read-back");
+    const unsigned long long* v = reinterpret_cast<const unsigned long long*>(ctx->h_pinned);
+    out->evaluations = (int64_t)v[0];
+    out->gauss_terms = (int64_t)v[1];
+    out->correction_terms = (int64_t)v[2];
+    out->pairs = (int64_t)v[3];
+    return RAPRAL_OK;
+}
+
+int rapral_reset_stats(rapral_ctx* ctx) {
+    if (!ctx) return RAPRAL_EINVAL;
+    cudaSetDevice(ctx->device);
+    return cuda_status(ctx, cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream),
+                       "stats reset");
+}
+
+int rapral_set_profile_events(rapral_ctx* ctx, void* before, void* after) {
+    if (!ctx || ((before == nullptr) != (after == nullptr))) return RAPRAL_EINVAL;
+    ctx->ev_before = reinterpret_cast<cudaEvent_t>(before);
+    ctx->ev_after = reinterpret_cast<cudaEvent_t>(after);
+    return RAPRAL_OK;
 }
 
 const char* rapral_last_error(const rapral_ctx* ctx) { return ctx ? ctx->err : "no context"; }
@@ -132,9 +164,8 @@ int rapral_set_constants(rapral_ctx* ctx, int codata) {
 int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block) {
     if (!ctx) return RAPRAL_EINVAL;
     if (tile_width != 0) {
-        if (tile_width != 128 && tile_width != 256 && tile_width != 512 && tile_width != 1024 &&
-            tile_width != 2048 && tile_width != 4096 && tile_width != 8192)
-            return set_error(ctx, RAPRAL_EINVAL, "tile width %d not a power of two in 128..8192", tile_width);
+        if (tile_width != 128 && tile_width != 256 && tile_width != 512 && tile_width != 1024)
+            return set_error(ctx, RAPRAL_EINVAL, "tile width %d not one of 128, 256, 512, 1024", tile_width);
         ctx->tile_w = tile_width;
     }
     if (cells_per_block != 0) {
@@ -216,8 +247,9 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
         return cuda_status(ctx, e, "zero coefficients");
     }
     const int W = ctx->tile_w;
-    if (precision == RAPRAL_FP64 && W > 512)
-        return set_error(ctx, RAPRAL_EINVAL, "FP64 line sum supports tile widths 128..512 (got %d)", W);
+    if ((precision == RAPRAL_FP64 && W > 512) || W > 1024)
+        return set_error(ctx, RAPRAL_EINVAL, "line sum supports tile widths 128..%d in this precision (got %d)",
+                         precision == RAPRAL_FP64 ? 512 : 1024, W);
     const int64_t T = (nk + W - 1) / W;
     if (T > 65535) return set_error(ctx, RAPRAL_EINVAL, "range of %lld points needs more than 65535 tiles", (long long)nk);
     const double h = grid_h(g);
@@ -276,7 +308,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     a.lp = lp; a.cp = cp; a.lnpref = cells->lnpref; a.S = sp->n_species; a.C = C;
     a.tile_off = plan.tile_off; a.tile_lines = plan.tile_lines;
     a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk; a.ld = ld; a.tile_w = W;
-    a.kappa = kappa; a.emis = emis; a.status = ctx->d_status;
+    a.kappa = kappa; a.emis = emis; a.status = ctx->d_status; a.stats = ctx->d_stats;
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");
 }

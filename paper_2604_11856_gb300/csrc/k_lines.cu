@@ -53,14 +53,23 @@ __global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, do
     p.lam0 = lam0;
     p.lnAj = log(1e-7 * (ph.h * ph.c / (4.0 * M_PI)) * A / lcm);
     p.lnAk = log(1e4 * A * (lcm * lcm) * (lcm * lcm) / (8.0 * M_PI * ph.c));
+    p.lngu = log(ln.gu[l]);
     p.Eve_u = ln.Eu_el[l] + ln.Eu_v[l];
     p.Er_u = ln.Eu_j[l];
-    p.lngu = log(ln.gu[l]);
-    p.dEve = (ln.Eu_el[l] + ln.Eu_v[l]) - (ln.El_el[l] + ln.El_v[l]);
-    p.dEr = ln.Eu_j[l] - ln.El_j[l];
+    p.Eve_l = ln.El_el[l] + ln.El_v[l];
+    p.Er_l = ln.El_j[l];
+    p.dEve = p.Eve_u - p.Eve_l;
+    p.dEr = p.Er_u - p.Er_l;
     p.cD = RAPRAL_DOPPLER_HALF * lam0 / sqrt(mass[s]);
     p.lamS0 = ln.lamS0[l];
     p.tpos = (lam0 - lam_min) / h;
+    p.dEve_f = (float)p.dEve;
+    p.dEr_f = (float)p.dEr;
+    p.cD_f = (float)p.cD;
+    p.lamS0_f = (float)p.lamS0;
+    const double kcd = rint(p.tpos);
+    p.kc = (int32_t)fmin(fmax(kcd, -1e9), 2e9);
+    p.delta_f = (float)(p.tpos - (double)p.kc);
     p.species = s;
     p.pad = 0;
     out[l] = p;
@@ -212,6 +221,23 @@ __global__ void __launch_bounds__(1024) k_scan(T* data, int64_t n) {
 
 // ------------------------------------------------------------ line sum FP64
 
+// Block-wide sum of the per-thread work counters, one atomic per counter.
+__device__ void block_count(unsigned long long* stats, int64_t ev, int64_t g, int64_t c, int64_t p) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        p += __shfl_xor_sync(0xffffffffu, p, o);
+    }
+    if ((threadIdx.x & 31) == 0 && p > 0) {
+        atomicAdd(&stats[0], (unsigned long long)ev);
+        atomicAdd(&stats[1], (unsigned long long)g);
+        atomicAdd(&stats[2], (unsigned long long)c);
+        atomicAdd(&stats[3], (unsigned long long)p);
+    }
+}
+
 struct __align__(16) PairF64 {
     double lam0, w100, inv2V, r, omr, c16, aj, ak;
     int klo, khi, pad0, pad1;
@@ -227,6 +253,7 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
     const int64_t kend = min(kt0 + W, a.k0 + a.nk);   // exclusive
     const int64_t kp = kt0 + (int64_t)threadIdx.x * PPT;
     __shared__ PairF64 pr[128];
+    int64_t n_ev = 0, n_g = 0, n_c = 0, n_pairs = 0;
     double acck[PPT], accj[PPT];
 #pragma unroll
     for (int i = 0; i < PPT; ++i) { acck[i] = 0.0; accj[i] = 0.0; }
@@ -261,6 +288,19 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 const double hi = floor((L.lam0 + P.w100 - a.lam_min) / a.h) + 1.0;
                 P.klo = (int)fmax(lo, (double)kt0);
                 P.khi = (int)fmin(hi, (double)(kend - 1));
+                if (P.klo <= P.khi) {
+                    // counters: candidate points (the exact window is tested per point), and
+                    // those where the two exponentials are above the FP64 underflow limit
+                    const double kcen = L.tpos;
+                    const double hg = 16.4 * 2.0 * lamV / a.h, hc = 28.4 * 2.0 * lamV / a.h;   // 2.772u^2, 0.4u^2.25 < 745.5
+                    n_ev += min((int64_t)P.khi, (int64_t)floor(kcen + RAPRAL_WINDOW * lamV / a.h)) -
+                            max((int64_t)P.klo, (int64_t)ceil(kcen - RAPRAL_WINDOW * lamV / a.h)) + 1;
+                    n_g += max((int64_t)0, min((int64_t)P.khi, (int64_t)floor(kcen + hg)) -
+                                               max((int64_t)P.klo, (int64_t)ceil(kcen - hg)) + 1);
+                    n_c += max((int64_t)0, min((int64_t)P.khi, (int64_t)floor(kcen + hc)) -
+                                               max((int64_t)P.klo, (int64_t)ceil(kcen - hc)) + 1);
+                    ++n_pairs;
+                }
             }
             pr[threadIdx.x] = P;
         }
@@ -292,12 +332,194 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
         }
         __syncthreads();
     }
+    block_count(a.stats, n_ev, n_g, n_c, n_pairs);
     double* K = reinterpret_cast<double*>(a.kappa) + c * a.ld - a.k0;
     double* J = reinterpret_cast<double*>(a.emis) + c * a.ld - a.k0;
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
         const int64_t k = kp + i;
         if (k < kend) { K[k] = acck[i]; J[k] = accj[i]; }
+    }
+}
+
+
+// ------------------------------------------------------ line sum FP32 (chosen)
+//
+// Set-up per (line, cell): log-space populations and strengths in FP64,
+// exponentials of the reduced log (integer power of two times 2^f, f in
+// [0, 1)) in FP32; widths, Voigt HWHM and profile constants in FP32.  The
+// window [klo, khi] is found in grid units in FP32 and certified: when an edge
+// lies within the FP32 error bound of a grid point, both edges are decided
+// again with the FP64 Voigt width and the literal test |lam_k - lam0| <=
+// 100 lamV, so every (line, point) inclusion matches the FP64 decision.
+// Per point: u = |(k - kc) s - u0| (s = h / 2lamV), the Whiting bracket with
+// MUFU ex2 / rsqrt / rcp, terms that underflow FP32 skipped, and Kahan
+// compensated sums of kappa and j over the tile's lines.
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// e^y for an FP64 exponent: y log2(e) = n + f, n integer, f in [0, 1);
+// 2^f in FP32, scaled by 2^n (0 below the FP32 range).
+__device__ __forceinline__ float exp_reduced(double y) {
+    const double t = y * 1.4426950408889634;
+    if (!(t > -200.0)) return 0.0f;
+    const double n = floor(fmin(t, 200.0));
+    return ldexpf(exp2f((float)(t - n)), (int)n);
+}
+
+__device__ __forceinline__ bool in_window64(int64_t k, double lam_min, double h, double lam0, double w100) {
+    const double lk = __dadd_rn(lam_min, __dmul_rn((double)k, h));
+    return fabs(lk - lam0) <= w100;
+}
+
+// Exact edges near the FP32 estimates (the estimate is within a fraction of a
+// grid point of the truth).
+__device__ void exact_edges(const LinePrep& L, const CellPrep& cp, double lam_min, double h, int64_t* klo,
+                            int64_t* khi) {
+    const double lamG = L.cD * cp.sqrtT;
+    const double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
+    const double w100 = RAPRAL_WINDOW * voigt_hwhm(lamL, lamG);
+    int64_t k = *khi + 2;
+    while (k > *khi - 3 && !in_window64(k, lam_min, h, L.lam0, w100)) --k;
+    const int64_t hi = k;
+    k = *klo - 2;
+    while (k < *klo + 3 && !in_window64(k, lam_min, h, L.lam0, w100)) ++k;
+    *klo = k;
+    *khi = hi;
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(128) k_line_sum_f32(LineSumArgs a) {
+    if (*a.status) return;
+    constexpr int W = 128 * PPT;
+    const int t = blockIdx.y;
+    const int64_t c = blockIdx.x;
+    const int64_t kt0 = a.k0 + (int64_t)t * W;
+    const int64_t kend = min(kt0 + W, a.k0 + a.nk);   // exclusive
+    const int64_t kp = kt0 + (int64_t)threadIdx.x * PPT;
+    __shared__ float4 pr0[128];   // klo, khi, kc (int bits), s
+    __shared__ float4 pr1[128];   // u0, r, aj, ak
+    float sk[PPT], ck[PPT], sj[PPT], cj[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) { sk[i] = ck[i] = sj[i] = cj[i] = 0.0f; }
+    int64_t n_ev = 0, n_g = 0, n_c = 0, n_pairs = 0;
+    const CellPrep cp = a.cp[c];
+    const float hf = (float)a.h;
+    const int beg = a.tile_off[t], end = a.tile_off[t + 1];
+    for (int b = beg; b < end; b += 128) {
+        const int nb = min(128, end - b);
+        if ((int)threadIdx.x < nb) {
+            const int l = a.tile_lines[b + threadIdx.x];
+            const LinePrep L = a.lp[l];
+            int64_t klo = 1, khi = 0;
+            float s = 0.f, u0 = 0.f, r = 0.f, aj = 0.f, ak = 0.f;
+            const double lp = a.lnpref[c * a.S + L.species];
+            if (lp > -INFINITY) {
+                const double yj = L.lnAj + L.lngu + lp - (L.Eve_u * cp.bve + L.Er_u * cp.btr);
+                const float Sj = exp_reduced(yj);
+                const float x = L.dEve_f * cp.bve_f + L.dEr_f * cp.btr_f;
+                float Sk;
+                if (x >= 0.0f) {
+                    const double yk = L.lnAk + L.lngu + lp - (L.Eve_l * cp.bve + L.Er_l * cp.btr);
+                    Sk = exp_reduced(yk) * -expm1f(-x);
+                } else {
+                    Sk = exp_reduced(yj - L.lnAj + L.lnAk) * expm1f(x);
+                }
+                if (Sj > 0.0f || Sk != 0.0f) {
+                    const float lamG = L.cD_f * cp.sqrtT_f;
+                    const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0_f * cp.stc_f;
+                    const float sum = lamL + lamG;
+                    const float d = (lamL - lamG) / sum;
+                    const float F = 1.0f - 0.18121f * (1.0f - d * d) -
+                                    (0.023665f * expf(0.6f * d) + 0.00418f * expf(-1.9f * d)) * sinpif(d);
+                    const float lamV = F * sum;
+                    r = lamL / lamV;
+                    const float pre = 1e3f / (2.0f * lamV * (1.065f + 0.447f * r + 0.058f * r * r));
+                    s = 0.5f * hf / lamV;
+                    u0 = L.delta_f * s;
+                    aj = Sj * pre;
+                    ak = Sk * pre;
+                    const float wpts = (float)RAPRAL_WINDOW * lamV / hf;
+                    const float hi = L.delta_f + wpts, lo = L.delta_f - wpts;
+                    const float fhi = floorf(hi), clo = ceilf(lo);
+                    khi = (int64_t)L.kc + (int64_t)fhi;
+                    klo = (int64_t)L.kc + (int64_t)clo;
+                    const float m = 2e-6f * wpts + 2e-3f;
+                    if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m)
+                        exact_edges(L, cp, a.lam_min, a.h, &klo, &khi);
+                    klo = max(klo, kt0);
+                    khi = min(khi, kend - 1);
+                    if (klo <= khi) {
+                        // work counters: points in the window, and those with u below the
+                        // underflow limits of the two exponential terms
+                        n_ev += khi - klo + 1;
+                        const float kcen = (float)L.kc + L.delta_f;
+                        const float hg = 5.6125f / s, hc = 10.95f / s;   // u^2 < 31.5, u^2.25 < 218
+                        n_g += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hg)) - max(klo, (int64_t)ceilf(kcen - hg)) + 1);
+                        n_c += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hc)) - max(klo, (int64_t)ceilf(kcen - hc)) + 1);
+                        ++n_pairs;
+                    }
+                }
+            }
+            pr0[threadIdx.x] = make_float4(__int_as_float((int)klo), __int_as_float((int)khi),
+                                           __int_as_float(L.kc), s);
+            pr1[threadIdx.x] = make_float4(u0, r, aj, ak);
+        }
+        __syncthreads();
+        for (int q = 0; q < nb; ++q) {
+            const float4 A = pr0[q];
+            const int klo = __float_as_int(A.x), khi = __float_as_int(A.y);
+            if (khi < kp || klo > kp + PPT - 1) continue;
+            const float4 B = pr1[q];
+            const float s = A.w, u0 = B.x, r = B.y, aj = B.z, ak = B.w;
+            const float omr = 1.0f - r, c16 = 0.016f * r * omr;
+            const float kk0 = (float)(int)(kp - (int64_t)__float_as_int(A.z));
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                const int64_t k = kp + i;
+                if (k < klo || k > khi) continue;
+                const float u = fabsf(fmaf(kk0 + (float)i, s, -u0));
+                const float u2 = u * u;
+                const float g = u2 < 31.5f ? ex2_approx(-3.99915f * u2) : 0.0f;       // e^{-2.772 u^2}
+                const float v = u2 * rsqrt_approx(rsqrt_approx(u));                      // u^2.25
+                const float e2 = v < 218.0f ? ex2_approx(-0.5770780f * v) : 0.0f;      // e^{-0.4 v}
+                const float q4 = fmaf(4.0f, u2, 1.0f);
+                const float p1 = fmaf(0.1f, v, 1.0f);
+                const float rd = rcp_approx(q4 * p1);
+                const float br = fmaf(omr, g, fmaf(fmaf(r, p1, -c16 * q4), rd, c16 * e2));
+                float y = fmaf(aj, br, -cj[i]);
+                float tt = sj[i] + y;
+                cj[i] = (tt - sj[i]) - y;
+                sj[i] = tt;
+                y = fmaf(ak, br, -ck[i]);
+                tt = sk[i] + y;
+                ck[i] = (tt - sk[i]) - y;
+                sk[i] = tt;
+            }
+        }
+        __syncthreads();
+    }
+    block_count(a.stats, n_ev, n_g, n_c, n_pairs);
+    float* K = reinterpret_cast<float*>(a.kappa) + c * a.ld - a.k0;
+    float* J = reinterpret_cast<float*>(a.emis) + c * a.ld - a.k0;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int64_t k = kp + i;
+        if (k < kend) { K[k] = sk[i]; J[k] = sj[i]; }
     }
 }
 
@@ -357,11 +579,20 @@ cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n) {
     return cudaGetLastError();
 }
 
+static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, int precision, dim3 grid);
+
 cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles) {
     if (n_tiles == 0 || a.C == 0) return cudaSuccess;
     // cells along x (up to 2^31 - 1), tiles along y (<= 65535): consecutive
     // blocks share a tile's line list in L2
     dim3 grid((unsigned)a.C, (unsigned)n_tiles);
+    if (ctx->ev_before) cudaEventRecord(ctx->ev_before, ctx->stream);
+    cudaError_t e = launch_line_sum_grid(ctx, a, precision, grid);
+    if (ctx->ev_after) cudaEventRecord(ctx->ev_after, ctx->stream);
+    return e;
+}
+
+static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, int precision, dim3 grid) {
     if (precision == RAPRAL_FP64) {
         switch (a.tile_w) {
             case 128: k_line_sum_f64<1><<<grid, 128, 0, ctx->stream>>>(a); break;
@@ -371,5 +602,12 @@ cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision
         }
         return cudaGetLastError();
     }
-    return cudaErrorInvalidValue;
+    switch (a.tile_w) {
+        case 128: k_line_sum_f32<1><<<grid, 128, 0, ctx->stream>>>(a); break;
+        case 256: k_line_sum_f32<2><<<grid, 128, 0, ctx->stream>>>(a); break;
+        case 512: k_line_sum_f32<4><<<grid, 128, 0, ctx->stream>>>(a); break;
+        case 1024: k_line_sum_f32<8><<<grid, 128, 0, ctx->stream>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }

@@ -77,6 +77,10 @@ __global__ void k_cell_prep(const double* __restrict__ Ttr, const double* __rest
     p.btr = c2 / tt;
     p.sqrtT = sqrt(tt);
     p.stc = pow(tv / 10000.0, 0.33) * (n[c * ncol + ne_col] / 1e16);
+    p.bve_f = (float)p.bve;
+    p.btr_f = (float)p.btr;
+    p.sqrtT_f = (float)p.sqrtT;
+    p.stc_f = (float)p.stc;
     out[c] = p;
     // positive doubles order like their bit patterns
     atomicMax(&dmax[0], (unsigned long long)__double_as_longlong(p.sqrtT));

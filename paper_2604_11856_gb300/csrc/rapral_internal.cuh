@@ -43,29 +43,36 @@ enum {
 
 // ------------------------------------------------------------- records ----
 
-// Per-line constants, independent of the cell (FP64).
+// Per-line constants, independent of the cell.
 struct __align__(16) LinePrep {
     double lam0;     // nm
+    double tpos;     // (lam0 - lam_min) / h, grid units
     double lnAj;     // ln(1e-7 (hc/4pi) A / (lam0 1e-7))       ln S_j = lnAj + ln N_u
     double lnAk;     // ln(1e4 A (lam0 1e-7)^4 / (8 pi c))        S_k = e^{lnAk + ln N_u} expm1(x)
+    double lngu;     // ln g_u
     double Eve_u;    // E_el + E_V of the upper level (at T_ve)
     double Er_u;     // E_J of the upper level (at T_tr)
-    double lngu;     // ln g_u
-    double dEve;     // (E_el + E_V)_u - (E_el + E_V)_l
-    double dEr;      // E_J,u - E_J,l
+    double Eve_l;    // E_el + E_V of the lower level
+    double Er_l;     // E_J of the lower level
+    double dEve;     // Eve_u - Eve_l
+    double dEr;      // Er_u - Er_l
     double cD;       // Doppler: lamG = cD sqrt(T_tr)
     double lamS0;    // Stark HWHM at the reference state
-    double tpos;     // (lam0 - lam_min) / h, grid units
+    // FP32 copies for the chosen-precision path
+    float dEve_f, dEr_f, cD_f, lamS0_f;
+    float delta_f;   // tpos - kc
+    int32_t kc;      // nearest grid index to lam0 (may lie outside the grid)
     int32_t species;
     int32_t pad;
 };
 
-// Per-cell constants (FP64).
+// Per-cell constants.
 struct __align__(16) CellPrep {
     double bve;      // c2 / T_ve
     double btr;      // c2 / T_tr
     double sqrtT;    // sqrt(T_tr)
     double stc;      // (T_ve/1e4)^0.33 (N_e/1e16)
+    float bve_f, btr_f, sqrtT_f, stc_f;
 };
 
 // ---------------------------------------------------------------- context ----
@@ -82,6 +89,8 @@ struct rapral_ctx {
     // status word (device) and a pinned host mirror
     int* d_status = nullptr;
     int* h_pinned = nullptr;    // [16] pinned scratch for small read-backs
+    unsigned long long* d_stats = nullptr;   // [4] line-sum work counters
+    cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing events
     char err[512] = {0};
 };
 
@@ -160,6 +169,7 @@ struct LineSumArgs {
     void* kappa;
     void* emis;
     const int* status;
+    unsigned long long* stats;   // [4] evaluations, gauss, correction, pairs
 };
 cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles);
 

@@ -31,6 +31,11 @@ class RapralError(RuntimeError):
         self.code = code
 
 
+class Stats(ct.Structure):
+    _fields_ = [("evaluations", ct.c_int64), ("gauss_terms", ct.c_int64), ("correction_terms", ct.c_int64),
+                ("pairs", ct.c_int64)]
+
+
 class Species(ct.Structure):
     _fields_ = [("n_species", ct.c_int32), ("kind", ct.c_void_p), ("density_col", ct.c_void_p),
                 ("mass", ct.c_void_p), ("atom_off", ct.c_void_p), ("atom_E", ct.c_void_p),
@@ -92,6 +97,9 @@ def load(build_if_missing=True):
             "rapral_set_constants": (i, [vp, i]),
             "rapral_set_tiling": (i, [vp, i, i]),
             "rapral_workspace_bytes": (i, [i64, i64, i64, P(ct.c_size_t)]),
+            "rapral_get_stats": (i, [vp, P(Stats)]),
+            "rapral_reset_stats": (i, [vp]),
+            "rapral_set_profile_events": (i, [vp, vp, vp]),
             "rapral_populations": (i, [vp, P(Species), P(Cells), vp]),
             "rapral_spectral_coeffs": (i, [vp, P(Species), P(Lines), P(Cells), P(Grid), i64, i64, i, vp, vp, i64]),
             "rapral_trace_rays": (i, [vp, P(Rays), i64, vp, vp, i64, P(Grid), i64, i64, i, vp, vp]),
@@ -144,6 +152,21 @@ class Context:
 
     def set_tiling(self, tile_width=0, cells_per_block=0):
         self.check(self.lib.rapral_set_tiling(self.h, tile_width, cells_per_block))
+
+    def get_stats(self):
+        st = Stats()
+        self.check(self.lib.rapral_get_stats(self.h, ct.byref(st)))
+        return dict(evaluations=st.evaluations, gauss_terms=st.gauss_terms,
+                    correction_terms=st.correction_terms, pairs=st.pairs)
+
+    def reset_stats(self):
+        self.check(self.lib.rapral_reset_stats(self.h))
+
+    def set_profile_events(self, before=None, after=None):
+        """torch.cuda.Event pair recorded around every line-sum launch (None: off)."""
+        b = ct.c_void_p(before.cuda_event) if before is not None else None
+        a = ct.c_void_p(after.cuda_event) if after is not None else None
+        self.check(self.lib.rapral_set_profile_events(self.h, b, a))
 
     def set_constants(self, codata):
         self.check(self.lib.rapral_set_constants(self.h, int(codata)))

@@ -562,7 +562,7 @@ def afterbody(seed=1002, nx=400, nr=200, x_len=200.0, r_body=33.5, r_len=150.0,
 
 
 def subset_lines(lines: Lines, idx):
-    idx = np.sort(np.asarray(idx))
+    idx = np.sort(np.asarray(idx, dtype=np.int64))
     return Lines(**{k: np.ascontiguousarray(getattr(lines, k)[idx]) for k in Lines.__dataclass_fields__})
 
 
