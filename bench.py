@@ -269,7 +269,10 @@ def main():
                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
            "secondary": {"ray_lambda_segments_per_s": world * seg_lambda / (ms_per_step * 1e-3),
                          "profile_evaluations_per_s": world * evals_per_step / (ms_per_step * 1e-3),
-                         "line_sum_ms": k3_mean, "wall_s": t_wall},
+                         "line_sum_ms": k3_mean, "wall_s": t_wall,
+                         "pairs_per_step": stats["pairs"] / args.steps,
+                         "gauss_terms_per_step": stats["gauss_terms"] / args.steps,
+                         "correction_terms_per_step": stats["correction_terms"] / args.steps},
            "roofline": roof, "clocks": clk.summary(), "gpu_launches": None}
     # launches per step: validate x2, line prep, cell prep, bounds, count, scan, fill, line sum,
     # populations + its validation, march + its validation, flux, slab rays are built once

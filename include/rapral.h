@@ -181,9 +181,10 @@ RAPRAL_API int rapral_clear_status(rapral_ctx* ctx);
  * 1 = CODATA 2018. */
 RAPRAL_API int rapral_set_constants(rapral_ctx* ctx, int codata);
 
-/* Spectral tile width (grid points per line-sum tile: 128, 256, 512 or
- * 1024; FP64 up to 512) and cells per line-sum block (1, 2 or 4).  0 keeps
- * the current value.  Used by the autotuner. */
+/* Spectral tile width (grid points per line-sum tile: 128, 256 or 512;
+ * default 512 for FP64 and 128 for FP32) and cells per FP32 line-sum
+ * block (2, 4 or 8; default 4).  0 keeps the current value; a tile width of -1 restores the
+ * default.  Used by the autotuner. */
 RAPRAL_API int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block);
 
 /* Work counters of the line sum, accumulated over rapral_spectral_coeffs
@@ -275,16 +276,67 @@ RAPRAL_API int rapral_wall_flux(rapral_ctx* ctx, const void* q_lambda, int preci
                      const rapral_grid* grid, int64_t k0, int64_t nk, int64_t n_points,
                      double* q);
 
+/* ------------------------------------------------------------------ batch -- */
+
+/* One request of a batch: a whole solve over the grid points [k0, k0+nk)
+ * (the steps of rapral_spectral_coeffs, rapral_trace_rays and
+ * rapral_wall_flux).  Host pointers to the descriptors; the arrays inside
+ * are device arrays.  cells->lnpref must hold rapral_populations' output
+ * when the batch runs.  kappa / emis [C][ld] and q_lambda [P][nk] are FP32
+ * scratch of the request; q [P] FP64 accumulates. */
+typedef struct {
+    const rapral_species* species;
+    const rapral_lines* lines;
+    const rapral_cells* cells;
+    const rapral_grid* grid;
+    const rapral_rays* rays;
+    int64_t k0, nk;
+    void* kappa;
+    void* emis;
+    int64_t ld;
+    void* q_lambda;
+    double* q;
+} rapral_batch_item;
+
+typedef struct rapral_batch rapral_batch;
+
+/* Plans a batch of independent, uneven requests (the batching the paper's
+ * per-LOS loop suggests; Sec. 2.2.3 runs one LBL + RTE per line of sight):
+ * checks every request, builds its line records and spectral-tile line lists
+ * with the context's tiling, and lays their work units end to end.  Copies
+ * the descriptors (not the arrays).  Allocates the batch's own device memory
+ * and synchronises the stream.  The plan stays valid while the arrays keep
+ * their addresses and the cells' temperatures and electron densities do not
+ * rise above the planned values (window bounds).  FP32 only.  Errors:
+ * EINVAL (a request, with its index in the message; failed device checks),
+ * ENOMEM, ECUDA. */
+RAPRAL_API int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* items, int precision,
+                                   rapral_batch** out);
+
+/* Enqueues the batch: one persistent line-sum launch over every request's
+ * (tile, cell group) units, pulled from an atomic counter, then each
+ * request's march and flux.  No allocation, no host synchronisation: the
+ * call can be captured in a CUDA graph on the context's stream. */
+RAPRAL_API int rapral_batch_run(rapral_ctx* ctx, rapral_batch* batch);
+
+/* Work units and persistent grid size of a planned batch (host only). */
+RAPRAL_API int rapral_batch_units(const rapral_batch* batch, int64_t* units, int* blocks);
+
+RAPRAL_API void rapral_batch_destroy(rapral_batch* batch);
+
 /* ------------------------------------------------------------ ray builders -- */
 
-/* Tangent slab (plane-parallel layers): one bundle through `n_layers` cells
- * cell_order[0] (far boundary) .. cell_order[m-1] (wall), thickness dx[i];
- * directions mu[m] with weight 2 pi wmu[m] mu[m] and path scale 1/mu[m];
- * with `normal_ray` a first direction mu = 1 of weight 0 (intensity output
- * only).  Inputs are device arrays; outputs are caller-owned device arrays
- * sized: point_off[2], seg_off[2], seg_cell[m], seg_ds[m], dir_off[2],
- * dir_scale/dir_weight[n_mu + normal_ray], bundle_wall[1].  Fills `rays`
- * (host struct) with those pointers and sizes. */
+/* Tangent slab (plane-parallel layers, Sec. 2.2.3 with the slab reading of
+ * the solid-angle integral): `n_layers` cells cell_order[0] (far boundary)
+ * .. cell_order[m-1] (wall), thickness dx[i]; directions mu[m] with weight
+ * 2 pi wmu[m] mu[m] and path scale 1/mu[m]; with `normal_ray` a first
+ * direction mu = 1 of weight 0 (intensity output only).  The nd = n_mu +
+ * normal_ray directions (1 .. 4096) are split into nb = ceil(nd / 17)
+ * bundles that each repeat the cell path.  Inputs are device arrays;
+ * outputs are caller-owned device arrays sized point_off[2], seg_off[nb+1],
+ * seg_cell / seg_ds[n_layers * nb], dir_off[nb+1], dir_scale /
+ * dir_weight[nd], bundle_wall[nb].  Fills `rays` (host struct) with those
+ * pointers and sizes. */
 RAPRAL_API int rapral_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx,
                      int32_t n_layers, const double* mu, const double* wmu, int32_t n_mu,
                      int32_t normal_ray, int32_t wall_start, double T_wall,

@@ -1,0 +1,218 @@
+// Batched solves: many independent, uneven requests planned once and run
+// with one persistent line-sum launch (rapral_batch_*).
+//
+// rapral_batch_create validates every request, builds its per-line and
+// per-cell records and its spectral-tile line lists (one synchronisation for
+// all tile-list lengths) in memory the batch owns, and lays the requests'
+// work units end to end.  rapral_batch_run then only enqueues kernels -- the
+// persistent line sum over all units, and each request's march and flux --
+// with no allocation and no host synchronisation, so it can be captured in a
+// CUDA graph and replayed.
+#include <new>
+#include <vector>
+
+#include "rapral_internal.cuh"
+
+struct BatchReq {
+    rapral_species sp;
+    rapral_lines ln;
+    rapral_cells cells;
+    rapral_grid grid;
+    rapral_rays rays;
+    int64_t k0, nk, ld;
+    void *kappa, *emis, *q_lambda;
+    double* q;
+    double h;
+};
+
+struct rapral_batch {
+    int n = 0;
+    int tile_w = 128, wpb = 4;
+    std::vector<BatchReq> req;
+    char* ws = nullptr;           // records, tile ranges, offsets of every request
+    int* csr = nullptr;           // tile lists of every request
+    BatchItem* d_items = nullptr;
+    unsigned long long* d_counter = nullptr;
+    int64_t total_units = 0;
+    int blocks = 0;
+};
+
+static int check_item(rapral_ctx* ctx, const rapral_batch_item& it, int i) {
+    if (!it.species || !it.lines || !it.cells || !it.grid || !it.rays || !it.kappa || !it.emis || !it.q_lambda || !it.q)
+        return set_error(ctx, RAPRAL_EINVAL, "request %d: null argument", i);
+    const rapral_grid* g = it.grid;
+    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || it.k0 < 0 || it.nk < 1 ||
+        it.k0 + it.nk > g->n || it.ld < it.nk)
+        return set_error(ctx, RAPRAL_EINVAL, "request %d: grid, range or ld", i);
+    if (it.lines->n_lines < 1 || it.lines->n_lines > 2147483647LL || it.cells->n_cells < 1 || !it.cells->lnpref ||
+        it.cells->n_cols < 1 || it.cells->ne_col < 0 || it.cells->ne_col >= it.cells->n_cols ||
+        it.species->n_species < 1 || it.species->n_species > RAPRAL_MAX_SPECIES)
+        return set_error(ctx, RAPRAL_EINVAL, "request %d: lines, cells or species", i);
+    if (it.rays->n_points < 1 || it.rays->max_dirs < 1 || it.rays->max_dirs > RAPRAL_MAX_DIRS ||
+        (it.nk + 31) / 32 > 65535)
+        return set_error(ctx, RAPRAL_EINVAL, "request %d: rays", i);
+    return RAPRAL_OK;
+}
+
+extern "C" {
+
+int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* items, int precision,
+                        rapral_batch** out) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!out || !items || n_items < 1) return set_error(ctx, RAPRAL_EINVAL, "batch: no requests");
+    if (precision != RAPRAL_FP32) return set_error(ctx, RAPRAL_EINVAL, "batch: only RAPRAL_FP32 is batched");
+    *out = nullptr;
+    for (int i = 0; i < n_items; ++i) {
+        int st = check_item(ctx, items[i], i);
+        if (st) return st;
+    }
+    cudaSetDevice(ctx->device);
+    rapral_batch* B = new (std::nothrow) rapral_batch();
+    if (!B) return RAPRAL_ENOMEM;
+    B->n = n_items;
+    B->tile_w = ctx->tile_w ? ctx->tile_w : 128;
+    B->wpb = B->tile_w == 512 ? 4 : ctx->cells_per_block;
+    const int W = B->tile_w;
+    B->req.resize(n_items);
+    // phase 1 sizes
+    std::vector<size_t> base(n_items);
+    size_t need = 0;
+    for (int i = 0; i < n_items; ++i) {
+        BatchReq& r = B->req[i];
+        r.sp = *items[i].species; r.ln = *items[i].lines; r.cells = *items[i].cells; r.grid = *items[i].grid;
+        r.rays = *items[i].rays;
+        r.k0 = items[i].k0; r.nk = items[i].nk; r.ld = items[i].ld;
+        r.kappa = items[i].kappa; r.emis = items[i].emis; r.q_lambda = items[i].q_lambda; r.q = items[i].q;
+        r.h = (r.grid.lam_max - r.grid.lam_min) / (double)(r.grid.n - 1);
+        const int64_t L = r.ln.n_lines, C = r.cells.n_cells, T = (r.nk + W - 1) / W;
+        if (T > 65535) { delete B; return set_error(ctx, RAPRAL_EINVAL, "request %d: too many tiles", i); }
+        base[i] = need;
+        need = arena_need(need, L * sizeof(LinePrep));
+        need = arena_need(need, C * sizeof(CellPrep));
+        need = arena_need(need, L * sizeof(int2));
+        need = arena_need(need, (T + 1) * sizeof(int));
+        need = arena_need(need, 4 * sizeof(unsigned long long));
+        need = arena_need(need, 4 * sizeof(int));
+        need = arena_need(need, 0);
+    }
+    cudaError_t e = cudaMalloc(&B->ws, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete B;
+        return set_error(ctx, RAPRAL_ENOMEM, "batch records of %zu bytes", need);
+    }
+    std::vector<BinPlan> plans(n_items);
+    std::vector<LinePrep*> lps(n_items);
+    std::vector<CellPrep*> cps(n_items);
+    const Phys ph = make_phys(ctx->codata);
+    static const int one = 1;
+    int* h_tot = nullptr;
+    e = cudaMallocHost(&h_tot, sizeof(int) * n_items);
+    for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+        BatchReq& r = B->req[i];
+        const int64_t L = r.ln.n_lines, C = r.cells.n_cells, T = (r.nk + W - 1) / W;
+        Arena ar{B->ws, need, base[i]};
+        lps[i] = ar.take<LinePrep>(L);
+        cps[i] = ar.take<CellPrep>(C);
+        BinPlan& pl = plans[i];
+        pl.k0 = r.k0; pl.nk = r.nk; pl.tile_w = W; pl.n_tiles = T;
+        pl.line_tiles = ar.take<int2>(L);
+        pl.tile_off = ar.take<int>(T + 1);
+        unsigned long long* dmax = ar.take<unsigned long long>(4);
+        pl.wmax = dmax + 2;
+        pl.sorted_flag = ar.take<int>(4);
+        e = cudaMemcpyAsync(pl.sorted_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(pl.wmax, 0, sizeof(unsigned long long), ctx->stream);
+        if (e == cudaSuccess) e = launch_validate_cells(ctx, &r.cells);
+        if (e == cudaSuccess) e = launch_validate_lines(ctx, &r.ln, r.sp.n_species);
+        if (e == cudaSuccess) e = launch_validate_rays(ctx, &r.rays, C);
+        if (e == cudaSuccess) e = launch_line_prep(ctx, &r.sp, &r.ln, r.grid.lam_min, r.h, ph, lps[i], pl.sorted_flag);
+        if (e == cudaSuccess) e = launch_cell_prep(ctx, &r.cells, ph, cps[i], dmax);
+        if (e == cudaSuccess) e = launch_bin_bounds(ctx, &r.ln, lps[i], cps[i], dmax, r.h, &pl);
+        if (e == cudaSuccess) e = launch_bin_count(ctx, &r.ln, &r.grid, r.h, &pl);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_tot + i, pl.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    size_t csr_need = 0;
+    std::vector<size_t> csr_base(n_items);
+    for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+        csr_base[i] = csr_need;
+        csr_need += (size_t)h_tot[i] + 1;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&B->csr, csr_need * sizeof(int));
+    std::vector<BatchItem> hitems(n_items);
+    int64_t units = 0;
+    for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+        BatchReq& r = B->req[i];
+        plans[i].tile_lines = B->csr + csr_base[i];
+        e = launch_bin_fill(ctx, &r.ln, &r.grid, r.h, &plans[i]);
+        LineSumArgs& a = hitems[i].a;
+        a.lp = lps[i]; a.cp = cps[i]; a.lnpref = r.cells.lnpref; a.S = r.sp.n_species; a.C = r.cells.n_cells;
+        a.tile_off = plans[i].tile_off; a.tile_lines = plans[i].tile_lines;
+        a.lam_min = r.grid.lam_min; a.h = r.h; a.k0 = r.k0; a.nk = r.nk; a.ld = r.ld; a.tile_w = W;
+        a.kappa = r.kappa; a.emis = r.emis; a.status = ctx->d_status; a.stats = ctx->d_stats;
+        hitems[i].unit_off = units;
+        hitems[i].n_groups = (r.cells.n_cells + B->wpb - 1) / B->wpb;
+        units += plans[i].n_tiles * hitems[i].n_groups;
+    }
+    B->total_units = units;
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(BatchItem) * n_items);
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_items, hitems.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess) e = launch_line_sum_batch(ctx, W, B->wpb, nullptr, 0, 0, nullptr, &B->blocks, false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (h_tot) cudaFreeHost(h_tot);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rapral_batch_destroy(B);
+        return cuda_status(ctx, e, "batch planning");
+    }
+    int st = rapral_sync(ctx);
+    if (st) {
+        rapral_batch_destroy(B);
+        return st;
+    }
+    *out = B;
+    return RAPRAL_OK;
+}
+
+int rapral_batch_run(rapral_ctx* ctx, rapral_batch* B) {
+    if (!ctx || !B) return RAPRAL_EINVAL;
+    cudaSetDevice(ctx->device);
+    const Phys ph = make_phys(ctx->codata);
+    cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), ctx->stream);
+    if (ctx->ev_before && e == cudaSuccess) e = cudaEventRecord(ctx->ev_before, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_line_sum_batch(ctx, B->tile_w, B->wpb, B->d_items, B->n, B->total_units, B->d_counter, nullptr,
+                                  true);
+    if (ctx->ev_after && e == cudaSuccess) e = cudaEventRecord(ctx->ev_after, ctx->stream);
+    for (int i = 0; i < B->n && e == cudaSuccess; ++i) {
+        const BatchReq& r = B->req[i];
+        e = launch_march(ctx, &r.rays, r.kappa, r.emis, r.ld, &r.grid, r.h, r.k0, r.nk, RAPRAL_FP32, r.q_lambda,
+                         nullptr, ph);
+        if (e == cudaSuccess)
+            e = launch_wall_flux(ctx, r.q_lambda, RAPRAL_FP32, &r.grid, r.h, r.k0, r.nk, r.rays.n_points, r.q);
+    }
+    return cuda_status(ctx, e, "batch run");
+}
+
+void rapral_batch_destroy(rapral_batch* B) {
+    if (!B) return;
+    if (B->ws) cudaFree(B->ws);
+    if (B->csr) cudaFree(B->csr);
+    if (B->d_items) cudaFree(B->d_items);
+    if (B->d_counter) cudaFree(B->d_counter);
+    delete B;
+}
+
+int rapral_batch_units(const rapral_batch* B, int64_t* units, int* blocks) {
+    if (!B) return RAPRAL_EINVAL;
+    if (units) *units = B->total_units;
+    if (blocks) *blocks = B->blocks;
+    return RAPRAL_OK;
+}
+
+}  // extern "C"

@@ -163,14 +163,16 @@ int rapral_set_constants(rapral_ctx* ctx, int codata) {
 
 int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block) {
     if (!ctx) return RAPRAL_EINVAL;
-    if (tile_width != 0) {
-        if (tile_width != 128 && tile_width != 256 && tile_width != 512 && tile_width != 1024)
-            return set_error(ctx, RAPRAL_EINVAL, "tile width %d not one of 128, 256, 512, 1024", tile_width);
+    if (tile_width == -1) {
+        ctx->tile_w = 0;   // back to the per-precision default
+    } else if (tile_width != 0) {
+        if (tile_width != 128 && tile_width != 256 && tile_width != 512)
+            return set_error(ctx, RAPRAL_EINVAL, "tile width %d not one of 128, 256, 512", tile_width);
         ctx->tile_w = tile_width;
     }
     if (cells_per_block != 0) {
-        if (cells_per_block != 1 && cells_per_block != 2 && cells_per_block != 4)
-            return set_error(ctx, RAPRAL_EINVAL, "cells per block %d not 1, 2 or 4", cells_per_block);
+        if (cells_per_block != 2 && cells_per_block != 4 && cells_per_block != 8)
+            return set_error(ctx, RAPRAL_EINVAL, "cells per block %d not 2, 4 or 8", cells_per_block);
         ctx->cells_per_block = cells_per_block;
     }
     return RAPRAL_OK;
@@ -246,10 +248,9 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
         if (e == cudaSuccess) e = cudaMemset2DAsync(emis, ld * esz, 0, nk * esz, C, ctx->stream);
         return cuda_status(ctx, e, "zero coefficients");
     }
-    const int W = ctx->tile_w;
-    if ((precision == RAPRAL_FP64 && W > 512) || W > 1024)
-        return set_error(ctx, RAPRAL_EINVAL, "line sum supports tile widths 128..%d in this precision (got %d)",
-                         precision == RAPRAL_FP64 ? 512 : 1024, W);
+    const int W = ctx->tile_w ? ctx->tile_w : (precision == RAPRAL_FP64 ? 512 : 128);
+    if (W != 128 && W != 256 && W != 512)
+        return set_error(ctx, RAPRAL_EINVAL, "line sum supports tile widths 128, 256, 512 (got %d)", W);
     const int64_t T = (nk + W - 1) / W;
     if (T > 65535) return set_error(ctx, RAPRAL_EINVAL, "range of %lld points needs more than 65535 tiles", (long long)nk);
     const double h = grid_h(g);
@@ -327,7 +328,8 @@ int rapral_trace_rays(rapral_ctx* ctx, const rapral_rays* rays, int64_t n_cells,
         return set_error(ctx, RAPRAL_EINVAL, "ray set sizes");
     if (rays->max_dirs < 0 || rays->max_dirs > RAPRAL_MAX_DIRS)
         return set_error(ctx, RAPRAL_EINVAL, "max_dirs %d not in 0..%d", rays->max_dirs, RAPRAL_MAX_DIRS);
-    if (rays->n_points > 65535) return set_error(ctx, RAPRAL_EINVAL, "more than 65535 surface points");
+    if (rays->n_points > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "too many surface points");
+    if ((nk + 31) / 32 > 65535) return set_error(ctx, RAPRAL_EINVAL, "range of %lld points too long for one march call", (long long)nk);
     if (rays->n_points == 0) return RAPRAL_OK;
     if (!rays->point_off || !rays->seg_off || !rays->dir_off || !rays->dir_scale || !rays->dir_weight ||
         !rays->bundle_wall || (rays->n_segments > 0 && (!rays->seg_cell || !rays->seg_ds)))
@@ -363,15 +365,16 @@ int rapral_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* d
     if (n_layers < 0 || (n_layers > 0 && (!cell_order || !dx || !seg_cell || !seg_ds)))
         return set_error(ctx, RAPRAL_EINVAL, "layers");
     const int nd = n_mu + (normal_ray ? 1 : 0);
-    if (n_mu < 0 || nd < 1 || nd > RAPRAL_MAX_DIRS || (n_mu > 0 && (!mu || !wmu)))
-        return set_error(ctx, RAPRAL_EINVAL, "direction count %d not in 1..%d", nd, RAPRAL_MAX_DIRS);
+    if (n_mu < 0 || nd < 1 || nd > 4096 || (n_mu > 0 && (!mu || !wmu)))
+        return set_error(ctx, RAPRAL_EINVAL, "direction count %d not in 1..4096", nd);
+    const int nb = (nd + RAPRAL_SLAB_DIRS - 1) / RAPRAL_SLAB_DIRS;
     if (wall_start && !(T_wall > 0.0)) return set_error(ctx, RAPRAL_EINVAL, "T_wall must be positive for a wall start");
     cudaSetDevice(ctx->device);
     cudaError_t e = launch_slab_rays(ctx, cell_order, dx, n_layers, mu, wmu, n_mu, normal_ray, wall_start, point_off,
                                      seg_off, seg_cell, seg_ds, dir_off, dir_scale, dir_weight, bundle_wall);
     if (e != cudaSuccess) return cuda_status(ctx, e, "slab rays");
-    rays->n_bundles = 1; rays->n_points = 1; rays->n_segments = n_layers; rays->n_dirs = nd;
-    rays->max_dirs = nd; rays->max_bundles_per_point = 1;
+    rays->n_bundles = nb; rays->n_points = 1; rays->n_segments = (int64_t)n_layers * nb; rays->n_dirs = nd;
+    rays->max_dirs = nd < RAPRAL_SLAB_DIRS ? nd : RAPRAL_SLAB_DIRS; rays->max_bundles_per_point = nb;
     rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
     rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
     rays->bundle_wall = bundle_wall; rays->T_wall = T_wall;

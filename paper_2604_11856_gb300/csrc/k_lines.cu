@@ -54,6 +54,8 @@ __global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, do
     p.lnAj = log(1e-7 * (ph.h * ph.c / (4.0 * M_PI)) * A / lcm);
     p.lnAk = log(1e4 * A * (lcm * lcm) * (lcm * lcm) / (8.0 * M_PI * ph.c));
     p.lngu = log(ln.gu[l]);
+    p.lnAjg = p.lnAj + p.lngu;
+    p.lnAkg = p.lnAk + p.lngu;
     p.Eve_u = ln.Eu_el[l] + ln.Eu_v[l];
     p.Er_u = ln.Eu_j[l];
     p.Eve_l = ln.El_el[l] + ln.El_v[l];
@@ -230,7 +232,7 @@ __device__ void block_count(unsigned long long* stats, int64_t ev, int64_t g, in
         c += __shfl_xor_sync(0xffffffffu, c, o);
         p += __shfl_xor_sync(0xffffffffu, p, o);
     }
-    if ((threadIdx.x & 31) == 0 && p > 0) {
+    if ((threadIdx.x & 31) == 0 && p > 0) {   // one atomic set per warp
         atomicAdd(&stats[0], (unsigned long long)ev);
         atomicAdd(&stats[1], (unsigned long long)g);
         atomicAdd(&stats[2], (unsigned long long)c);
@@ -388,7 +390,7 @@ __device__ __forceinline__ bool in_window64(int64_t k, double lam_min, double h,
 
 // Exact edges near the FP32 estimates (the estimate is within a fraction of a
 // grid point of the truth).
-__device__ void exact_edges(const LinePrep& L, const CellPrep& cp, double lam_min, double h, int64_t* klo,
+__device__ __noinline__ void exact_edges(const LinePrep& L, const CellPrep& cp, double lam_min, double h, int64_t* klo,
                             int64_t* khi) {
     const double lamG = L.cD * cp.sqrtT;
     const double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
@@ -402,125 +404,235 @@ __device__ void exact_edges(const LinePrep& L, const CellPrep& cp, double lam_mi
     *khi = hi;
 }
 
+// One (line, cell) pair set up for the tile: window [klo, khi] (grid
+// indices, certified), profile constants and strengths.  Returns false when
+// the pair adds nothing to the tile.
+struct PairF32 {
+    int klo, khi, kc;
+    float s, u0, r, aj, ak;
+};
+
+__device__ __forceinline__ bool setup_pair_f32(const LinePrep& L, const CellPrep& cp, double lp, double lam_min,
+                                               double h, float hf, int kt0, int kt1, PairF32* P, int64_t* cnt) {
+    if (!(lp > -INFINITY)) return false;
+    const double base = lp - (L.Eve_u * cp.bve + L.Er_u * cp.btr);   // ln N_u - ln g_u
+    const double yj = L.lnAjg + base;
+    const float Sj = exp_reduced(yj);
+    const float x = L.dEve_f * cp.bve_f + L.dEr_f * cp.btr_f;
+    float Sk;
+    if (x >= 0.0f) {
+        const double yk = L.lnAkg + lp - (L.Eve_l * cp.bve + L.Er_l * cp.btr);
+        Sk = exp_reduced(yk) * -expm1f(-x);
+    } else {
+        Sk = exp_reduced(yj - L.lnAj + L.lnAk) * expm1f(x);
+    }
+    if (!(Sj > 0.0f) && Sk == 0.0f) return false;
+    const float lamG = L.cD_f * cp.sqrtT_f;
+    const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0_f * cp.stc_f;
+    const float sum = lamL + lamG;
+    const float d = (lamL - lamG) / sum;
+    const float F = 1.0f - 0.18121f * (1.0f - d * d) -
+                    (0.023665f * expf(0.6f * d) + 0.00418f * expf(-1.9f * d)) * sinpif(d);
+    const float lamV = F * sum;
+    const float wpts = (float)RAPRAL_WINDOW * lamV / hf;
+    const float hi = L.delta_f + wpts, lo = L.delta_f - wpts;
+    const float fhi = floorf(hi), clo = ceilf(lo);
+    int64_t khi = (int64_t)L.kc + (int64_t)fhi;
+    int64_t klo = (int64_t)L.kc + (int64_t)clo;
+    const float m = 2e-6f * wpts + 2e-3f;
+    if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m)
+        exact_edges(L, cp, lam_min, h, &klo, &khi);
+    klo = max(klo, (int64_t)kt0);
+    khi = min(khi, (int64_t)kt1);
+    if (klo > khi) return false;
+    const float r = lamL / lamV;
+    const float pre = 1e3f / (2.0f * lamV * (1.065f + 0.447f * r + 0.058f * r * r));
+    P->klo = (int)klo; P->khi = (int)khi; P->kc = L.kc;
+    P->s = 0.5f * hf / lamV;
+    P->u0 = L.delta_f * P->s;
+    P->r = r;
+    P->aj = Sj * pre;
+    P->ak = Sk * pre;
+    // work counters: points in the window; those where the Gaussian core and
+    // the exponential correction are above the FP32 underflow limits
+    cnt[0] += khi - klo + 1;
+    const float kcen = (float)L.kc + L.delta_f;
+    const float hg = 5.6125f / P->s, hc = 10.95f / P->s;   // u^2 < 31.5, u^2.25 < 218
+    cnt[1] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hg)) - max(klo, (int64_t)ceilf(kcen - hg)) + 1);
+    cnt[2] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hc)) - max(klo, (int64_t)ceilf(kcen - hc)) + 1);
+    cnt[3] += 1;
+    return true;
+}
+
+// One Whiting evaluation, bracket only (the factor 1e3 / (2 lamV (1.065 +
+// 0.447 r + 0.058 r^2)) is folded into aj, ak).  Near the line centre both
+// exponentials are kept; `far` drops them where they are zero in FP32
+// (u^2 >= 31.5 and u^2.25 >= 218 over the whole span being evaluated).
+template <bool FAR>
+__device__ __forceinline__ float whiting_bracket(float u, float r, float omr, float c16) {
+    const float u2 = u * u;
+    const float v = u2 * rsqrt_approx(rsqrt_approx(u));                      // u^2.25
+    const float q4 = fmaf(4.0f, u2, 1.0f);
+    const float p1 = fmaf(0.1f, v, 1.0f);
+    const float rd = rcp_approx(q4 * p1);
+    const float num = fmaf(r, p1, -c16 * q4);                                // r(1+0.1v) - c16(1+4u^2)
+    if (FAR) return num * rd;
+    const float g = u2 < 31.5f ? ex2_approx(-3.99915f * u2) : 0.0f;       // e^{-2.772 u^2}
+    const float e2 = v < 218.0f ? ex2_approx(-0.5770780f * v) : 0.0f;      // e^{-0.4 v}
+    return fmaf(omr, g, fmaf(num, rd, c16 * e2));
+}
+
+// Kahan step: (s, c) += x.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Warp-level line sum: a warp owns one cell and the TW = 32 PPT points of
+// tile t (PPT consecutive points per lane); it stages 32 (line, cell) pairs
+// at a time in its own shared-memory slice (one per lane), then sweeps them
+// over its points.  Warps never wait for each other.
 template <int PPT>
-__global__ void __launch_bounds__(128) k_line_sum_f32(LineSumArgs a) {
-    if (*a.status) return;
-    constexpr int W = 128 * PPT;
-    const int t = blockIdx.y;
-    const int64_t c = blockIdx.x;
-    const int64_t kt0 = a.k0 + (int64_t)t * W;
-    const int64_t kend = min(kt0 + W, a.k0 + a.nk);   // exclusive
-    const int64_t kp = kt0 + (int64_t)threadIdx.x * PPT;
-    __shared__ float4 pr0[128];   // klo, khi, kc (int bits), s
-    __shared__ float4 pr1[128];   // u0, r, aj, ak
-    float sk[PPT], ck[PPT], sj[PPT], cj[PPT];
+__device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
+                                              int lane, int64_t* cnt) {
+    constexpr int TW = 32 * PPT;
+    const int kt0 = (int)(a.k0 + (int64_t)t * TW);
+    const int kt1 = (int)min(a.k0 + (int64_t)(t + 1) * TW, a.k0 + a.nk) - 1;   // inclusive
+    const int kp = kt0 + lane * PPT;
+    // compensated sums (Kahan) of the per-batch partial sums; inside a batch
+    // of at most 32 lines the terms are added plainly (error <= 31 u of the
+    // batch's magnitude, u = 2^-24)
+    float sk[PPT], ck[PPT], sj[PPT], cj[PPT], bk[PPT], bj[PPT];
 #pragma unroll
-    for (int i = 0; i < PPT; ++i) { sk[i] = ck[i] = sj[i] = cj[i] = 0.0f; }
-    int64_t n_ev = 0, n_g = 0, n_c = 0, n_pairs = 0;
+    for (int i = 0; i < PPT; ++i) { sk[i] = ck[i] = sj[i] = cj[i] = bk[i] = bj[i] = 0.0f; }
     const CellPrep cp = a.cp[c];
     const float hf = (float)a.h;
+    const double* lnp = a.lnpref + c * a.S;
     const int beg = a.tile_off[t], end = a.tile_off[t + 1];
-    for (int b = beg; b < end; b += 128) {
-        const int nb = min(128, end - b);
-        if ((int)threadIdx.x < nb) {
-            const int l = a.tile_lines[b + threadIdx.x];
+    for (int b = beg; b < end; b += 32) {
+        const int nb = min(32, end - b);
+        if (lane < nb) {
+            const int l = a.tile_lines[b + lane];
             const LinePrep L = a.lp[l];
-            int64_t klo = 1, khi = 0;
-            float s = 0.f, u0 = 0.f, r = 0.f, aj = 0.f, ak = 0.f;
-            const double lp = a.lnpref[c * a.S + L.species];
-            if (lp > -INFINITY) {
-                const double yj = L.lnAj + L.lngu + lp - (L.Eve_u * cp.bve + L.Er_u * cp.btr);
-                const float Sj = exp_reduced(yj);
-                const float x = L.dEve_f * cp.bve_f + L.dEr_f * cp.btr_f;
-                float Sk;
-                if (x >= 0.0f) {
-                    const double yk = L.lnAk + L.lngu + lp - (L.Eve_l * cp.bve + L.Er_l * cp.btr);
-                    Sk = exp_reduced(yk) * -expm1f(-x);
-                } else {
-                    Sk = exp_reduced(yj - L.lnAj + L.lnAk) * expm1f(x);
-                }
-                if (Sj > 0.0f || Sk != 0.0f) {
-                    const float lamG = L.cD_f * cp.sqrtT_f;
-                    const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0_f * cp.stc_f;
-                    const float sum = lamL + lamG;
-                    const float d = (lamL - lamG) / sum;
-                    const float F = 1.0f - 0.18121f * (1.0f - d * d) -
-                                    (0.023665f * expf(0.6f * d) + 0.00418f * expf(-1.9f * d)) * sinpif(d);
-                    const float lamV = F * sum;
-                    r = lamL / lamV;
-                    const float pre = 1e3f / (2.0f * lamV * (1.065f + 0.447f * r + 0.058f * r * r));
-                    s = 0.5f * hf / lamV;
-                    u0 = L.delta_f * s;
-                    aj = Sj * pre;
-                    ak = Sk * pre;
-                    const float wpts = (float)RAPRAL_WINDOW * lamV / hf;
-                    const float hi = L.delta_f + wpts, lo = L.delta_f - wpts;
-                    const float fhi = floorf(hi), clo = ceilf(lo);
-                    khi = (int64_t)L.kc + (int64_t)fhi;
-                    klo = (int64_t)L.kc + (int64_t)clo;
-                    const float m = 2e-6f * wpts + 2e-3f;
-                    if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m)
-                        exact_edges(L, cp, a.lam_min, a.h, &klo, &khi);
-                    klo = max(klo, kt0);
-                    khi = min(khi, kend - 1);
-                    if (klo <= khi) {
-                        // work counters: points in the window, and those with u below the
-                        // underflow limits of the two exponential terms
-                        n_ev += khi - klo + 1;
-                        const float kcen = (float)L.kc + L.delta_f;
-                        const float hg = 5.6125f / s, hc = 10.95f / s;   // u^2 < 31.5, u^2.25 < 218
-                        n_g += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hg)) - max(klo, (int64_t)ceilf(kcen - hg)) + 1);
-                        n_c += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hc)) - max(klo, (int64_t)ceilf(kcen - hc)) + 1);
-                        ++n_pairs;
-                    }
-                }
+            PairF32 P;
+            if (setup_pair_f32(L, cp, lnp[L.species], a.lam_min, a.h, hf, kt0, kt1, &P, cnt)) {
+                sm0[lane] = make_float4(__int_as_float(P.klo), __int_as_float(P.khi), __int_as_float(P.kc), P.s);
+                sm1[lane] = make_float4(P.u0, P.r, P.aj, P.ak);
+            } else {
+                sm0[lane] = make_float4(__int_as_float(1), __int_as_float(0), 0.0f, 0.0f);
             }
-            pr0[threadIdx.x] = make_float4(__int_as_float((int)klo), __int_as_float((int)khi),
-                                           __int_as_float(L.kc), s);
-            pr1[threadIdx.x] = make_float4(u0, r, aj, ak);
         }
-        __syncthreads();
+        __syncwarp();
         for (int q = 0; q < nb; ++q) {
-            const float4 A = pr0[q];
+            const float4 A = sm0[q];
             const int klo = __float_as_int(A.x), khi = __float_as_int(A.y);
-            if (khi < kp || klo > kp + PPT - 1) continue;
-            const float4 B = pr1[q];
+            if (khi < kt0) continue;   // nothing of this pair in the tile (uniform over the warp)
+            const int i0 = max(klo - kp, 0);
+            const int i1 = min(khi - kp, PPT - 1);
+            const float4 B = sm1[q];
             const float s = A.w, u0 = B.x, r = B.y, aj = B.z, ak = B.w;
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
-            const float kk0 = (float)(int)(kp - (int64_t)__float_as_int(A.z));
+            const int kc = __float_as_int(A.z);
+            // distance (in u) from the line centre to the nearest evaluated point
+            // of the whole warp: decides, uniformly, whether the exponentials can
+            // be dropped
+            const float cen = u0 / s;                    // centre offset from kc, grid units
+            const float dlo = (float)(max(klo, kt0) - kc) - cen, dhi = (float)(min(khi, kt1) - kc) - cen;
+            const float umin = (dlo > 0.0f ? dlo : (dhi < 0.0f ? -dhi : 0.0f)) * s;
+            const float x0 = fmaf((float)(kp - kc), s, -u0);   // signed u of the lane's first point
+            if (i0 > i1) continue;
+            if (umin > 11.0f) {
+                if (i0 == 0 && i1 == PPT - 1) {
 #pragma unroll
-            for (int i = 0; i < PPT; ++i) {
-                const int64_t k = kp + i;
-                if (k < klo || k > khi) continue;
-                const float u = fabsf(fmaf(kk0 + (float)i, s, -u0));
-                const float u2 = u * u;
-                const float g = u2 < 31.5f ? ex2_approx(-3.99915f * u2) : 0.0f;       // e^{-2.772 u^2}
-                const float v = u2 * rsqrt_approx(rsqrt_approx(u));                      // u^2.25
-                const float e2 = v < 218.0f ? ex2_approx(-0.5770780f * v) : 0.0f;      // e^{-0.4 v}
-                const float q4 = fmaf(4.0f, u2, 1.0f);
-                const float p1 = fmaf(0.1f, v, 1.0f);
-                const float rd = rcp_approx(q4 * p1);
-                const float br = fmaf(omr, g, fmaf(fmaf(r, p1, -c16 * q4), rd, c16 * e2));
-                float y = fmaf(aj, br, -cj[i]);
-                float tt = sj[i] + y;
-                cj[i] = (tt - sj[i]) - y;
-                sj[i] = tt;
-                y = fmaf(ak, br, -ck[i]);
-                tt = sk[i] + y;
-                ck[i] = (tt - sk[i]) - y;
-                sk[i] = tt;
+                    for (int i = 0; i < PPT; ++i) {
+                        const float br = whiting_bracket<true>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
+                        bj[i] = fmaf(aj, br, bj[i]);
+                        bk[i] = fmaf(ak, br, bk[i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < PPT; ++i)
+                        if (i >= i0 && i <= i1) {
+                            const float br = whiting_bracket<true>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
+                            bj[i] = fmaf(aj, br, bj[i]);
+                            bk[i] = fmaf(ak, br, bk[i]);
+                        }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < PPT; ++i)
+                    if (i >= i0 && i <= i1) {
+                        const float br = whiting_bracket<false>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
+                        bj[i] = fmaf(aj, br, bj[i]);
+                        bk[i] = fmaf(ak, br, bk[i]);
+                    }
             }
         }
-        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            kahan_add(sj[i], cj[i], bj[i]);
+            kahan_add(sk[i], ck[i], bk[i]);
+            bj[i] = bk[i] = 0.0f;
+        }
+        __syncwarp();
     }
-    block_count(a.stats, n_ev, n_g, n_c, n_pairs);
     float* K = reinterpret_cast<float*>(a.kappa) + c * a.ld - a.k0;
     float* J = reinterpret_cast<float*>(a.emis) + c * a.ld - a.k0;
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
-        const int64_t k = kp + i;
-        if (k < kend) { K[k] = sk[i]; J[k] = sj[i]; }
+        const int k = kp + i;
+        if (k <= kt1) { K[k] = sk[i]; J[k] = sj[i]; }
     }
+}
+
+template <int PPT, int WPB>
+__global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_f32(LineSumArgs a) {
+    if (*a.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * WPB + warp;
+    if (c >= a.C) return;
+    __shared__ float4 sm0[WPB][32];   // klo, khi, kc (int bits), s
+    __shared__ float4 sm1[WPB][32];   // u0, r, aj, ak
+    int64_t cnt[4] = {0, 0, 0, 0};
+    warp_tile_f32<PPT>(a, blockIdx.y, c, sm0[warp], sm1[warp], lane, cnt);
+    block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
+}
+
+// Persistent line sum over many independent requests: blocks pull work
+// units (request, tile, group of WPB cells) from one atomic counter until the
+// list is exhausted; units of a request are ordered tile by tile so blocks
+// working at the same time share a tile's line list in L2.
+template <int PPT, int WPB>
+__global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_batch(const BatchItem* __restrict__ items,
+                                                                       int n_items, int64_t total,
+                                                                       unsigned long long* counter,
+                                                                       unsigned long long* stats, const int* status) {
+    if (*status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ float4 sm0[WPB][32];
+    __shared__ float4 sm1[WPB][32];
+    __shared__ long long unit_s;
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (;;) {
+        if (threadIdx.x == 0) unit_s = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const int64_t u = unit_s;
+        __syncthreads();
+        if (u >= total) break;
+        int lo = 0, hi = n_items;     // last item whose first unit is <= u
+        while (hi - lo > 1) {
+            const int m = (lo + hi) >> 1;
+            if (items[m].unit_off <= u) lo = m; else hi = m;
+        }
+        const BatchItem& it = items[lo];
+        const int64_t local = u - it.unit_off;
+        const int t = (int)(local / it.n_groups);
+        const int64_t c = (local - (int64_t)t * it.n_groups) * WPB + warp;
+        if (c < it.a.C) warp_tile_f32<PPT>(it.a, t, c, sm0[warp], sm1[warp], lane, cnt);
+    }
+    block_count(stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
 }  // namespace
@@ -602,12 +714,46 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
         }
         return cudaGetLastError();
     }
-    switch (a.tile_w) {
-        case 128: k_line_sum_f32<1><<<grid, 128, 0, ctx->stream>>>(a); break;
-        case 256: k_line_sum_f32<2><<<grid, 128, 0, ctx->stream>>>(a); break;
-        case 512: k_line_sum_f32<4><<<grid, 128, 0, ctx->stream>>>(a); break;
-        case 1024: k_line_sum_f32<8><<<grid, 128, 0, ctx->stream>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+    // FP32: warp-level kernel, WPB cells per block
+    const int wpb = a.tile_w == 512 ? 4 : ctx->cells_per_block;
+    dim3 g32(div_up(a.C, wpb), grid.y);
+#define RAPRAL_LS32(PPT, WPB) k_line_sum_f32<PPT, WPB><<<g32, 32 * WPB, 0, ctx->stream>>>(a)
+    if (a.tile_w == 128 && wpb == 2) RAPRAL_LS32(4, 2);
+    else if (a.tile_w == 128 && wpb == 4) RAPRAL_LS32(4, 4);
+    else if (a.tile_w == 128 && wpb == 8) RAPRAL_LS32(4, 8);
+    else if (a.tile_w == 256 && wpb == 2) RAPRAL_LS32(8, 2);
+    else if (a.tile_w == 256 && wpb == 4) RAPRAL_LS32(8, 4);
+    else if (a.tile_w == 256 && wpb == 8) RAPRAL_LS32(8, 8);
+    else if (a.tile_w == 512) RAPRAL_LS32(16, 4);
+    else return cudaErrorInvalidValue;
+#undef RAPRAL_LS32
     return cudaGetLastError();
+}
+
+template <int PPT, int WPB>
+static cudaError_t batch_launch(rapral_ctx* ctx, const BatchItem* items, int n, int64_t total,
+                                unsigned long long* counter, int* blocks_out, bool launch) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_batch<PPT, WPB>, 32 * WPB, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = max(1, per_sm) * sms;
+    if (blocks_out) *blocks_out = blocks;
+    if (!launch) return cudaSuccess;
+    k_line_sum_batch<PPT, WPB><<<blocks, 32 * WPB, 0, ctx->stream>>>(items, n, total, counter, ctx->d_stats,
+                                                                     ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const BatchItem* items, int n, int64_t total,
+                                  unsigned long long* counter, int* blocks_out, bool launch) {
+    if (tile_w == 128 && wpb == 2) return batch_launch<4, 2>(ctx, items, n, total, counter, blocks_out, launch);
+    if (tile_w == 128 && wpb == 4) return batch_launch<4, 4>(ctx, items, n, total, counter, blocks_out, launch);
+    if (tile_w == 128 && wpb == 8) return batch_launch<4, 8>(ctx, items, n, total, counter, blocks_out, launch);
+    if (tile_w == 256 && wpb == 2) return batch_launch<8, 2>(ctx, items, n, total, counter, blocks_out, launch);
+    if (tile_w == 256 && wpb == 4) return batch_launch<8, 4>(ctx, items, n, total, counter, blocks_out, launch);
+    if (tile_w == 256 && wpb == 8) return batch_launch<8, 8>(ctx, items, n, total, counter, blocks_out, launch);
+    if (tile_w == 512) return batch_launch<16, 4>(ctx, items, n, total, counter, blocks_out, launch);
+    return cudaErrorInvalidValue;
 }

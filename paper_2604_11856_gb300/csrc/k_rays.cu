@@ -2,7 +2,7 @@
 // march with the angular reduction, and the spectral flux integral
 // (Sec. 2.2.3).
 //
-// k_march: one block per (surface point, wavelength tile).  Threads are
+// k_march: one block per (surface point, wavelength tile), points along x.  Threads are
 // (wavelength lane, bundle slice): lanes run over consecutive grid points so
 // every kappa / j gather of a segment is a coalesced row read; slices take the
 // point's bundles round-robin.  Per bundle the kernel walks the segments from
@@ -74,8 +74,8 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
     constexpr int LW = 256 / SL;        // wavelength lanes per block
     const int lane = threadIdx.x % LW;
     const int slice = threadIdx.x / LW;
-    const int64_t p = blockIdx.y;
-    const int64_t kk = (int64_t)blockIdx.x * LW + lane;     // column within the range
+    const int64_t p = blockIdx.x;                           // points vary fastest: concurrent blocks share
+    const int64_t kk = (int64_t)blockIdx.y * LW + lane;     // a wavelength tile, whose kappa / j stay in L2
     const bool active = kk < a.nk;
     const int64_t kcol = active ? kk : a.nk - 1;
     const T* Kt = reinterpret_cast<const T*>(a.kappa) + kcol;
@@ -184,24 +184,31 @@ __global__ void __launch_bounds__(256) k_wall_flux(const T* __restrict__ qlam, i
     if (threadIdx.x == 0) q[p] += red[0];
 }
 
+// Tangent slab: directions are split into bundles of at most SLAB_DIRS
+// (the normal ray first); every bundle repeats the cell path.
 __global__ void k_slab_rays(const int32_t* cell_order, const double* dx, int32_t m, const double* mu,
                             const double* wmu, int32_t n_mu, int32_t normal_ray, int32_t wall_start,
                             int64_t* point_off, int64_t* seg_off, int32_t* seg_cell, double* seg_ds,
                             int64_t* dir_off, double* dir_scale, double* dir_weight, int32_t* bundle_wall) {
     const int nd = n_mu + (normal_ray ? 1 : 0);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) { seg_cell[i] = cell_order[i]; seg_ds[i] = dx[i]; }
+    const int nb = (nd + RAPRAL_SLAB_DIRS - 1) / RAPRAL_SLAB_DIRS;
+    for (int64_t i = threadIdx.x; i < (int64_t)m * nb; i += blockDim.x) {
+        const int64_t j = i % m;
+        seg_cell[i] = cell_order[j];
+        seg_ds[i] = dx[j];
+    }
     for (int d = threadIdx.x; d < nd; d += blockDim.x) {
         if (normal_ray && d == 0) { dir_scale[0] = 1.0; dir_weight[0] = 0.0; continue; }
         const int mm = d - (normal_ray ? 1 : 0);
         dir_scale[d] = 1.0 / mu[mm];
         dir_weight[d] = 2.0 * M_PI * wmu[mm] * mu[mm];
     }
-    if (threadIdx.x == 0) {
-        point_off[0] = 0; point_off[1] = 1;
-        seg_off[0] = 0; seg_off[1] = m;
-        dir_off[0] = 0; dir_off[1] = nd;
-        bundle_wall[0] = wall_start;
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) {
+        seg_off[b] = (int64_t)b * m;
+        dir_off[b] = min(b * RAPRAL_SLAB_DIRS, nd);
+        if (b < nb) bundle_wall[b] = wall_start;
     }
+    if (threadIdx.x == 0) { point_off[0] = 0; point_off[1] = nb; }
 }
 
 // Ray from the surface point (x0, rb): position x = x0 + t dx, radius
@@ -292,10 +299,10 @@ __global__ void k_axisym_fill(const double* xf, int32_t nx, const double* rf, in
 template <class T, int MAXD>
 cudaError_t march_sl(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxb) {
     if (maxb >= 8) {
-        dim3 g(div_up(nk, 32), (unsigned)P);
+        dim3 g((unsigned)P, div_up(nk, 32));
         k_march<T, MAXD, 8><<<g, 256, 0, ctx->stream>>>(a);
     } else {
-        dim3 g(div_up(nk, 256), (unsigned)P);
+        dim3 g((unsigned)P, div_up(nk, 256));
         k_march<T, MAXD, 1><<<g, 256, 0, ctx->stream>>>(a);
     }
     return cudaGetLastError();

@@ -33,6 +33,7 @@ inline Phys make_phys(int codata) {
 #define RAPRAL_WINDOW 100.0              // lines reach |dlam| <= 100 lamV
 #define RAPRAL_THIN_F64 4e-4             // |dtau| below which the series is used
 #define RAPRAL_THIN_F32 5e-2
+#define RAPRAL_SLAB_DIRS 17              // directions per tangent-slab bundle
 
 // Status word layout (device int[8]).
 enum { ST_CODE = 0, ST_CHECK = 1, ST_INDEX = 2 };
@@ -58,6 +59,8 @@ struct __align__(16) LinePrep {
     double dEr;      // Er_u - Er_l
     double cD;       // Doppler: lamG = cD sqrt(T_tr)
     double lamS0;    // Stark HWHM at the reference state
+    double lnAjg;    // lnAj + ln g_u
+    double lnAkg;    // lnAk + ln g_u
     // FP32 copies for the chosen-precision path
     float dEve_f, dEr_f, cD_f, lamS0_f;
     float delta_f;   // tpos - kc
@@ -81,8 +84,8 @@ struct rapral_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int codata = 0;
-    int tile_w = 512;          // grid points per line-sum tile
-    int cells_per_block = 1;
+    int tile_w = 0;            // grid points per line-sum tile (0: 512 for FP64, 128 for FP32)
+    int cells_per_block = 4;   // warps (cells) per FP32 line-sum block
     // workspace arena (grown on demand; all users are stream-ordered)
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -172,6 +175,18 @@ struct LineSumArgs {
     unsigned long long* stats;   // [4] evaluations, gauss, correction, pairs
 };
 cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles);
+
+// One request of a batched (persistent) line sum: its arguments and the
+// first of its work units (tile-major, groups of WPB cells).
+struct BatchItem {
+    LineSumArgs a;
+    int64_t unit_off;
+    int64_t n_groups;   // cell groups per tile
+};
+// Launches the persistent FP32 line sum over all units (or only reports the
+// grid size when `launch` is false).
+cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const BatchItem* items, int n, int64_t total,
+                                  unsigned long long* counter, int* blocks_out, bool launch);
 
 // Rays
 cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells);

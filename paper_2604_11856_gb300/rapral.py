@@ -19,6 +19,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECANCELED = range(6)
 FP64, FP32 = 0, 1
 MAX_DIRS = 65
+SLAB_DIRS = 17   # directions per tangent-slab bundle
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ECANCELED: "ECANCELED"}
 
 _lib = None
@@ -69,6 +70,12 @@ class Rays(ct.Structure):
                 ("dir_weight", ct.c_void_p), ("bundle_wall", ct.c_void_p), ("T_wall", ct.c_double)]
 
 
+class BatchItem(ct.Structure):
+    _fields_ = [("species", ct.c_void_p), ("lines", ct.c_void_p), ("cells", ct.c_void_p), ("grid", ct.c_void_p),
+                ("rays", ct.c_void_p), ("k0", ct.c_int64), ("nk", ct.c_int64), ("kappa", ct.c_void_p),
+                ("emis", ct.c_void_p), ("ld", ct.c_int64), ("q_lambda", ct.c_void_p), ("q", ct.c_void_p)]
+
+
 def lib_path():
     return _build.LIB
 
@@ -101,6 +108,10 @@ def load(build_if_missing=True):
             "rapral_reset_stats": (i, [vp]),
             "rapral_set_profile_events": (i, [vp, vp, vp]),
             "rapral_populations": (i, [vp, P(Species), P(Cells), vp]),
+            "rapral_batch_create": (i, [vp, i, P(BatchItem), i, P(vp)]),
+            "rapral_batch_run": (i, [vp, vp]),
+            "rapral_batch_units": (i, [vp, P(i64), P(i)]),
+            "rapral_batch_destroy": (None, [vp]),
             "rapral_spectral_coeffs": (i, [vp, P(Species), P(Lines), P(Cells), P(Grid), i64, i64, i, vp, vp, i64]),
             "rapral_trace_rays": (i, [vp, P(Rays), i64, vp, vp, i64, P(Grid), i64, i64, i, vp, vp]),
             "rapral_wall_flux": (i, [vp, vp, i, P(Grid), i64, i64, i64, vp]),
@@ -318,6 +329,7 @@ def slab_rays(ctx, geo, device):
     m = int(len(geo.cell_order))
     n_mu = int(len(geo.mu))
     nd = n_mu + (1 if geo.normal_ray else 0)
+    nb = (nd + SLAB_DIRS - 1) // SLAB_DIRS
     i32, i64, f8 = torch.int32, torch.int64, torch.float64
     t = r.t
     t["cell_order"] = _t(geo.cell_order, np.int32, device)
@@ -325,13 +337,13 @@ def slab_rays(ctx, geo, device):
     t["mu"] = _t(geo.mu, np.float64, device)
     t["wmu"] = _t(geo.wmu, np.float64, device)
     t["point_off"] = torch.empty(2, dtype=i64, device=device)
-    t["seg_off"] = torch.empty(2, dtype=i64, device=device)
-    t["seg_cell"] = torch.empty(max(m, 1), dtype=i32, device=device)
-    t["seg_ds"] = torch.empty(max(m, 1), dtype=f8, device=device)
-    t["dir_off"] = torch.empty(2, dtype=i64, device=device)
+    t["seg_off"] = torch.empty(nb + 1, dtype=i64, device=device)
+    t["seg_cell"] = torch.empty(max(m * nb, 1), dtype=i32, device=device)
+    t["seg_ds"] = torch.empty(max(m * nb, 1), dtype=f8, device=device)
+    t["dir_off"] = torch.empty(nb + 1, dtype=i64, device=device)
     t["dir_scale"] = torch.empty(nd, dtype=f8, device=device)
     t["dir_weight"] = torch.empty(nd, dtype=f8, device=device)
-    t["bundle_wall"] = torch.empty(1, dtype=i32, device=device)
+    t["bundle_wall"] = torch.empty(nb, dtype=i32, device=device)
     ctx.check(ctx.lib.rapral_slab_rays(ctx.h, _ptr(t["cell_order"]), _ptr(t["dx"]), m, _ptr(t["mu"]),
                                        _ptr(t["wmu"]), n_mu, int(bool(geo.normal_ray)), int(bool(geo.wall_start)),
                                        float(geo.T_wall), _ptr(t["point_off"]), _ptr(t["seg_off"]),

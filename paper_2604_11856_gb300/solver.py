@@ -41,15 +41,28 @@ def _dtype(precision):
     return torch.float64 if precision == R.FP64 else torch.float32
 
 
+def shard_range(n, rank, world, align=512):
+    """Contiguous part [k0, k0 + nk) of an n-point grid for `rank` of
+    `world`, boundaries on multiples of `align` (a tile width)."""
+    blocks = (n + align - 1) // align
+    b0 = blocks * rank // world
+    b1 = blocks * (rank + 1) // world
+    k0 = min(n, b0 * align)
+    k1 = min(n, b1 * align)
+    return k0, k1 - k0
+
+
 def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensity=False, ctx2=None,
-          buffers=None):
-    """Runs the whole path on device-resident inputs.  Returns a dict with
-    q [P] (FP64, device) and, on request, kappa / emis [C, n] and
-    q_lambda [P, n] / I [n_dirs, n] for the whole grid (single chunk only).
-    With ctx2 (a second context on another stream) chunk k+1's line sum
-    overlaps chunk k's march."""
-    n = dp.grid.n
-    chunk = n if not chunk else min(chunk, n)
+          buffers=None, k_start=0, k_stop=None):
+    """Runs the whole path on device-resident inputs over the grid points
+    [k_start, k_stop) (default: all).  Returns a dict with q [P] (FP64,
+    device; the range's part of the flux with the whole grid's trapezoid
+    weights) and, on request, kappa / emis [C, nk] and q_lambda [P, nk] /
+    I [n_dirs, nk] (single chunk only).  With ctx2 (a second context on
+    another stream) chunk k+1's line sum overlaps chunk k's march."""
+    k_stop = dp.grid.n if k_stop is None else k_stop
+    n_range = k_stop - k_start
+    chunk = n_range if not chunk else min(chunk, n_range)
     dev = ctx.device
     dt = _dtype(precision)
     C, P = dp.C, dp.P
@@ -64,10 +77,10 @@ def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensi
     I = None
     if keep_intensity:
         I = torch.empty((dp.rays.n_dirs, chunk), dtype=dt, device=dev)
-    starts = list(range(0, n, chunk))
+    starts = list(range(k_start, k_stop, chunk))
     if ctx2 is None:
         for k0 in starts:
-            nk = min(chunk, n - k0)
+            nk = min(chunk, k_stop - k0)
             kap, em = buffers[0]
             R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
             R.trace_rays(ctx, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)
@@ -82,7 +95,7 @@ def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensi
         ev_pop.record(sa)
         sb.wait_event(ev_pop)
         for i, k0 in enumerate(starts):
-            nk = min(chunk, n - k0)
+            nk = min(chunk, k_stop - k0)
             kap, em = buffers[i % nbuf]
             if used[i % nbuf]:
                 sa.wait_event(free[i % nbuf])
@@ -104,6 +117,21 @@ def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensi
         if keep_intensity:
             out["I"] = I
     return out
+
+
+def solve_sharded(dp, ctx, rank, world, precision=R.FP32, chunk=None, group=None):
+    """Spectral sharding across ranks: each rank solves its contiguous part of
+    the grid (populations are replicated, no data exchange), then one sum of
+    the P partial fluxes (FP64) over the process group finishes the job."""
+    import torch.distributed as dist
+    k0, nk = shard_range(dp.grid.n, rank, world)
+    if nk > 0:
+        q = solve(dp, ctx, precision, chunk=chunk, k_start=k0, k_stop=k0 + nk)["q"]
+    else:
+        q = torch.zeros(dp.P, dtype=torch.float64, device=ctx.device)
+    if world > 1:
+        dist.all_reduce(q, op=dist.ReduceOp.SUM, group=group)
+    return q
 
 
 def solve_host(problem, precision=R.FP64, chunk=None, ctx=None, device=None):

@@ -1,0 +1,52 @@
+"""Batched persistent solves: many uneven slab solves in one persistent
+line-sum launch per spectral round, eager and replayed from a CUDA graph;
+every solve equals the same solve run alone (same chunking) and the
+oracle within the FP32 tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_11856_gb300 import batch, rapral as R, solver, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def problems():
+    pool = synth._air_lines(np.random.default_rng(1001), 2000, 20000)
+    probs = synth.batch_slabs(n_solves=6, pool=pool, scale=0.01)
+    probs += synth.batch_slabs(seed=77, n_solves=3, pool=pool, scale=0.01, iid_cells=True)
+    return probs
+
+
+def test_batch_equals_solo_and_graph_replays(problems):
+    ctx = R.Context(0)
+    chunk = 3000
+    bs = batch.BatchSolver(problems, ctx, chunk=chunk)
+    assert len(bs.handles) >= 2   # several spectral rounds
+    q_eager = [q.cpu().numpy().copy() for q in bs.run()]
+    ctx.sync()
+    bs.capture()
+    q_g1 = [q.cpu().numpy().copy() for q in bs.replay()]
+    q_g2 = [q.cpu().numpy().copy() for q in bs.replay()]
+    torch.cuda.synchronize()
+    ctx.sync()
+    for i, p in enumerate(problems):
+        dp = solver.DeviceProblem(p, ctx)
+        solo = solver.solve(dp, ctx, R.FP32, chunk=chunk)["q"].cpu().numpy()
+        ctx.sync()
+        np.testing.assert_allclose(q_eager[i], solo, rtol=1e-12, atol=0)
+        assert np.array_equal(q_g1[i], q_eager[i]) and np.array_equal(q_g2[i], q_eager[i])
+    bs.close()
+
+
+def test_batch_matches_oracle(problems):
+    ctx = R.Context(0)
+    p = problems[0]
+    bs = batch.BatchSolver([p], ctx, chunk=2500)
+    q = bs.run()[0].cpu().numpy()
+    ctx.sync()
+    ref = oracle.solve_slab(p)["q"]
+    assert abs(q[0] / ref - 1) <= 1e-4, (q, ref)
+    bs.close()
