@@ -324,6 +324,31 @@ RAPRAL_API int rapral_batch_units(const rapral_batch* batch, int64_t* units, int
 
 RAPRAL_API void rapral_batch_destroy(rapral_batch* batch);
 
+/* rapral_spectral_coeffs without any device allocation.  (No counterpart in
+ * the paper: it exists for callers that cannot allocate.)  Code that runs
+ * while a CUDA graph is being captured on its stream, real-time loops that
+ * must stay off the allocator, and programs whose device memory belongs to
+ * an outer framework's pool cannot call cudaMalloc; this entry point needs
+ * neither a context nor a workspace.  Its scratch is one static device array
+ * of 64 MiB inside the library, held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array and clears what must start at zero;
+ * calls that overlap on the GPU (other streams, unordered host threads) race
+ * on it, so serialise them.  The call synchronises `cuda_stream` once (to
+ * read the input checks and the tile-list length) and then enqueues the line
+ * sum; outputs are valid once the stream synchronises.  Default tile
+ * widths (512 FP64, 128 FP32), paper constants.  Arguments as rapral_spectral_coeffs, plus an optional
+ * caller buffer `err` (err_len bytes) for a message.  Errors: EINVAL (sizes,
+ * ranges, failed device-side input checks), ENOMEM (the problem needs more
+ * than the 64 MiB scratch: about 160 bytes per line plus 48 per cell and the
+ * tile lists), ECUDA. */
+RAPRAL_API int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_species* sp,
+                                              const rapral_lines* lines, const rapral_cells* cells,
+                                              const rapral_grid* grid, int64_t k0, int64_t nk,
+                                              int precision, void* kappa, void* emis, int64_t ld,
+                                              char* err, size_t err_len);
+
 /* ------------------------------------------------------------ ray builders -- */
 
 /* Tangent slab (plane-parallel layers, Sec. 2.2.3 with the slab reading of
