@@ -43,6 +43,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-requests measurement")
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-fp64-requests", type=int, default=4)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
+    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch"], default="stagnation",
+                    help="stagnation line (the bench line); afterbody / batch: one-off measurements")
     ap.add_argument("--cells", type=int, default=200,
                     help="cells of the stagnation line (fewer only for profiler captures)")
     return ap.parse_args()
@@ -133,6 +140,32 @@ def cpu_baseline(problem, seconds, precision_note="f64"):
                       f"{len(p.lines)} lines, kappa and j in FP64 ({dt2:.1f} s)"}
 
 
+def served(p, args, device):
+    """Open-loop served requests (line-of-sight and slab solves, config-4
+    sizes) sharing the resident stagnation-line lists; FP32-chosen vs FP64
+    plain on the same requests (FP64 on the first few only: it is ~80x
+    slower)."""
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import serve, synth
+    pool = (p.lines, p.species, {})
+    gen = synth.served_requests(seed=1004, n_requests=args.serve_requests, rate=args.serve_rate, pool=pool)
+    res = {"offered_rate_req_s": args.serve_rate, "slots": 4, "budget_bytes": 150 << 30}
+    q32 = {}
+    for prec, n, name in ((R.FP32, args.serve_requests, "fp32"), (R.FP64, args.serve_fp64_requests, "fp64")):
+        if n <= 0:
+            continue
+        reqs = [serve.Request(rid=i, problem=g["problem"], arrival=g["t"], precision=prec)
+                for i, g in enumerate(gen[:n])]
+        srv = serve.Server(p.lines, p.species, device=device, slots=4)
+        res[name] = serve.run_open_loop(srv, reqs)
+        if prec == R.FP32:
+            q32 = {r.rid: r.q for r in reqs if r.status == "done"}
+        else:
+            errs = [float(np.max(np.abs(q32[r.rid] / r.q - 1))) for r in reqs if r.status == "done" and r.rid in q32]
+            res["q_rel_err_fp32_vs_fp64_max"] = max(errs) if errs else None
+    return res
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, bounded samples of the
     bench workload per step."""
@@ -160,10 +193,83 @@ def run_reference(args):
     return 0
 
 
+def run_afterbody(args):
+    """The axisymmetric afterbody (80,000 cells, 1e6 points in 65,536-point
+    chunks, 102,400 rays): one FP32 solve with the two-stream chunk pipeline."""
+    import torch
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver, synth
+    p = synth.afterbody()
+    ctx = R.Context(0)
+    ctx2 = R.Context(0, stream=torch.cuda.Stream())
+    dp = solver.DeviceProblem(p, ctx)
+    ctx.sync()
+    bufs = [(torch.empty((dp.C, p.chunk), dtype=torch.float32, device=ctx.device),
+             torch.empty((dp.C, p.chunk), dtype=torch.float32, device=ctx.device)) for _ in range(2)]
+    ms = []
+    with ClockSampler(0) as clk:
+        for i in range(max(1, args.steps)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            out = solver.solve(dp, ctx, R.FP32, chunk=p.chunk, ctx2=ctx2, buffers=bufs)
+            b.record(ctx.stream)
+            ctx.sync(); ctx2.sync()
+            ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms)) * 1e-3
+    nseg = dp.rays.struct.n_segments
+    print(json.dumps({"workload": "afterbody 400x200 cells, 320k lines, 1e6 points in 65,536-point chunks, "
+                                  "200 points x 512 rays", "ms_per_solve": t * 1e3,
+                      "cell_lambda_per_s": dp.C * p.grid.n / t, "ray_lambda_segments_per_s": nseg * p.grid.n / t,
+                      "segments": int(nseg), "q_mean_W_cm2": float(out["q"].mean().item()), "clocks": clk.summary()}))
+    return 0
+
+
+def run_batch(args):
+    """64 uneven uniform-slab solves (FP32): one persistent line-sum launch per
+    spectral round, the whole run captured in one CUDA graph, against the
+    same solves run one after another."""
+    import torch
+    from paper_2604_11856_gb300 import autotune, batch, rapral as R, solver, synth
+    probs = synth.batch_slabs()
+    ctx = R.Context(0)
+    tw, wpb, times = autotune.tune(ctx, max(probs, key=lambda q: len(q.lines)))
+    bs = batch.BatchSolver(probs, ctx, chunk=65536)
+    bs.run(); ctx.sync()
+    bs.capture()
+    bs.replay(); torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(1, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(); bs.replay(); b.record(); torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms)) * 1e-3
+    cl = sum(len(q.cells) * q.grid.n for q in probs)
+    # the same solves one after another through the regular entry points
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dps = [solver.DeviceProblem(q, ctx) for q in probs]
+    ctx.sync()
+    a.record(ctx.stream)
+    for dp in dps:
+        solver.solve(dp, ctx, R.FP32, chunk=65536)
+    b.record(ctx.stream)
+    ctx.sync()
+    t_seq = a.elapsed_time(b) * 1e-3
+    print(json.dumps({"workload": "64 uneven slab solves (cells 20-2000, 1e5-2e6 points, 1e3-5e4 atomic + "
+                                  "0-3e5 molecular lines)", "tiling": [tw, wpb], "graph_ms": t * 1e3,
+                      "cell_lambda_per_s": cl / t, "sequential_ms": t_seq * 1e3,
+                      "sequential_cell_lambda_per_s": cl / t_seq, "rounds": len(bs.handles),
+                      "units": bs.units()[:3]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "afterbody":
+        return run_afterbody(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import torch
     import torch.distributed as dist
 
@@ -181,8 +287,13 @@ def main():
 
     p = synth.stagnation_line(n_cells=args.cells)
     ctx = R.Context(local)
+    tuned = None
     if args.tile:
         ctx.set_tiling(tile_width=args.tile)
+    elif precision == R.FP32 and not args.no_tune:
+        from paper_2604_11856_gb300 import autotune
+        tw, wpb, times = autotune.tune(ctx, p)
+        tuned = {"tile_width": tw, "cells_per_block": wpb, "candidates_ms": times}
     dp = solver.DeviceProblem(p, ctx)
     C, K = dp.C, p.grid.n
     n_dirs = dp.rays.n_dirs
@@ -207,8 +318,14 @@ def main():
 
     for _ in range(args.warmup):
         step()
-    ctx.sync()
+    # one untimed step with the work counters on (evaluations, XU terms), then
+    # the timed steps without them
+    ctx.set_counters(True)
     ctx.reset_stats()
+    step()
+    stats = ctx.get_stats()
+    ctx.set_counters(False)
+    ctx.sync()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     k3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -227,7 +344,6 @@ def main():
     ctx.sync()
     step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
     k3_ms = [k3[i][0].elapsed_time(k3[i][1]) for i in range(args.steps)]
-    stats = ctx.get_stats()
     total_ms = float(np.sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -235,7 +351,7 @@ def main():
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * C * K / (ms_per_step * 1e-3)
-    evals_per_step = stats["evaluations"] / args.steps
+    evals_per_step = stats["evaluations"]
     k3_mean = float(np.mean(k3_ms))
 
     # roofline of the line sum: transcendental (XU / MUFU) work the FP32
@@ -245,7 +361,7 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     if precision == R.FP32:
-        xu_ops = (3 * stats["evaluations"] + stats["gauss_terms"] + stats["correction_terms"]) / args.steps
+        xu_ops = 3 * stats["evaluations"] + stats["gauss_terms"] + stats["correction_terms"]
         peak = n_sm * 16 * sm_max / 1e9               # Gop/s: 16 XU lanes per SM per clock
         achieved = xu_ops / (k3_mean * 1e-3) / 1e9
         roof = {"bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)", "achieved": achieved, "peak": peak,
@@ -266,13 +382,14 @@ def main():
            "vs_baseline": None, "dtype": "f32" if precision == R.FP32 else "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": args.precision + ("-chosen" if precision == R.FP32 else "-plain"),
                       "cells": C, "lines": len(p.lines), "grid_points": K, "directions": n_dirs,
-                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
+                      "tiling": tuned},
            "secondary": {"ray_lambda_segments_per_s": world * seg_lambda / (ms_per_step * 1e-3),
                          "profile_evaluations_per_s": world * evals_per_step / (ms_per_step * 1e-3),
                          "line_sum_ms": k3_mean, "wall_s": t_wall,
-                         "pairs_per_step": stats["pairs"] / args.steps,
-                         "gauss_terms_per_step": stats["gauss_terms"] / args.steps,
-                         "correction_terms_per_step": stats["correction_terms"] / args.steps},
+                         "pairs_per_step": stats["pairs"],
+                         "gauss_terms_per_step": stats["gauss_terms"],
+                         "correction_terms_per_step": stats["correction_terms"]},
            "roofline": roof, "clocks": clk.summary(), "gpu_launches": None}
     # launches per step: validate x2, line prep, cell prep, bounds, count, scan, fill, line sum,
     # populations + its validation, march + its validation, flux, slab rays are built once
@@ -310,6 +427,8 @@ def main():
         out["e2e"] = {"value": world * C * K / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
                       "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3}
         ectx.close()
+    if not args.no_serve:
+        out["served"] = served(p, args, local)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
     if rank == 0:

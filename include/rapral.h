@@ -199,6 +199,11 @@ typedef struct {
     int64_t pairs;
 } rapral_stats;
 
+/* Turns the FP32 line sum's work counters on (default) or off; counting
+ * costs a few conversions per (line, cell, tile) pair.  The FP64 path
+ * always counts. */
+RAPRAL_API int rapral_set_counters(rapral_ctx* ctx, int on);
+
 /* Reads the counters (synchronises the stream). */
 RAPRAL_API int rapral_get_stats(rapral_ctx* ctx, rapral_stats* out);
 RAPRAL_API int rapral_reset_stats(rapral_ctx* ctx);
@@ -254,7 +259,8 @@ RAPRAL_API int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp,
  *   I <- I e^{-dtau} + a j_far + b j_near,  dtau = kappa_far ds scale,
  *   a = (f - e^{-dtau}) / kappa_far,  b = (1 - f) / kappa_far,
  *   f = (1 - e^{-dtau}) / dtau,
- * with three-term series of a and b when |dtau| < 4e-4 (FP64) / 5e-2 (FP32).
+ * with the series of a and b when |dtau| < 4e-4 (FP64, three terms) or
+ * |dtau| < 0.5 (FP32, seven terms).
  * The march starts from 0 (far field) or the Planck intensity at T_wall.
  * Then q_lambda[p][k] = sum over the point's directions of weight * I.
  * In: kappa, emis [C][ld] for grid points [k0, k0+nk) (as written by
@@ -341,7 +347,7 @@ RAPRAL_API void rapral_batch_destroy(rapral_batch* batch);
  * widths (512 FP64, 128 FP32), paper constants.  Arguments as rapral_spectral_coeffs, plus an optional
  * caller buffer `err` (err_len bytes) for a message.  Errors: EINVAL (sizes,
  * ranges, failed device-side input checks), ENOMEM (the problem needs more
- * than the 64 MiB scratch: about 160 bytes per line plus 48 per cell and the
+ * than the 64 MiB scratch: about 230 bytes per line plus 64 per cell and the
  * tile lists), ECUDA. */
 RAPRAL_API int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_species* sp,
                                               const rapral_lines* lines, const rapral_cells* cells,

@@ -8,6 +8,7 @@
 // persistent line sum over all units, and each request's march and flux --
 // with no allocation and no host synchronisation, so it can be captured in a
 // CUDA graph and replayed.
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -33,6 +34,7 @@ struct rapral_batch {
     int* csr = nullptr;           // tile lists of every request
     BatchItem* d_items = nullptr;
     unsigned long long* d_counter = nullptr;
+    void* d_flux = nullptr;       // partial sums of the spectral integral (largest request)
     int64_t total_units = 0;
     int blocks = 0;
 };
@@ -88,6 +90,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         if (T > 65535) { delete B; return set_error(ctx, RAPRAL_EINVAL, "request %d: too many tiles", i); }
         base[i] = need;
         need = arena_need(need, L * sizeof(LinePrep));
+        need = arena_need(need, L * sizeof(LineF32));
         need = arena_need(need, C * sizeof(CellPrep));
         need = arena_need(need, L * sizeof(int2));
         need = arena_need(need, (T + 1) * sizeof(int));
@@ -103,6 +106,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     }
     std::vector<BinPlan> plans(n_items);
     std::vector<LinePrep*> lps(n_items);
+    std::vector<LineF32*> lfs(n_items);
     std::vector<CellPrep*> cps(n_items);
     const Phys ph = make_phys(ctx->codata);
     static const int one = 1;
@@ -113,6 +117,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         const int64_t L = r.ln.n_lines, C = r.cells.n_cells, T = (r.nk + W - 1) / W;
         Arena ar{B->ws, need, base[i]};
         lps[i] = ar.take<LinePrep>(L);
+        lfs[i] = ar.take<LineF32>(L);
         cps[i] = ar.take<CellPrep>(C);
         BinPlan& pl = plans[i];
         pl.k0 = r.k0; pl.nk = r.nk; pl.tile_w = W; pl.n_tiles = T;
@@ -126,7 +131,8 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         if (e == cudaSuccess) e = launch_validate_cells(ctx, &r.cells);
         if (e == cudaSuccess) e = launch_validate_lines(ctx, &r.ln, r.sp.n_species);
         if (e == cudaSuccess) e = launch_validate_rays(ctx, &r.rays, C);
-        if (e == cudaSuccess) e = launch_line_prep(ctx, &r.sp, &r.ln, r.grid.lam_min, r.h, ph, lps[i], pl.sorted_flag);
+        if (e == cudaSuccess) e = launch_line_prep(ctx, &r.sp, &r.ln, r.grid.lam_min, r.h, ph, lps[i], lfs[i],
+                                                  pl.sorted_flag);
         if (e == cudaSuccess) e = launch_cell_prep(ctx, &r.cells, ph, cps[i], dmax);
         if (e == cudaSuccess) e = launch_bin_bounds(ctx, &r.ln, lps[i], cps[i], dmax, r.h, &pl);
         if (e == cudaSuccess) e = launch_bin_count(ctx, &r.ln, &r.grid, r.h, &pl);
@@ -148,10 +154,10 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         plans[i].tile_lines = B->csr + csr_base[i];
         e = launch_bin_fill(ctx, &r.ln, &r.grid, r.h, &plans[i]);
         LineSumArgs& a = hitems[i].a;
-        a.lp = lps[i]; a.cp = cps[i]; a.lnpref = r.cells.lnpref; a.S = r.sp.n_species; a.C = r.cells.n_cells;
+        a.lp = lps[i]; a.lf = lfs[i]; a.cp = cps[i]; a.lnpref = r.cells.lnpref; a.S = r.sp.n_species; a.C = r.cells.n_cells;
         a.tile_off = plans[i].tile_off; a.tile_lines = plans[i].tile_lines;
         a.lam_min = r.grid.lam_min; a.h = r.h; a.k0 = r.k0; a.nk = r.nk; a.ld = r.ld; a.tile_w = W;
-        a.kappa = r.kappa; a.emis = r.emis; a.status = ctx->d_status; a.stats = ctx->d_stats;
+        a.kappa = r.kappa; a.emis = r.emis; a.status = ctx->d_status; a.stats = ctx->d_stats; a.count = ctx->count_work;
         hitems[i].unit_off = units;
         hitems[i].n_groups = (r.cells.n_cells + B->wpb - 1) / B->wpb;
         units += plans[i].n_tiles * hitems[i].n_groups;
@@ -159,6 +165,10 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     B->total_units = units;
     if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(BatchItem) * n_items);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned long long));
+    size_t flux_bytes = 256;
+    for (int i = 0; i < n_items; ++i)
+        flux_bytes = std::max(flux_bytes, (size_t)wall_flux_parts(B->req[i].nk) * (size_t)B->req[i].rays.n_points * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_flux, flux_bytes);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_items, hitems.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice,
                             ctx->stream);
@@ -194,7 +204,8 @@ int rapral_batch_run(rapral_ctx* ctx, rapral_batch* B) {
         e = launch_march(ctx, &r.rays, r.kappa, r.emis, r.ld, &r.grid, r.h, r.k0, r.nk, RAPRAL_FP32, r.q_lambda,
                          nullptr, ph);
         if (e == cudaSuccess)
-            e = launch_wall_flux(ctx, r.q_lambda, RAPRAL_FP32, &r.grid, r.h, r.k0, r.nk, r.rays.n_points, r.q);
+            e = launch_wall_flux(ctx, r.q_lambda, RAPRAL_FP32, &r.grid, r.h, r.k0, r.nk, r.rays.n_points, r.q,
+                                 B->d_flux);
     }
     return cuda_status(ctx, e, "batch run");
 }
@@ -205,6 +216,7 @@ void rapral_batch_destroy(rapral_batch* B) {
     if (B->csr) cudaFree(B->csr);
     if (B->d_items) cudaFree(B->d_items);
     if (B->d_counter) cudaFree(B->d_counter);
+    if (B->d_flux) cudaFree(B->d_flux);
     delete B;
 }
 

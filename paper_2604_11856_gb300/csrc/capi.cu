@@ -128,6 +128,12 @@ int rapral_reset_stats(rapral_ctx* ctx) {
                        "stats reset");
 }
 
+int rapral_set_counters(rapral_ctx* ctx, int on) {
+    if (!ctx) return RAPRAL_EINVAL;
+    ctx->count_work = on ? 1 : 0;
+    return RAPRAL_OK;
+}
+
 int rapral_set_profile_events(rapral_ctx* ctx, void* before, void* after) {
     if (!ctx || ((before == nullptr) != (after == nullptr))) return RAPRAL_EINVAL;
     ctx->ev_before = reinterpret_cast<cudaEvent_t>(before);
@@ -185,6 +191,7 @@ int rapral_workspace_bytes(int64_t n_lines, int64_t n_cells, int64_t nk, size_t*
     const int64_t tiles = nk / 128 + 2;
     size_t b = 0;
     b = arena_need(b, (size_t)n_lines * sizeof(LinePrep));
+    b = arena_need(b, (size_t)n_lines * sizeof(LineF32));
     b = arena_need(b, (size_t)n_lines * sizeof(int2));
     b = arena_need(b, (size_t)n_cells * sizeof(CellPrep));
     b = arena_need(b, (size_t)(tiles + 1) * sizeof(int));
@@ -259,6 +266,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     // phase 1: per-line and per-cell records, tile ranges, tile counts
     size_t need = 0;
     need = arena_need(need, L * sizeof(LinePrep));
+    need = arena_need(need, L * sizeof(LineF32));
     need = arena_need(need, C * sizeof(CellPrep));
     need = arena_need(need, L * sizeof(int2));
     need = arena_need(need, (T + 1) * sizeof(int));
@@ -270,6 +278,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     if (st) return st;
     Arena ar{ctx->ws, ctx->ws_bytes};
     LinePrep* lp = ar.take<LinePrep>(L);
+    LineF32* lf = ar.take<LineF32>(L);
     CellPrep* cp = ar.take<CellPrep>(C);
     BinPlan plan;
     plan.k0 = k0; plan.nk = nk; plan.tile_w = W; plan.n_tiles = T;
@@ -283,7 +292,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     if (e == cudaSuccess) e = cudaMemsetAsync(plan.wmax, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = launch_validate_cells(ctx, cells);
     if (e == cudaSuccess) e = launch_validate_lines(ctx, ln, sp->n_species);
-    if (e == cudaSuccess) e = launch_line_prep(ctx, sp, ln, g->lam_min, h, ph, lp, plan.sorted_flag);
+    if (e == cudaSuccess) e = launch_line_prep(ctx, sp, ln, g->lam_min, h, ph, lp, lf, plan.sorted_flag);
     if (e == cudaSuccess) e = launch_cell_prep(ctx, cells, ph, cp, dmax);
     if (e == cudaSuccess) e = launch_bin_bounds(ctx, ln, lp, cp, dmax, h, &plan);
     if (e == cudaSuccess) e = launch_bin_count(ctx, ln, g, h, &plan);
@@ -306,10 +315,10 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     if (e != cudaSuccess) return cuda_status(ctx, e, "line binning");
 
     LineSumArgs a;
-    a.lp = lp; a.cp = cp; a.lnpref = cells->lnpref; a.S = sp->n_species; a.C = C;
+    a.lp = lp; a.lf = lf; a.cp = cp; a.lnpref = cells->lnpref; a.S = sp->n_species; a.C = C;
     a.tile_off = plan.tile_off; a.tile_lines = plan.tile_lines;
     a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk; a.ld = ld; a.tile_w = W;
-    a.kappa = kappa; a.emis = emis; a.status = ctx->d_status; a.stats = ctx->d_stats;
+    a.kappa = kappa; a.emis = emis; a.status = ctx->d_status; a.stats = ctx->d_stats; a.count = ctx->count_work;
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");
 }
@@ -352,7 +361,12 @@ int rapral_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const
         return set_error(ctx, RAPRAL_EINVAL, "precision %d", precision);
     if (n_points < 0 || n_points > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "n_points");
     cudaSetDevice(ctx->device);
-    return cuda_status(ctx, launch_wall_flux(ctx, q_lambda, precision, g, grid_h(g), k0, nk, n_points, q), "wall flux");
+    // the partial sums live at the start of the workspace: every earlier user
+    // of the workspace on this stream has been enqueued before
+    st = ws_reserve(ctx, (size_t)wall_flux_parts(nk) * (size_t)n_points * 16 + 256);
+    if (st) return st;
+    return cuda_status(ctx, launch_wall_flux(ctx, q_lambda, precision, g, grid_h(g), k0, nk, n_points, q, ctx->ws),
+                       "wall flux");
 }
 
 int rapral_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx, int32_t n_layers, const double* mu,

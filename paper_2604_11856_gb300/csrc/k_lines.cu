@@ -41,7 +41,8 @@ __global__ void k_validate_lines(rapral_lines ln, int32_t S, int* status) {
 }
 
 __global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, double lam_min, double h, Phys ph,
-                            LinePrep* __restrict__ out, int* sorted_flag, const int* status) {
+                            LinePrep* __restrict__ out, LineF32* __restrict__ out32, int* sorted_flag,
+                            const int* status) {
     if (*status) return;
     int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (l >= ln.n_lines) return;
@@ -75,6 +76,22 @@ __global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, do
     p.species = s;
     p.pad = 0;
     out[l] = p;
+    if (out32) {
+        LineF32 f;
+        f.lnAjg = ff_from(p.lnAjg);
+        f.dAkj = ff_from(p.lnAk - p.lnAj);
+        f.Eve_u = ff_from(p.Eve_u);
+        f.Er_u = ff_from(p.Er_u);
+        f.dEve = ff_from(p.dEve);
+        f.dEr = ff_from(p.dEr);
+        f.cD = p.cD_f;
+        f.lamS0 = p.lamS0_f;
+        f.delta = p.delta_f;
+        f.kc = p.kc;
+        f.species = s;
+        f.kcf = (float)p.kc;
+        out32[l] = f;
+    }
     if (l + 1 < ln.n_lines && ln.lam0[l + 1] < lam0) *sorted_flag = 0;
 }
 
@@ -374,15 +391,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// e^y for an FP64 exponent: y log2(e) = n + f, n integer, f in [0, 1);
-// 2^f in FP32, scaled by 2^n (0 below the FP32 range).
-__device__ __forceinline__ float exp_reduced(double y) {
-    const double t = y * 1.4426950408889634;
-    if (!(t > -200.0)) return 0.0f;
-    const double n = floor(fmin(t, 200.0));
-    return ldexpf(exp2f((float)(t - n)), (int)n);
-}
-
 __device__ __forceinline__ bool in_window64(int64_t k, double lam_min, double h, double lam0, double w100) {
     const double lk = __dadd_rn(lam_min, __dmul_rn((double)k, h));
     return fabs(lk - lam0) <= w100;
@@ -404,63 +412,96 @@ __device__ __noinline__ void exact_edges(const LinePrep& L, const CellPrep& cp, 
     *khi = hi;
 }
 
-// One (line, cell) pair set up for the tile: window [klo, khi] (grid
-// indices, certified), profile constants and strengths.  Returns false when
-// the pair adds nothing to the tile.
+// One (line, cell) pair set up for a warp's tile [kt0, kt0 + TW): window
+// offsets inside the tile, u at the tile's first point, profile constants,
+// and whether every point of the window part in the tile lies in the far
+// wings (|u| > 11, where both exponentials are zero in FP32).  Everything a
+// warp needs per pair is computed here, by one lane per pair.
 struct PairF32 {
-    int klo, khi, kc;
-    float s, u0, r, aj, ak;
+    int rel;          // (klo - kt0) | (khi - kt0) << 16
+    int far;
+    float ub, ub_lo;  // signed u at kt0, (kt0 - kc) s - u0, as a float-float pair
+    float s;          // h / (2 lamV): step of u per grid point
+    float r, aj, ak;
 };
 
-__device__ __forceinline__ bool setup_pair_f32(const LinePrep& L, const CellPrep& cp, double lp, double lam_min,
-                                               double h, float hf, int kt0, int kt1, PairF32* P, int64_t* cnt) {
-    if (!(lp > -INFINITY)) return false;
-    const double base = lp - (L.Eve_u * cp.bve + L.Er_u * cp.btr);   // ln N_u - ln g_u
-    const double yj = L.lnAjg + base;
-    const float Sj = exp_reduced(yj);
-    const float x = L.dEve_f * cp.bve_f + L.dEr_f * cp.btr_f;
-    float Sk;
-    if (x >= 0.0f) {
-        const double yk = L.lnAkg + lp - (L.Eve_l * cp.bve + L.Er_l * cp.btr);
-        Sk = exp_reduced(yk) * -expm1f(-x);
-    } else {
-        Sk = exp_reduced(yj - L.lnAj + L.lnAk) * expm1f(x);
-    }
-    if (!(Sj > 0.0f) && Sk == 0.0f) return false;
-    const float lamG = L.cD_f * cp.sqrtT_f;
-    const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0_f * cp.stc_f;
+__device__ __forceinline__ bool setup_pair_f32(const LineF32& L, const CellPrep& cp, float2 lp, int line,
+                                               const LinePrep* lp64, double lam_min, double h, float hf, int kt0,
+                                               int kt1, float kt0f, float kt1f, bool count, PairF32* P,
+                                               int64_t* cnt) {
+    if (!(lp.x > -INFINITY)) return false;
+    // widths first: most candidates of a tile list miss the tile in a given cell
+    const float lamG = L.cD * cp.sqrtT_f;
+    const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc_f;
     const float sum = lamL + lamG;
+    {   // lamV <= lamL + lamG: cheap rejection before the Voigt fit
+        const float wmax = (float)RAPRAL_WINDOW * sum / hf * 1.0001f + 1.0f;
+        if (kt1f - L.kcf < L.delta - wmax || kt0f - L.kcf > L.delta + wmax) return false;
+    }
     const float d = (lamL - lamG) / sum;
     const float F = 1.0f - 0.18121f * (1.0f - d * d) -
                     (0.023665f * expf(0.6f * d) + 0.00418f * expf(-1.9f * d)) * sinpif(d);
     const float lamV = F * sum;
     const float wpts = (float)RAPRAL_WINDOW * lamV / hf;
-    const float hi = L.delta_f + wpts, lo = L.delta_f - wpts;
+    const float hi = L.delta + wpts, lo = L.delta - wpts;
     const float fhi = floorf(hi), clo = ceilf(lo);
-    int64_t khi = (int64_t)L.kc + (int64_t)fhi;
-    int64_t klo = (int64_t)L.kc + (int64_t)clo;
+    int64_t khi = (int64_t)L.kc + __float2int_rd(hi);
+    int64_t klo = (int64_t)L.kc + __float2int_ru(lo);
     const float m = 2e-6f * wpts + 2e-3f;
     if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m)
-        exact_edges(L, cp, lam_min, h, &klo, &khi);
+        exact_edges(lp64[line], cp, lam_min, h, &klo, &khi);
     klo = max(klo, (int64_t)kt0);
     khi = min(khi, (int64_t)kt1);
     if (klo > khi) return false;
+    // strengths: ln S_j = lnAj + ln g_u + ln(N_s/Z_s) - (E_el + E_V)_u c2/T_ve - E_J,u c2/T_tr
+    // and x = ln(N_l g_u / (N_u g_l)) = dE_ve c2/T_ve + dE_J c2/T_tr, in float-float
+    const float2 yj = ff_add(ff_add(L.lnAjg, lp), ff_neg(ff_add(ff_mul(L.Eve_u, cp.bve_ff), ff_mul(L.Er_u, cp.btr_ff))));
+    const float2 x = ff_add(ff_mul(L.dEve, cp.bve_ff), ff_mul(L.dEr, cp.btr_ff));
+    const float Sj = expf(yj.x) * (1.0f + yj.y);
+    float2 yk = ff_add(yj, L.dAkj);
+    float fk;
+    if (x.x >= 0.0f) {           // kappa0 = e^{lnAk + ln N_l g_u/g_l} (1 - e^{-x})
+        yk = ff_add(yk, x);
+        fk = -expm1f(-x.x);
+    } else {                     // kappa0 = e^{lnAk + ln N_u} (e^{x} - 1)
+        fk = expm1f(x.x);
+    }
+    const float Sk = expf(yk.x) * (1.0f + yk.y) * fk;
+    if (!(Sj > 0.0f) && Sk == 0.0f) return false;
     const float r = lamL / lamV;
     const float pre = 1e3f / (2.0f * lamV * (1.065f + 0.447f * r + 0.058f * r * r));
-    P->klo = (int)klo; P->khi = (int)khi; P->kc = L.kc;
+    const int lo_rel = (int)(klo - kt0), hi_rel = (int)(khi - kt0);
+    P->rel = lo_rel | (hi_rel << 16);
     P->s = 0.5f * hf / lamV;
-    P->u0 = L.delta_f * P->s;
+    const float u0 = L.delta * P->s;                 // u of the centre's offset from kc
+    {   // signed u at kt0 without rounding loss: (kt0 - kc) is exact, its
+        // product with s and the sum with -u0 are split into hi + lo
+        const float dk = kt0f - L.kcf;
+        const float p = dk * P->s;
+        const float pe = fmaf(dk, P->s, -p);
+        const float hi = p - u0;
+        const float bb = hi - p;
+        const float e = (p - (hi - bb)) + (-u0 - bb);
+        P->ub = hi;
+        P->ub_lo = e + pe;
+    }
+    // smallest |u| over the evaluated part [klo, khi] of the tile
+    const float ua = fmaf((float)lo_rel, P->s, P->ub), ue = fmaf((float)hi_rel, P->s, P->ub);
+    const float umin = (ua > 0.0f) ? ua : (ue < 0.0f ? -ue : 0.0f);
+    P->far = umin > 11.0f;
     P->r = r;
     P->aj = Sj * pre;
     P->ak = Sk * pre;
-    // work counters: points in the window; those where the Gaussian core and
-    // the exponential correction are above the FP32 underflow limits
-    cnt[0] += khi - klo + 1;
-    const float kcen = (float)L.kc + L.delta_f;
-    const float hg = 5.6125f / P->s, hc = 10.95f / P->s;   // u^2 < 31.5, u^2.25 < 218
-    cnt[1] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hg)) - max(klo, (int64_t)ceilf(kcen - hg)) + 1);
-    cnt[2] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hc)) - max(klo, (int64_t)ceilf(kcen - hc)) + 1);
-    cnt[3] += 1;
+    if (count) {
+        // work counters: points in the window; those where the Gaussian core and
+        // the exponential correction are above the FP32 underflow limits
+        cnt[0] += khi - klo + 1;
+        const float kcen = L.kcf + L.delta;
+        const float hg = 5.6125f / P->s, hc = 10.95f / P->s;   // u^2 < 31.5, u^2.25 < 218
+        cnt[1] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hg)) - max(klo, (int64_t)ceilf(kcen - hg)) + 1);
+        cnt[2] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hc)) - max(klo, (int64_t)ceilf(kcen - hc)) + 1);
+        cnt[3] += 1;
+    }
     return true;
 }
 
@@ -496,54 +537,62 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 // over its points.  Warps never wait for each other.
 template <int PPT>
 __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
-                                              int lane, int64_t* cnt) {
+                                              float2* smlp, float4* acc, int lane, int64_t* cnt) {
     constexpr int TW = 32 * PPT;
     const int kt0 = (int)(a.k0 + (int64_t)t * TW);
     const int kt1 = (int)min(a.k0 + (int64_t)(t + 1) * TW, a.k0 + a.nk) - 1;   // inclusive
-    const int kp = kt0 + lane * PPT;
-    // compensated sums (Kahan) of the per-batch partial sums; inside a batch
-    // of at most 32 lines the terms are added plainly (error <= 31 u of the
-    // batch's magnitude, u = 2^-24)
-    float sk[PPT], ck[PPT], sj[PPT], cj[PPT], bk[PPT], bj[PPT];
+    const float kt0f = (float)kt0, kt1f = (float)kt1;
+    const int lp0 = lane * PPT;            // lane's first point, relative to kt0
+    const float lpf = (float)lp0;
+    // compensated sums (Kahan) of the per-batch partial sums, kept in shared
+    // memory (acc[i * 32 + lane] = (s_j, c_j, s_k, c_k)); inside a batch of at
+    // most 32 lines the terms are added plainly in registers (error <= 31 u
+    // of the batch's magnitude, u = 2^-24)
+    float bk[PPT], bj[PPT];
 #pragma unroll
-    for (int i = 0; i < PPT; ++i) { sk[i] = ck[i] = sj[i] = cj[i] = bk[i] = bj[i] = 0.0f; }
+    for (int i = 0; i < PPT; ++i) {
+        bk[i] = bj[i] = 0.0f;
+        acc[i * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
     const CellPrep cp = a.cp[c];
     const float hf = (float)a.h;
-    const double* lnp = a.lnpref + c * a.S;
+    const bool count = a.count != 0;
+    if (lane < a.S) {   // the cell's ln(N_s / Z_s) as float-float pairs
+        const double v = a.lnpref[c * a.S + lane];
+        smlp[lane] = v > -INFINITY ? ff_from(v) : make_float2(-INFINITY, 0.0f);
+    }
+    __syncwarp();
     const int beg = a.tile_off[t], end = a.tile_off[t + 1];
     for (int b = beg; b < end; b += 32) {
         const int nb = min(32, end - b);
+        PairF32 P;
+        bool valid = false;
         if (lane < nb) {
             const int l = a.tile_lines[b + lane];
-            const LinePrep L = a.lp[l];
-            PairF32 P;
-            if (setup_pair_f32(L, cp, lnp[L.species], a.lam_min, a.h, hf, kt0, kt1, &P, cnt)) {
-                sm0[lane] = make_float4(__int_as_float(P.klo), __int_as_float(P.khi), __int_as_float(P.kc), P.s);
-                sm1[lane] = make_float4(P.u0, P.r, P.aj, P.ak);
-            } else {
-                sm0[lane] = make_float4(__int_as_float(1), __int_as_float(0), 0.0f, 0.0f);
-            }
+            const LineF32 L = a.lf[l];
+            valid = setup_pair_f32(L, cp, smlp[L.species], l, a.lp, a.lam_min, a.h, hf, kt0, kt1, kt0f, kt1f, count,
+                                   &P, cnt);
+        }
+        // compact the pairs that reach the tile to the front of the staging area
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const int nv = __popc(vmask);
+        if (valid) {
+            const int pos = __popc(vmask & ((1u << lane) - 1u));
+            sm0[pos] = make_float4(__int_as_float(P.rel), __int_as_float(P.far), P.ub, P.s);
+            sm1[pos] = make_float4(P.r, P.ub_lo, P.aj, P.ak);
         }
         __syncwarp();
-        for (int q = 0; q < nb; ++q) {
+        for (int q = 0; q < nv; ++q) {
             const float4 A = sm0[q];
-            const int klo = __float_as_int(A.x), khi = __float_as_int(A.y);
-            if (khi < kt0) continue;   // nothing of this pair in the tile (uniform over the warp)
-            const int i0 = max(klo - kp, 0);
-            const int i1 = min(khi - kp, PPT - 1);
-            const float4 B = sm1[q];
-            const float s = A.w, u0 = B.x, r = B.y, aj = B.z, ak = B.w;
-            const float omr = 1.0f - r, c16 = 0.016f * r * omr;
-            const int kc = __float_as_int(A.z);
-            // distance (in u) from the line centre to the nearest evaluated point
-            // of the whole warp: decides, uniformly, whether the exponentials can
-            // be dropped
-            const float cen = u0 / s;                    // centre offset from kc, grid units
-            const float dlo = (float)(max(klo, kt0) - kc) - cen, dhi = (float)(min(khi, kt1) - kc) - cen;
-            const float umin = (dlo > 0.0f ? dlo : (dhi < 0.0f ? -dhi : 0.0f)) * s;
-            const float x0 = fmaf((float)(kp - kc), s, -u0);   // signed u of the lane's first point
+            const int rel = __float_as_int(A.x);
+            const int i0 = max((rel & 0xffff) - lp0, 0);
+            const int i1 = min((rel >> 16) - lp0, PPT - 1);
             if (i0 > i1) continue;
-            if (umin > 11.0f) {
+            const float4 B = sm1[q];
+            const float s = A.w, r = B.x, aj = B.z, ak = B.w;
+            const float omr = 1.0f - r, c16 = 0.016f * r * omr;
+            const float x0 = fmaf(lpf, s, A.z) + B.y;   // signed u of the lane's first point
+            if (__float_as_int(A.y)) {                // far wings only (uniform over the warp)
                 if (i0 == 0 && i1 == PPT - 1) {
 #pragma unroll
                     for (int i = 0; i < PPT; ++i) {
@@ -572,8 +621,10 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
         }
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-            kahan_add(sj[i], cj[i], bj[i]);
-            kahan_add(sk[i], ck[i], bk[i]);
+            float4 v = acc[i * 32 + lane];
+            kahan_add(v.x, v.y, bj[i]);
+            kahan_add(v.z, v.w, bk[i]);
+            acc[i * 32 + lane] = v;
             bj[i] = bk[i] = 0.0f;
         }
         __syncwarp();
@@ -582,22 +633,32 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     float* J = reinterpret_cast<float*>(a.emis) + c * a.ld - a.k0;
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
-        const int k = kp + i;
-        if (k <= kt1) { K[k] = sk[i]; J[k] = sj[i]; }
+        const int k = kt0 + lp0 + i;
+        const float4 v = acc[i * 32 + lane];
+        if (k <= kt1) { K[k] = v.z; J[k] = v.x; }
     }
 }
 
+// Resident blocks per SM asked of the compiler: 32 warps per SM, so at most
+// 64 registers per thread (measured best against 24 and 20 warps).
+#ifndef RAPRAL_LS_WARPS
+#define RAPRAL_LS_WARPS 32
+#endif
+#define RAPRAL_LS_BLOCKS(WPB) (RAPRAL_LS_WARPS / (WPB))
+
 template <int PPT, int WPB>
-__global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_f32(LineSumArgs a) {
+__global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f32(LineSumArgs a) {
     if (*a.status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * WPB + warp;
     if (c >= a.C) return;
     __shared__ float4 sm0[WPB][32];   // klo, khi, kc (int bits), s
     __shared__ float4 sm1[WPB][32];   // u0, r, aj, ak
+    __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
+    __shared__ float4 acc[WPB][32 * PPT];
     int64_t cnt[4] = {0, 0, 0, 0};
-    warp_tile_f32<PPT>(a, blockIdx.y, c, sm0[warp], sm1[warp], lane, cnt);
-    block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
+    warp_tile_f32<PPT>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], acc[warp], lane, cnt);
+    if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
 // Persistent line sum over many independent requests: blocks pull work
@@ -605,7 +666,7 @@ __global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_f32(LineSumArgs
 // list is exhausted; units of a request are ordered tile by tile so blocks
 // working at the same time share a tile's line list in L2.
 template <int PPT, int WPB>
-__global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_batch(const BatchItem* __restrict__ items,
+__global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_batch(const BatchItem* __restrict__ items,
                                                                        int n_items, int64_t total,
                                                                        unsigned long long* counter,
                                                                        unsigned long long* stats, const int* status) {
@@ -613,6 +674,8 @@ __global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_batch(const Bat
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ float4 sm0[WPB][32];
     __shared__ float4 sm1[WPB][32];
+    __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
+    __shared__ float4 acc[WPB][32 * PPT];
     __shared__ long long unit_s;
     int64_t cnt[4] = {0, 0, 0, 0};
     for (;;) {
@@ -630,9 +693,10 @@ __global__ void __launch_bounds__(32 * WPB, 32 / WPB) k_line_sum_batch(const Bat
         const int64_t local = u - it.unit_off;
         const int t = (int)(local / it.n_groups);
         const int64_t c = (local - (int64_t)t * it.n_groups) * WPB + warp;
-        if (c < it.a.C) warp_tile_f32<PPT>(it.a, t, c, sm0[warp], sm1[warp], lane, cnt);
+        if (c < it.a.C) warp_tile_f32<PPT>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], acc[warp], lane, cnt);
+        __syncwarp();
     }
-    block_count(stats, cnt[0], cnt[1], cnt[2], cnt[3]);
+    if (items[0].a.count) block_count(stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
 }  // namespace
@@ -644,10 +708,11 @@ cudaError_t launch_validate_lines(rapral_ctx* ctx, const rapral_lines* ln, int32
 }
 
 cudaError_t launch_line_prep(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
-                             double lam_min, double h, const Phys& ph, LinePrep* out, int* sorted_flag) {
+                             double lam_min, double h, const Phys& ph, LinePrep* out, LineF32* out32,
+                             int* sorted_flag) {
     if (ln->n_lines == 0) return cudaSuccess;
-    k_line_prep<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(*ln, sp->mass, lam_min, h, ph, out, sorted_flag,
-                                                                   ctx->d_status);
+    k_line_prep<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(*ln, sp->mass, lam_min, h, ph, out, out32,
+                                                                   sorted_flag, ctx->d_status);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,8 @@ __global__ void k_cell_prep(const double* __restrict__ Ttr, const double* __rest
     p.btr_f = (float)p.btr;
     p.sqrtT_f = (float)p.sqrtT;
     p.stc_f = (float)p.stc;
+    p.bve_ff = ff_from(p.bve);
+    p.btr_ff = ff_from(p.btr);
     out[c] = p;
     // positive doubles order like their bit patterns
     atomicMax(&dmax[0], (unsigned long long)__double_as_longlong(p.sqrtT));

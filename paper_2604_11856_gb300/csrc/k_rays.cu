@@ -15,15 +15,60 @@
 
 namespace {
 
-template <class T> struct Real;
-template <> struct Real<double> {
-    static __device__ __forceinline__ double em1(double x) { return expm1(x); }
-    static constexpr double thin = RAPRAL_THIN_F64;
-};
-template <> struct Real<float> {
-    static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
-    static constexpr float thin = (float)RAPRAL_THIN_F32;
-};
+// Segment coefficients: e = e^{-dtau}, far-node coefficient ca = (f - e)/kappa
+// and near-node coefficient cb = (1 - f)/kappa, f = (1 - e)/dtau, with their
+// series for small |dtau|.
+//   FP64: |dtau| < 4e-4 takes three terms of each series; e from expm1.
+//   FP32: |dtau| < 0.5 takes seven terms (truncation <= 4e-7 relative), so
+//   the closed form is used only where 1 - e >= 0.39 and an approximate ex2
+//   for e keeps FP32 accuracy without expm1f.
+__device__ __forceinline__ void seg_coeffs(double kap, double s, double inv_k, double* e, double* ca, double* cb) {
+    const double dtau = kap * s;
+    const double em1 = expm1(-dtau);   // e^{-dtau} - 1
+    *e = 1.0 + em1;
+    if (fabs(dtau) < RAPRAL_THIN_F64) {
+        *ca = s * (0.5 - dtau * (1.0 / 3.0) + dtau * dtau * 0.125);
+        *cb = s * (0.5 - dtau * (1.0 / 6.0) + dtau * dtau * (1.0 / 24.0));
+    } else {
+        const double f = -em1 / dtau;
+        *ca = (f - *e) * inv_k;
+        *cb = (1.0 - f) * inv_k;
+    }
+}
+
+__device__ __forceinline__ float ex2f_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void seg_coeffs(float kap, float s, float inv_k, float* e, float* ca, float* cb) {
+    const float dtau = kap * s;
+    *e = ex2f_approx(-1.44269504f * dtau);
+    if (fabsf(dtau) < (float)RAPRAL_THIN_F32) {
+        const float t = dtau;
+        // a/s = 1/2 - t/3 + t^2/8 - t^3/30 + t^4/144 - t^5/840 + t^6/5760
+        float pa = fmaf(t, 1.0f / 5760.0f, -1.0f / 840.0f);
+        pa = fmaf(t, pa, 1.0f / 144.0f);
+        pa = fmaf(t, pa, -1.0f / 30.0f);
+        pa = fmaf(t, pa, 0.125f);
+        pa = fmaf(t, pa, -1.0f / 3.0f);
+        pa = fmaf(t, pa, 0.5f);
+        // b/s = 1/2 - t/6 + t^2/24 - t^3/120 + t^4/720 - t^5/5040 + t^6/40320
+        float pb = fmaf(t, 1.0f / 40320.0f, -1.0f / 5040.0f);
+        pb = fmaf(t, pb, 1.0f / 720.0f);
+        pb = fmaf(t, pb, -1.0f / 120.0f);
+        pb = fmaf(t, pb, 1.0f / 24.0f);
+        pb = fmaf(t, pb, -1.0f / 6.0f);
+        pb = fmaf(t, pb, 0.5f);
+        *ca = s * pa;
+        *cb = s * pb;
+    } else {
+        const float f = (1.0f - *e) / dtau;
+        *ca = (f - *e) * inv_k;
+        *cb = (1.0f - f) * inv_k;
+    }
+}
 
 __global__ void k_validate_rays(const int32_t* seg_cell, const double* seg_ds, int64_t nseg, int64_t C,
                                 const double* dir_scale, int64_t ndir, int* status) {
@@ -80,7 +125,6 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
     const int64_t kcol = active ? kk : a.nk - 1;
     const T* Kt = reinterpret_cast<const T*>(a.kappa) + kcol;
     const T* Jt = reinterpret_cast<const T*>(a.emis) + kcol;
-    const T thin = Real<T>::thin;
     T acc = T(0), comp = T(0);
     for (int64_t b = a.point_off[p] + slice; b < a.point_off[p + 1]; b += SL) {
         const int64_t d0 = a.dir_off[b];
@@ -112,19 +156,8 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
 #pragma unroll
                 for (int d = 0; d < MAXD; ++d) {
                     if (d < nd) {
-                        const T s = ds * (T)a.dir_scale[d0 + d];
-                        const T dtau = kf * s;
-                        const T em1 = Real<T>::em1(-dtau);     // e^{-dtau} - 1
-                        const T e = T(1) + em1;
-                        T ca, cb;
-                        if (fabs(dtau) < thin) {
-                            ca = s * (T(0.5) - dtau * (T(1) / T(3)) + dtau * dtau * T(0.125));
-                            cb = s * (T(0.5) - dtau * (T(1) / T(6)) + dtau * dtau * (T(1) / T(24)));
-                        } else {
-                            const T f = -em1 / dtau;
-                            ca = (f - e) * inv_k;
-                            cb = (T(1) - f) * inv_k;
-                        }
+                        T e, ca, cb;
+                        seg_coeffs(kf, ds * (T)a.dir_scale[d0 + d], inv_k, &e, &ca, &cb);
                         I[d] = I[d] * e + ca * jf + cb * jn;
                     }
                 }
@@ -160,13 +193,20 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
     }
 }
 
+// Spectral integral in two deterministic stages: blocks (point, slice)
+// Neumaier-sum a slice of FLUX_SPAN grid points each, then one block per
+// point adds the slices in order.
+constexpr int FLUX_SPAN = 4096;
+
 template <class T>
-__global__ void __launch_bounds__(256) k_wall_flux(const T* __restrict__ qlam, int64_t nk, int64_t k0, int64_t n,
-                                                   double h_um, double* __restrict__ q, const int* status) {
+__global__ void __launch_bounds__(256) k_wall_flux_part(const T* __restrict__ qlam, int64_t nk, int64_t k0,
+                                                        int64_t n, double h_um, double2* __restrict__ part,
+                                                        const int* status) {
     if (*status) return;
     const int64_t p = blockIdx.x;
+    const int64_t a = (int64_t)blockIdx.y * FLUX_SPAN, b = min(a + FLUX_SPAN, nk);
     double s = 0.0, c = 0.0;
-    for (int64_t k = threadIdx.x; k < nk; k += blockDim.x) {
+    for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
         const int64_t kg = k0 + k;
         const double w = (kg == 0 || kg == n - 1) ? 0.5 : 1.0;
         const double x = w * (double)qlam[p * nk + k] * h_um;
@@ -181,7 +221,23 @@ __global__ void __launch_bounds__(256) k_wall_flux(const T* __restrict__ qlam, i
         if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) q[p] += red[0];
+    if (threadIdx.x == 0) part[p * gridDim.y + blockIdx.y] = make_double2(red[0], 0.0);
+}
+
+__global__ void __launch_bounds__(32) k_wall_flux_sum(const double2* __restrict__ part, int nparts,
+                                                      double* __restrict__ q, const int* status) {
+    if (*status) return;
+    const int64_t p = blockIdx.x;
+    if (threadIdx.x == 0) {
+        double s = 0.0, c = 0.0;
+        for (int i = 0; i < nparts; ++i) {
+            const double x = part[p * nparts + i].x;
+            const double t = s + x;
+            if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+            s = t;
+        }
+        q[p] += s + c;
+    }
 }
 
 // Tangent slab: directions are split into bundles of at most SLAB_DIRS
@@ -340,16 +396,24 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
     return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
 }
 
+int64_t wall_flux_parts(int64_t nk) { return (nk + FLUX_SPAN - 1) / FLUX_SPAN; }
+
 cudaError_t launch_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const rapral_grid* g, double h,
-                             int64_t k0, int64_t nk, int64_t n_points, double* q) {
+                             int64_t k0, int64_t nk, int64_t n_points, double* q, void* partials) {
     if (n_points == 0) return cudaSuccess;
     const double h_um = h * 1e-3;
+    const int64_t np = wall_flux_parts(nk);
+    double2* part = reinterpret_cast<double2*>(partials);
+    dim3 grid((unsigned)n_points, (unsigned)np);
     if (precision == RAPRAL_FP64)
-        k_wall_flux<double><<<(unsigned)n_points, 256, 0, ctx->stream>>>(
-            reinterpret_cast<const double*>(q_lambda), nk, k0, g->n, h_um, q, ctx->d_status);
+        k_wall_flux_part<double><<<grid, 256, 0, ctx->stream>>>(reinterpret_cast<const double*>(q_lambda), nk, k0,
+                                                                g->n, h_um, part, ctx->d_status);
     else
-        k_wall_flux<float><<<(unsigned)n_points, 256, 0, ctx->stream>>>(
-            reinterpret_cast<const float*>(q_lambda), nk, k0, g->n, h_um, q, ctx->d_status);
+        k_wall_flux_part<float><<<grid, 256, 0, ctx->stream>>>(reinterpret_cast<const float*>(q_lambda), nk, k0,
+                                                               g->n, h_um, part, ctx->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_wall_flux_sum<<<(unsigned)n_points, 32, 0, ctx->stream>>>(part, (int)np, q, ctx->d_status);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     need = arena_need(need, 4 * sizeof(unsigned long long));       // maxima
     need = arena_need(need, 4 * sizeof(int));                      // sorted flag
     need = arena_need(need, (size_t)L * sizeof(LinePrep));
+    need = arena_need(need, (size_t)L * sizeof(LineF32));
     need = arena_need(need, (size_t)C * sizeof(CellPrep));
     need = arena_need(need, (size_t)L * sizeof(int2));
     need = arena_need(need, (size_t)(T + 1) * sizeof(int));
@@ -121,6 +122,7 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     unsigned long long* dmax = ar.take<unsigned long long>(4);
     int* sorted_flag = ar.take<int>(4);
     LinePrep* lp = ar.take<LinePrep>(L);
+    LineF32* lf = ar.take<LineF32>(L);
     CellPrep* cp = ar.take<CellPrep>(C);
     BinPlan plan;
     plan.k0 = k0; plan.nk = nk; plan.tile_w = W; plan.n_tiles = T;
@@ -148,7 +150,7 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     if (e == cudaSuccess) e = cudaMemcpyAsync(sorted_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx.stream);
     if (e == cudaSuccess) e = launch_validate_cells(&ctx, cells);
     if (e == cudaSuccess) e = launch_validate_lines(&ctx, ln, sp->n_species);
-    if (e == cudaSuccess) e = launch_line_prep(&ctx, sp, ln, g->lam_min, h, ph, lp, sorted_flag);
+    if (e == cudaSuccess) e = launch_line_prep(&ctx, sp, ln, g->lam_min, h, ph, lp, lf, sorted_flag);
     if (e == cudaSuccess) e = launch_cell_prep(&ctx, cells, ph, cp, dmax);
     if (e == cudaSuccess) e = launch_bin_bounds(&ctx, ln, lp, cp, dmax, h, &plan);
     if (e == cudaSuccess) e = launch_bin_count(&ctx, ln, g, h, &plan);
@@ -181,10 +183,10 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     e = launch_bin_fill(&ctx, ln, g, h, &plan);
     if (e == cudaSuccess) {
         LineSumArgs a;
-        a.lp = lp; a.cp = cp; a.lnpref = cells->lnpref; a.S = sp->n_species; a.C = C;
+        a.lp = lp; a.lf = lf; a.cp = cp; a.lnpref = cells->lnpref; a.S = sp->n_species; a.C = C;
         a.tile_off = plan.tile_off; a.tile_lines = plan.tile_lines;
         a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk; a.ld = ld; a.tile_w = W;
-        a.kappa = kappa; a.emis = emis; a.status = ctx.d_status; a.stats = ctx.d_stats;
+        a.kappa = kappa; a.emis = emis; a.status = ctx.d_status; a.stats = ctx.d_stats; a.count = 0;
         e = launch_line_sum(&ctx, a, precision, T);
     }
     if (e != cudaSuccess) {

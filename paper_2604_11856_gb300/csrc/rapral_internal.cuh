@@ -32,7 +32,7 @@ inline Phys make_phys(int codata) {
 #define RAPRAL_DOPPLER_HALF (7.16233e-7 / 2.0)
 #define RAPRAL_WINDOW 100.0              // lines reach |dlam| <= 100 lamV
 #define RAPRAL_THIN_F64 4e-4             // |dtau| below which the series is used
-#define RAPRAL_THIN_F32 5e-2
+#define RAPRAL_THIN_F32 0.5               // with seven-term series in FP32
 #define RAPRAL_SLAB_DIRS 17              // directions per tangent-slab bundle
 
 // Status word layout (device int[8]).
@@ -69,6 +69,22 @@ struct __align__(16) LinePrep {
     int32_t pad;
 };
 
+// Compact per-line record of the FP32-chosen path.  The log-space terms are
+// float-float pairs (hi + lo, about 44 significant bits): GB300's FP64 pipe
+// is too narrow to run the per-(line, cell, tile) set-up in FP64, and pair
+// arithmetic in the FP32 pipe keeps the same accuracy.
+struct __align__(16) LineF32 {
+    float2 lnAjg;    // lnAj + ln g_u
+    float2 dAkj;     // lnAk - lnAj
+    float2 Eve_u;    // E_el + E_V of the upper level
+    float2 Er_u;     // E_J of the upper level
+    float2 dEve;     // Eve_u - Eve_l
+    float2 dEr;      // Er_u - Er_l
+    float cD, lamS0, delta;
+    int32_t kc, species;
+    float kcf;       // kc as a float (exact for |kc| < 2^24)
+};
+
 // Per-cell constants.
 struct __align__(16) CellPrep {
     double bve;      // c2 / T_ve
@@ -76,7 +92,28 @@ struct __align__(16) CellPrep {
     double sqrtT;    // sqrt(T_tr)
     double stc;      // (T_ve/1e4)^0.33 (N_e/1e16)
     float bve_f, btr_f, sqrtT_f, stc_f;
+    float2 bve_ff, btr_ff;   // float-float copies of bve, btr
 };
+
+// Float-float arithmetic (a value is hi + lo with |lo| <= ulp(hi)/2).
+__host__ __device__ __forceinline__ float2 ff_from(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb) + a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    const float e = fmaf(a.x, b.x, -p) + (a.x * b.y + a.y * b.x);
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+}
 
 // ---------------------------------------------------------------- context ----
 
@@ -93,6 +130,7 @@ struct rapral_ctx {
     int* d_status = nullptr;
     int* h_pinned = nullptr;    // [16] pinned scratch for small read-backs
     unsigned long long* d_stats = nullptr;   // [4] line-sum work counters
+    int count_work = 1;                      // counters on (rapral_set_counters)
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing events
     char err[512] = {0};
 };
@@ -136,7 +174,8 @@ cudaError_t launch_populations(rapral_ctx* ctx, const rapral_species* sp, const 
                                double* lnpref, const Phys& ph);
 cudaError_t launch_validate_lines(rapral_ctx* ctx, const rapral_lines* ln, int32_t n_species);
 cudaError_t launch_line_prep(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
-                             double lam_min, double h, const Phys& ph, LinePrep* out, int* sorted_flag);
+                             double lam_min, double h, const Phys& ph, LinePrep* out, LineF32* out32,
+                             int* sorted_flag);
 cudaError_t launch_cell_prep(rapral_ctx* ctx, const rapral_cells* cells, const Phys& ph, CellPrep* out,
                              unsigned long long* d_max /*[2]*/);
 
@@ -160,6 +199,7 @@ cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapra
 
 struct LineSumArgs {
     const LinePrep* lp;
+    const LineF32* lf;        // compact records (FP32 path)
     const CellPrep* cp;
     const double* lnpref;     // [C][S]
     int32_t S;
@@ -173,6 +213,7 @@ struct LineSumArgs {
     void* emis;
     const int* status;
     unsigned long long* stats;   // [4] evaluations, gauss, correction, pairs
+    int count;                   // accumulate the work counters (costs conversions per pair)
 };
 cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles);
 
@@ -193,8 +234,10 @@ cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t 
 cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis,
                          int64_t ld, const rapral_grid* g, double h, int64_t k0, int64_t nk, int precision,
                          void* q_lambda, void* I_out, const Phys& ph);
+// Spectral flux: needs `partials` of wall_flux_parts(nk) * n_points * 16 bytes.
+int64_t wall_flux_parts(int64_t nk);
 cudaError_t launch_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const rapral_grid* g,
-                             double h, int64_t k0, int64_t nk, int64_t n_points, double* q);
+                             double h, int64_t k0, int64_t nk, int64_t n_points, double* q, void* partials);
 cudaError_t launch_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* dx, int32_t m,
                              const double* mu, const double* wmu, int32_t n_mu, int32_t normal_ray,
                              int32_t wall_start, int64_t* point_off, int64_t* seg_off, int32_t* seg_cell,

@@ -106,6 +106,7 @@ def load(build_if_missing=True):
             "rapral_workspace_bytes": (i, [i64, i64, i64, P(ct.c_size_t)]),
             "rapral_get_stats": (i, [vp, P(Stats)]),
             "rapral_reset_stats": (i, [vp]),
+            "rapral_set_counters": (i, [vp, i]),
             "rapral_set_profile_events": (i, [vp, vp, vp]),
             "rapral_populations": (i, [vp, P(Species), P(Cells), vp]),
             "rapral_batch_create": (i, [vp, i, P(BatchItem), i, P(vp)]),
@@ -169,6 +170,9 @@ class Context:
         self.check(self.lib.rapral_get_stats(self.h, ct.byref(st)))
         return dict(evaluations=st.evaluations, gauss_terms=st.gauss_terms,
                     correction_terms=st.correction_terms, pairs=st.pairs)
+
+    def set_counters(self, on):
+        self.check(self.lib.rapral_set_counters(self.h, int(bool(on))))
 
     def reset_stats(self):
         self.check(self.lib.rapral_reset_stats(self.h))
