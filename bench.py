@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
     ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch"], default="stagnation",
                     help="stagnation line (the bench line); afterbody / batch: one-off measurements")
+    ap.add_argument("--ab-small", action="store_true",
+                    help="afterbody workload at 100 x 50 cells, 20 points, 2e5 grid points (profiler captures)")
     ap.add_argument("--cells", type=int, default=200,
                     help="cells of the stagnation line (fewer only for profiler captures)")
     return ap.parse_args()
@@ -199,7 +201,10 @@ def run_afterbody(args):
     import torch
     from paper_2604_11856_gb300 import rapral as R
     from paper_2604_11856_gb300 import solver, synth
-    p = synth.afterbody()
+    if args.ab_small:
+        p = synth.afterbody(nx=100, nr=50, n_points=20, n_grid=200_000)
+    else:
+        p = synth.afterbody()
     ctx = R.Context(0)
     ctx2 = R.Context(0, stream=torch.cuda.Stream())
     dp = solver.DeviceProblem(p, ctx)

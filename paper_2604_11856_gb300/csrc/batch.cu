@@ -35,6 +35,7 @@ struct rapral_batch {
     BatchItem* d_items = nullptr;
     unsigned long long* d_counter = nullptr;
     void* d_flux = nullptr;       // partial sums of the spectral integral (largest request)
+    std::vector<void*> d_march;   // FP32 copies of each request's ray data
     int64_t total_units = 0;
     int blocks = 0;
 };
@@ -169,6 +170,8 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     for (int i = 0; i < n_items; ++i)
         flux_bytes = std::max(flux_bytes, (size_t)wall_flux_parts(B->req[i].nk) * (size_t)B->req[i].rays.n_points * 16);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_flux, flux_bytes);
+    B->d_march.assign(n_items, nullptr);
+    for (int i = 0; i < n_items && e == cudaSuccess; ++i) e = cudaMalloc(&B->d_march[i], march_scratch_bytes(&B->req[i].rays));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_items, hitems.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice,
                             ctx->stream);
@@ -202,7 +205,7 @@ int rapral_batch_run(rapral_ctx* ctx, rapral_batch* B) {
     for (int i = 0; i < B->n && e == cudaSuccess; ++i) {
         const BatchReq& r = B->req[i];
         e = launch_march(ctx, &r.rays, r.kappa, r.emis, r.ld, &r.grid, r.h, r.k0, r.nk, RAPRAL_FP32, r.q_lambda,
-                         nullptr, ph);
+                         nullptr, ph, B->d_march[i]);
         if (e == cudaSuccess)
             e = launch_wall_flux(ctx, r.q_lambda, RAPRAL_FP32, &r.grid, r.h, r.k0, r.nk, r.rays.n_points, r.q,
                                  B->d_flux);
@@ -217,6 +220,8 @@ void rapral_batch_destroy(rapral_batch* B) {
     if (B->d_items) cudaFree(B->d_items);
     if (B->d_counter) cudaFree(B->d_counter);
     if (B->d_flux) cudaFree(B->d_flux);
+    for (void* p : B->d_march)
+        if (p) cudaFree(p);
     delete B;
 }
 

@@ -412,22 +412,73 @@ __device__ __noinline__ void exact_edges(const LinePrep& L, const CellPrep& cp, 
     *khi = hi;
 }
 
+// Conversion-free helpers for the FP32 set-up.  On GB300 float/integer
+// conversions and roundings share the narrow FP64 pipe, so the set-up keeps
+// to FMA-pipe arithmetic and MUFU ex2 / rcp.
+
+// Nearest integer of |x| < 2^22 (adding and removing 1.5 * 2^23).
+__device__ __forceinline__ float round_near(float x) { return (x + 12582912.0f) - 12582912.0f; }
+__device__ __forceinline__ float floor_f(float x) { const float n = round_near(x); return n > x ? n - 1.0f : n; }
+__device__ __forceinline__ float ceil_f(float x) { const float n = round_near(x); return n < x ? n + 1.0f : n; }
+
+// e^y for y = hi + lo: t = y log2(e) (float-float), t = n + f with n the
+// nearest integer, 2^f and 2^n by MUFU ex2.
+__device__ __forceinline__ float exp_ff(float2 y) {
+    const float2 t = ff_mul(y, make_float2(1.4426950216293335f, 1.925963033500011e-08f));
+    const float n = round_near(t.x);
+    return ex2_approx((t.x - n) + t.y) * ex2_approx(n);
+}
+
+// e^z - 1 for z <= 0: Taylor series through z^9 for z > -1/2 (error below
+// 3e-10 relative), else 2^(z log2 e) - 1 (|result| >= 0.39).
+__device__ __forceinline__ float expm1_neg(float z) {
+    if (z > -0.5f) {
+        float p = 1.0f / 362880.0f;
+        p = fmaf(p, z, 1.0f / 40320.0f);
+        p = fmaf(p, z, 1.0f / 5040.0f);
+        p = fmaf(p, z, 1.0f / 720.0f);
+        p = fmaf(p, z, 1.0f / 120.0f);
+        p = fmaf(p, z, 1.0f / 24.0f);
+        p = fmaf(p, z, 1.0f / 6.0f);
+        p = fmaf(p, z, 0.5f);
+        p = fmaf(p, z, 1.0f);
+        return p * z;
+    }
+    return ex2_approx(z * 1.44269504f) - 1.0f;
+}
+
+// sin(pi d) for |d| <= 1: sin(pi a) = sin(pi (1 - a)) maps |d| to [0, 1/2],
+// then the Taylor series of sin(pi x) through x^13 (error below 1e-9).
+__device__ __forceinline__ float sinpi_series(float d) {
+    const float a = fabsf(d);
+    const float x = a > 0.5f ? 1.0f - a : a;
+    const float z = x * x;
+    float p = 4.663027939386666e-4f;
+    p = fmaf(p, z, -7.37043097615242e-3f);
+    p = fmaf(p, z, 8.214588463306427e-2f);
+    p = fmaf(p, z, -0.5992645025253296f);
+    p = fmaf(p, z, 2.550163984298706f);
+    p = fmaf(p, z, -5.167712688446045f);
+    p = fmaf(p, z, 3.1415927410125732f);
+    return copysignf(x * p, d);
+}
+
 // One (line, cell) pair set up for a warp's tile [kt0, kt0 + TW): window
-// offsets inside the tile, u at the tile's first point, profile constants,
-// and whether every point of the window part in the tile lies in the far
-// wings (|u| > 11, where both exponentials are zero in FP32).  Everything a
-// warp needs per pair is computed here, by one lane per pair.
+// offsets inside the tile (as floats), u at the tile's first point, profile
+// constants, and whether every point of the window part in the tile lies in
+// the far wings (|u| > 11, where both exponentials are zero in FP32: then s
+// is stored negated).  Everything a warp needs per pair is computed here, by
+// one lane per pair.
 struct PairF32 {
-    int rel;          // (klo - kt0) | (khi - kt0) << 16
-    int far;
+    float lo, hi;     // window part inside the tile, offsets from kt0
     float ub, ub_lo;  // signed u at kt0, (kt0 - kc) s - u0, as a float-float pair
-    float s;          // h / (2 lamV): step of u per grid point
+    float s;          // h / (2 lamV): step of u per grid point (negative: far wings only)
     float r, aj, ak;
 };
 
 __device__ __forceinline__ bool setup_pair_f32(const LineF32& L, const CellPrep& cp, float2 lp, int line,
-                                               const LinePrep* lp64, double lam_min, double h, float hf, int kt0,
-                                               int kt1, float kt0f, float kt1f, bool count, PairF32* P,
+                                               const LinePrep* lp64, double lam_min, double h, float hf, float inv_hf,
+                                               int kt0, float kt0f, float kt1f, bool count, PairF32* P,
                                                int64_t* cnt) {
     if (!(lp.x > -INFINITY)) return false;
     // widths first: most candidates of a tile list miss the tile in a given cell
@@ -435,69 +486,76 @@ __device__ __forceinline__ bool setup_pair_f32(const LineF32& L, const CellPrep&
     const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc_f;
     const float sum = lamL + lamG;
     {   // lamV <= lamL + lamG: cheap rejection before the Voigt fit
-        const float wmax = (float)RAPRAL_WINDOW * sum / hf * 1.0001f + 1.0f;
+        const float wmax = (float)RAPRAL_WINDOW * sum * inv_hf * 1.0001f + 1.0f;
         if (kt1f - L.kcf < L.delta - wmax || kt0f - L.kcf > L.delta + wmax) return false;
     }
-    const float d = (lamL - lamG) / sum;
+    const float d = (lamL - lamG) * rcp_approx(sum);
     const float F = 1.0f - 0.18121f * (1.0f - d * d) -
-                    (0.023665f * expf(0.6f * d) + 0.00418f * expf(-1.9f * d)) * sinpif(d);
+                    (0.023665f * ex2_approx(0.6f * 1.44269504f * d) + 0.00418f * ex2_approx(-1.9f * 1.44269504f * d)) *
+                        sinpi_series(d);
     const float lamV = F * sum;
-    const float wpts = (float)RAPRAL_WINDOW * lamV / hf;
+    const float wpts = (float)RAPRAL_WINDOW * lamV * inv_hf;
     const float hi = L.delta + wpts, lo = L.delta - wpts;
-    const float fhi = floorf(hi), clo = ceilf(lo);
-    int64_t khi = (int64_t)L.kc + __float2int_rd(hi);
-    int64_t klo = (int64_t)L.kc + __float2int_ru(lo);
+    const float fhi = floor_f(hi), clo = ceil_f(lo);
+    // window in offsets from kt0 (exact: integers below 2^24)
+    float lo_rel = L.kcf + clo - kt0f, hi_rel = L.kcf + fhi - kt0f;
     const float m = 2e-6f * wpts + 2e-3f;
-    if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m)
+    if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m) {
+        int64_t klo = (int64_t)L.kc + (int64_t)clo, khi = (int64_t)L.kc + (int64_t)fhi;
         exact_edges(lp64[line], cp, lam_min, h, &klo, &khi);
-    klo = max(klo, (int64_t)kt0);
-    khi = min(khi, (int64_t)kt1);
-    if (klo > khi) return false;
+        lo_rel = (float)(klo - kt0);
+        hi_rel = (float)(khi - kt0);
+    }
+    lo_rel = fmaxf(lo_rel, 0.0f);
+    hi_rel = fminf(hi_rel, kt1f - kt0f);
+    if (lo_rel > hi_rel) return false;
     // strengths: ln S_j = lnAj + ln g_u + ln(N_s/Z_s) - (E_el + E_V)_u c2/T_ve - E_J,u c2/T_tr
     // and x = ln(N_l g_u / (N_u g_l)) = dE_ve c2/T_ve + dE_J c2/T_tr, in float-float
     const float2 yj = ff_add(ff_add(L.lnAjg, lp), ff_neg(ff_add(ff_mul(L.Eve_u, cp.bve_ff), ff_mul(L.Er_u, cp.btr_ff))));
     const float2 x = ff_add(ff_mul(L.dEve, cp.bve_ff), ff_mul(L.dEr, cp.btr_ff));
-    const float Sj = expf(yj.x) * (1.0f + yj.y);
+    const float Sj = exp_ff(yj);
     float2 yk = ff_add(yj, L.dAkj);
     float fk;
     if (x.x >= 0.0f) {           // kappa0 = e^{lnAk + ln N_l g_u/g_l} (1 - e^{-x})
         yk = ff_add(yk, x);
-        fk = -expm1f(-x.x);
+        fk = -expm1_neg(-x.x);
     } else {                     // kappa0 = e^{lnAk + ln N_u} (e^{x} - 1)
-        fk = expm1f(x.x);
+        fk = expm1_neg(x.x);
     }
-    const float Sk = expf(yk.x) * (1.0f + yk.y) * fk;
+    const float Sk = exp_ff(yk) * fk;
     if (!(Sj > 0.0f) && Sk == 0.0f) return false;
-    const float r = lamL / lamV;
-    const float pre = 1e3f / (2.0f * lamV * (1.065f + 0.447f * r + 0.058f * r * r));
-    const int lo_rel = (int)(klo - kt0), hi_rel = (int)(khi - kt0);
-    P->rel = lo_rel | (hi_rel << 16);
-    P->s = 0.5f * hf / lamV;
-    const float u0 = L.delta * P->s;                 // u of the centre's offset from kc
+    const float iv = rcp_approx(lamV);
+    const float r = lamL * iv;
+    const float pre = 1e3f * 0.5f * iv * rcp_approx(1.065f + 0.447f * r + 0.058f * r * r);
+    const float s = 0.5f * hf * iv;
+    const float u0 = L.delta * s;                    // u of the centre's offset from kc
     {   // signed u at kt0 without rounding loss: (kt0 - kc) is exact, its
         // product with s and the sum with -u0 are split into hi + lo
         const float dk = kt0f - L.kcf;
-        const float p = dk * P->s;
-        const float pe = fmaf(dk, P->s, -p);
-        const float hi = p - u0;
-        const float bb = hi - p;
-        const float e = (p - (hi - bb)) + (-u0 - bb);
-        P->ub = hi;
+        const float p = dk * s;
+        const float pe = fmaf(dk, s, -p);
+        const float uh = p - u0;
+        const float bb = uh - p;
+        const float e = (p - (uh - bb)) + (-u0 - bb);
+        P->ub = uh;
         P->ub_lo = e + pe;
     }
-    // smallest |u| over the evaluated part [klo, khi] of the tile
-    const float ua = fmaf((float)lo_rel, P->s, P->ub), ue = fmaf((float)hi_rel, P->s, P->ub);
+    // smallest |u| over the evaluated part of the tile
+    const float ua = fmaf(lo_rel, s, P->ub), ue = fmaf(hi_rel, s, P->ub);
     const float umin = (ua > 0.0f) ? ua : (ue < 0.0f ? -ue : 0.0f);
-    P->far = umin > 11.0f;
+    P->lo = lo_rel;
+    P->hi = hi_rel;
+    P->s = umin > 11.0f ? -s : s;
     P->r = r;
     P->aj = Sj * pre;
     P->ak = Sk * pre;
     if (count) {
         // work counters: points in the window; those where the Gaussian core and
         // the exponential correction are above the FP32 underflow limits
+        const int64_t klo = kt0 + (int64_t)lo_rel, khi = kt0 + (int64_t)hi_rel;
         cnt[0] += khi - klo + 1;
         const float kcen = L.kcf + L.delta;
-        const float hg = 5.6125f / P->s, hc = 10.95f / P->s;   // u^2 < 31.5, u^2.25 < 218
+        const float hg = 5.6125f / s, hc = 10.95f / s;   // u^2 < 31.5, u^2.25 < 218
         cnt[1] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hg)) - max(klo, (int64_t)ceilf(kcen - hg)) + 1);
         cnt[2] += max((int64_t)0, min(khi, (int64_t)floorf(kcen + hc)) - max(klo, (int64_t)ceilf(kcen - hc)) + 1);
         cnt[3] += 1;
@@ -556,6 +614,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     }
     const CellPrep cp = a.cp[c];
     const float hf = (float)a.h;
+    const float inv_hf = (float)(1.0 / a.h);
     const bool count = a.count != 0;
     if (lane < a.S) {   // the cell's ln(N_s / Z_s) as float-float pairs
         const double v = a.lnpref[c * a.S + lane];
@@ -570,30 +629,29 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
         if (lane < nb) {
             const int l = a.tile_lines[b + lane];
             const LineF32 L = a.lf[l];
-            valid = setup_pair_f32(L, cp, smlp[L.species], l, a.lp, a.lam_min, a.h, hf, kt0, kt1, kt0f, kt1f, count,
-                                   &P, cnt);
+            valid = setup_pair_f32(L, cp, smlp[L.species], l, a.lp, a.lam_min, a.h, hf, inv_hf, kt0, kt0f, kt1f,
+                                   count, &P, cnt);
         }
         // compact the pairs that reach the tile to the front of the staging area
         const unsigned vmask = __ballot_sync(0xffffffffu, valid);
         const int nv = __popc(vmask);
         if (valid) {
             const int pos = __popc(vmask & ((1u << lane) - 1u));
-            sm0[pos] = make_float4(__int_as_float(P.rel), __int_as_float(P.far), P.ub, P.s);
+            sm0[pos] = make_float4(P.lo, P.hi, P.ub, P.s);
             sm1[pos] = make_float4(P.r, P.ub_lo, P.aj, P.ak);
         }
         __syncwarp();
         for (int q = 0; q < nv; ++q) {
             const float4 A = sm0[q];
-            const int rel = __float_as_int(A.x);
-            const int i0 = max((rel & 0xffff) - lp0, 0);
-            const int i1 = min((rel >> 16) - lp0, PPT - 1);
+            const float i0 = fmaxf(A.x - lpf, 0.0f);
+            const float i1 = fminf(A.y - lpf, (float)(PPT - 1));
             if (i0 > i1) continue;
             const float4 B = sm1[q];
-            const float s = A.w, r = B.x, aj = B.z, ak = B.w;
+            const float s = fabsf(A.w), r = B.x, aj = B.z, ak = B.w;
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
             const float x0 = fmaf(lpf, s, A.z) + B.y;   // signed u of the lane's first point
-            if (__float_as_int(A.y)) {                // far wings only (uniform over the warp)
-                if (i0 == 0 && i1 == PPT - 1) {
+            if (A.w < 0.0f) {                           // far wings only (uniform over the warp)
+                if (i0 == 0.0f && i1 == (float)(PPT - 1)) {
 #pragma unroll
                     for (int i = 0; i < PPT; ++i) {
                         const float br = whiting_bracket<true>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
@@ -603,7 +661,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
                 } else {
 #pragma unroll
                     for (int i = 0; i < PPT; ++i)
-                        if (i >= i0 && i <= i1) {
+                        if ((float)i >= i0 && (float)i <= i1) {
                             const float br = whiting_bracket<true>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
                             bj[i] = fmaf(aj, br, bj[i]);
                             bk[i] = fmaf(ak, br, bk[i]);
@@ -612,7 +670,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
             } else {
 #pragma unroll
                 for (int i = 0; i < PPT; ++i)
-                    if (i >= i0 && i <= i1) {
+                    if ((float)i >= i0 && (float)i <= i1) {
                         const float br = whiting_bracket<false>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
                         bj[i] = fmaf(aj, br, bj[i]);
                         bk[i] = fmaf(ak, br, bk[i]);

@@ -11,6 +11,8 @@
 // registers) with the far/near coefficients of the linear-emission integral.
 // The weighted directions are summed per thread; slices are combined in
 // shared memory in a fixed order, so results do not depend on timing.
+#include <algorithm>
+
 #include "rapral_internal.cuh"
 
 namespace {
@@ -93,6 +95,9 @@ struct MarchArgs {
     const int64_t* dir_off;
     const double* dir_scale;
     const double* dir_weight;
+    const float* seg_ds_f;       // FP32 copies (FP32 march only): no conversion per
+    const float* dir_scale_f;    // (segment, direction, wavelength)
+    const float* dir_weight_f;
     const int32_t* bundle_wall;
     double T_wall;
     const void* kappa;
@@ -105,6 +110,18 @@ struct MarchArgs {
     Phys ph;
     const int* status;
 };
+
+template <class T> __device__ __forceinline__ T seg_len(const MarchArgs& a, int64_t i);
+template <> __device__ __forceinline__ double seg_len<double>(const MarchArgs& a, int64_t i) { return a.seg_ds[i]; }
+template <> __device__ __forceinline__ float seg_len<float>(const MarchArgs& a, int64_t i) { return a.seg_ds_f[i]; }
+template <class T> __device__ __forceinline__ T dir_val(const double* d, const float* f, int64_t i);
+template <> __device__ __forceinline__ double dir_val<double>(const double* d, const float*, int64_t i) { return d[i]; }
+template <> __device__ __forceinline__ float dir_val<float>(const double*, const float* f, int64_t i) { return f[i]; }
+
+__global__ void k_to_float(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
 
 // Planck intensity, temperature form (Sec. 2.2), W/cm^2/sr/um.
 __device__ __forceinline__ double planck(double lam_nm, double T, const Phys& ph) {
@@ -129,7 +146,9 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
     for (int64_t b = a.point_off[p] + slice; b < a.point_off[p + 1]; b += SL) {
         const int64_t d0 = a.dir_off[b];
         const int nd = (int)(a.dir_off[b + 1] - d0);
-        T I[MAXD];
+        T I[MAXD], sc[MAXD];
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) sc[d] = d < nd ? dir_val<T>(a.dir_scale, a.dir_scale_f, d0 + d) : T(0);
         T I0 = T(0);
         if (a.bundle_wall[b]) I0 = (T)planck(a.lam_min + (double)(a.k0 + kcol) * a.h, a.T_wall, a.ph);
 #pragma unroll
@@ -151,13 +170,13 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
                 } else {
                     kn = kc; jn = jc;
                 }
-                const T ds = (T)a.seg_ds[i];
+                const T ds = seg_len<T>(a, i);
                 const T inv_k = T(1) / kf;
 #pragma unroll
                 for (int d = 0; d < MAXD; ++d) {
                     if (d < nd) {
                         T e, ca, cb;
-                        seg_coeffs(kf, ds * (T)a.dir_scale[d0 + d], inv_k, &e, &ca, &cb);
+                        seg_coeffs(kf, ds * sc[d], inv_k, &e, &ca, &cb);
                         I[d] = I[d] * e + ca * jf + cb * jn;
                     }
                 }
@@ -169,7 +188,7 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
 #pragma unroll
         for (int d = 0; d < MAXD; ++d) {
             if (d < nd) {
-                part += (T)a.dir_weight[d0 + d] * I[d];
+                part += dir_val<T>(a.dir_weight, a.dir_weight_f, d0 + d) * I[d];
                 if (a.I_out && active) reinterpret_cast<T*>(a.I_out)[(d0 + d) * a.nk + kk] = I[d];
             }
         }
@@ -381,18 +400,37 @@ cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t 
     return cudaGetLastError();
 }
 
+size_t march_scratch_bytes(const rapral_rays* r) {
+    return (size_t)(r->n_segments + 2 * r->n_dirs) * sizeof(float) + 1024;
+}
+
 cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis, int64_t ld,
                          const rapral_grid* g, double h, int64_t k0, int64_t nk, int precision, void* q_lambda,
-                         void* I_out, const Phys& ph) {
+                         void* I_out, const Phys& ph, void* scratch) {
     MarchArgs a;
     a.point_off = r->point_off; a.seg_off = r->seg_off; a.seg_cell = r->seg_cell; a.seg_ds = r->seg_ds;
     a.dir_off = r->dir_off; a.dir_scale = r->dir_scale; a.dir_weight = r->dir_weight;
+    a.seg_ds_f = nullptr; a.dir_scale_f = nullptr; a.dir_weight_f = nullptr;
     a.bundle_wall = r->bundle_wall; a.T_wall = r->T_wall;
     a.kappa = kappa; a.emis = emis; a.ld = ld;
     a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk;
     a.q_lambda = q_lambda; a.I_out = I_out; a.ph = ph; a.status = ctx->d_status;
     if (precision == RAPRAL_FP64)
         return march_t<double>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
+    // FP32 copies of the path lengths, direction scales and weights
+    float* f = reinterpret_cast<float*>(scratch);
+    float* fd = f + ((r->n_segments + 63) / 64) * 64;
+    float* fw = fd + ((r->n_dirs + 63) / 64) * 64;
+    if (r->n_segments > 0)
+        k_to_float<<<(unsigned)std::min<int64_t>(div_up(r->n_segments, 256), 4096), 256, 0, ctx->stream>>>(
+            r->seg_ds, r->n_segments, f);
+    if (r->n_dirs > 0) {
+        k_to_float<<<(unsigned)std::min<int64_t>(div_up(r->n_dirs, 256), 4096), 256, 0, ctx->stream>>>(
+            r->dir_scale, r->n_dirs, fd);
+        k_to_float<<<(unsigned)std::min<int64_t>(div_up(r->n_dirs, 256), 4096), 256, 0, ctx->stream>>>(
+            r->dir_weight, r->n_dirs, fw);
+    }
+    a.seg_ds_f = f; a.dir_scale_f = fd; a.dir_weight_f = fw;
     return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
 }
 

@@ -231,9 +231,12 @@ cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const Ba
 
 // Rays
 cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells);
+// FP32 march needs march_scratch_bytes(r) of scratch for FP32 copies of the
+// ray lengths, direction scales and weights.
+size_t march_scratch_bytes(const rapral_rays* r);
 cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis,
                          int64_t ld, const rapral_grid* g, double h, int64_t k0, int64_t nk, int precision,
-                         void* q_lambda, void* I_out, const Phys& ph);
+                         void* q_lambda, void* I_out, const Phys& ph, void* scratch);
 // Spectral flux: needs `partials` of wall_flux_parts(nk) * n_points * 16 bytes.
 int64_t wall_flux_parts(int64_t nk);
 cudaError_t launch_wall_flux(rapral_ctx* ctx, const void* q_lambda, int precision, const rapral_grid* g,
