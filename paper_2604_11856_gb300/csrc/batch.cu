@@ -171,7 +171,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         flux_bytes = std::max(flux_bytes, (size_t)wall_flux_parts(B->req[i].nk) * (size_t)B->req[i].rays.n_points * 16);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_flux, flux_bytes);
     B->d_march.assign(n_items, nullptr);
-    for (int i = 0; i < n_items && e == cudaSuccess; ++i) e = cudaMalloc(&B->d_march[i], march_scratch_bytes(&B->req[i].rays));
+    for (int i = 0; i < n_items && e == cudaSuccess; ++i) e = cudaMalloc(&B->d_march[i], march_scratch_bytes(&B->req[i].rays, B->req[i].nk, RAPRAL_FP32));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_items, hitems.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice,
                             ctx->stream);

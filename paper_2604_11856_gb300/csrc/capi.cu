@@ -346,10 +346,8 @@ int rapral_trace_rays(rapral_ctx* ctx, const rapral_rays* rays, int64_t n_cells,
     if (rays->bundle_wall && !(rays->T_wall >= 0.0)) return set_error(ctx, RAPRAL_EINVAL, "T_wall");
     cudaSetDevice(ctx->device);
     const Phys ph = make_phys(ctx->codata);
-    if (precision == RAPRAL_FP32) {
-        st = ws_reserve(ctx, march_scratch_bytes(rays));
-        if (st) return st;
-    }
+    st = ws_reserve(ctx, march_scratch_bytes(rays, nk, precision));
+    if (st) return st;
     cudaError_t e = launch_validate_rays(ctx, rays, n_cells);
     if (e == cudaSuccess)
         e = launch_march(ctx, rays, kappa, emis, ld, g, grid_h(g), k0, nk, precision, q_lambda, I_out, ph, ctx->ws);

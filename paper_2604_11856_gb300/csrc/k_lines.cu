@@ -499,8 +499,16 @@ __device__ __forceinline__ bool setup_pair_f32(const LineF32& L, const CellPrep&
     const float fhi = floor_f(hi), clo = ceil_f(lo);
     // window in offsets from kt0 (exact: integers below 2^24)
     float lo_rel = L.kcf + clo - kt0f, hi_rel = L.kcf + fhi - kt0f;
-    const float m = 2e-6f * wpts + 2e-3f;
-    if (hi - fhi < m || fhi + 1.0f - hi < m || clo - lo < m || lo - (clo - 1.0f) < m) {
+    // Certification.  The FP32 edge positions are within 1.2e-6 wpts + 6e-8
+    // grid units of the exact ones (lamV to 9e-7 relative through widths,
+    // the Voigt fit, ex2 and the sin series; wpts and the sums to a few more
+    // roundings).  Only an edge that lies inside this tile and within m of a
+    // grid point is decided again in FP64.
+    const float m = 1.5e-6f * wpts + 1e-6f;
+    const float span = kt1f - kt0f;
+    const bool lo_in = lo_rel >= -1.0f && lo_rel <= span + 1.0f;
+    const bool hi_in = hi_rel >= -1.0f && hi_rel <= span + 1.0f;
+    if ((hi_in && (hi - fhi < m || fhi + 1.0f - hi < m)) || (lo_in && (clo - lo < m || lo - (clo - 1.0f) < m))) {
         int64_t klo = (int64_t)L.kc + (int64_t)clo, khi = (int64_t)L.kc + (int64_t)fhi;
         exact_edges(lp64[line], cp, lam_min, h, &klo, &khi);
         lo_rel = (float)(klo - kt0);

@@ -24,7 +24,8 @@ namespace {
 //   FP32: |dtau| < 0.5 takes seven terms (truncation <= 4e-7 relative), so
 //   the closed form is used only where 1 - e >= 0.39 and an approximate ex2
 //   for e keeps FP32 accuracy without expm1f.
-__device__ __forceinline__ void seg_coeffs(double kap, double s, double inv_k, double* e, double* ca, double* cb) {
+__device__ __forceinline__ void seg_coeffs(double kap, double s, double inv_k, double /*inv_s*/, double* e,
+                                           double* ca, double* cb) {
     const double dtau = kap * s;
     const double em1 = expm1(-dtau);   // e^{-dtau} - 1
     *e = 1.0 + em1;
@@ -44,7 +45,8 @@ __device__ __forceinline__ float ex2f_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ void seg_coeffs(float kap, float s, float inv_k, float* e, float* ca, float* cb) {
+__device__ __forceinline__ void seg_coeffs(float kap, float s, float inv_k, float inv_s, float* e, float* ca,
+                                           float* cb) {
     const float dtau = kap * s;
     *e = ex2f_approx(-1.44269504f * dtau);
     if (fabsf(dtau) < (float)RAPRAL_THIN_F32) {
@@ -66,10 +68,59 @@ __device__ __forceinline__ void seg_coeffs(float kap, float s, float inv_k, floa
         *ca = s * pa;
         *cb = s * pb;
     } else {
-        const float f = (1.0f - *e) / dtau;
+        const float f = (1.0f - *e) * (inv_k * inv_s);   // (1 - e) / dtau
         *ca = (f - *e) * inv_k;
         *cb = (1.0f - f) * inv_k;
     }
+}
+
+__device__ __forceinline__ float recip(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// The same coefficients for one direction per segment: the closed form takes
+// a single reciprocal, of dtau, inside its branch (1/kappa = s / dtau).
+__device__ __forceinline__ void seg_coeffs1(double kap, double s, double* e, double* ca, double* cb) {
+    seg_coeffs(kap, s, 1.0 / kap, 0.0, e, ca, cb);
+}
+// One segment of the march for one direction: I <- I e + ca j_far + cb j_near.
+// FP32 folds the common factor of ca and cb (s, or s / dtau) into one
+// multiply: I e + m (a j_far + b j_near).
+__device__ __forceinline__ void seg_step(double& I, double kf, double s, double jf, double jn) {
+    double e, ca, cb;
+    seg_coeffs1(kf, s, &e, &ca, &cb);
+    I = I * e + ca * jf + cb * jn;
+}
+__device__ __forceinline__ void seg_step(float& I, float kf, float s, float jf, float jn) {
+    const float dtau = kf * s;
+    const float e = ex2f_approx(-1.44269504f * dtau);
+    float pa, pb, m;
+    if (fabsf(dtau) < (float)RAPRAL_THIN_F32) {
+        const float t = dtau;
+        pa = fmaf(t, 1.0f / 5760.0f, -1.0f / 840.0f);
+        pa = fmaf(t, pa, 1.0f / 144.0f);
+        pa = fmaf(t, pa, -1.0f / 30.0f);
+        pa = fmaf(t, pa, 0.125f);
+        pa = fmaf(t, pa, -1.0f / 3.0f);
+        pa = fmaf(t, pa, 0.5f);
+        pb = fmaf(t, 1.0f / 40320.0f, -1.0f / 5040.0f);
+        pb = fmaf(t, pb, 1.0f / 720.0f);
+        pb = fmaf(t, pb, -1.0f / 120.0f);
+        pb = fmaf(t, pb, 1.0f / 24.0f);
+        pb = fmaf(t, pb, -1.0f / 6.0f);
+        pb = fmaf(t, pb, 0.5f);
+        m = s;
+    } else {
+        const float r = recip(dtau);
+        const float f = (1.0f - e) * r;
+        pa = f - e;
+        pb = 1.0f - f;
+        m = s * r;
+    }
+    I = fmaf(m, fmaf(pa, jf, pb * jn), I * e);
 }
 
 __global__ void k_validate_rays(const int32_t* seg_cell, const double* seg_ds, int64_t nseg, int64_t C,
@@ -100,6 +151,7 @@ struct MarchArgs {
     const float* dir_weight_f;
     const int32_t* bundle_wall;
     double T_wall;
+    const void* wall_row;        // Planck intensity at T_wall per column (k_march_rays; null: T_wall = 0)
     const void* kappa;
     const void* emis;
     int64_t ld;
@@ -146,9 +198,12 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
     for (int64_t b = a.point_off[p] + slice; b < a.point_off[p + 1]; b += SL) {
         const int64_t d0 = a.dir_off[b];
         const int nd = (int)(a.dir_off[b + 1] - d0);
-        T I[MAXD], sc[MAXD];
+        T I[MAXD], sc[MAXD], isc[MAXD];
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) sc[d] = d < nd ? dir_val<T>(a.dir_scale, a.dir_scale_f, d0 + d) : T(0);
+        for (int d = 0; d < MAXD; ++d) {
+            sc[d] = d < nd ? dir_val<T>(a.dir_scale, a.dir_scale_f, d0 + d) : T(1);
+            isc[d] = recip(sc[d]);
+        }
         T I0 = T(0);
         if (a.bundle_wall[b]) I0 = (T)planck(a.lam_min + (double)(a.k0 + kcol) * a.h, a.T_wall, a.ph);
 #pragma unroll
@@ -171,12 +226,13 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
                     kn = kc; jn = jc;
                 }
                 const T ds = seg_len<T>(a, i);
-                const T inv_k = T(1) / kf;
+                const T inv_k = recip(kf);
+                const T inv_ds = recip(ds);
 #pragma unroll
                 for (int d = 0; d < MAXD; ++d) {
                     if (d < nd) {
                         T e, ca, cb;
-                        seg_coeffs(kf, ds * sc[d], inv_k, &e, &ca, &cb);
+                        seg_coeffs(kf, ds * sc[d], inv_k, inv_ds * isc[d], &e, &ca, &cb);
                         I[d] = I[d] * e + ca * jf + cb * jn;
                     }
                 }
@@ -209,6 +265,177 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a) {
         T s = red[lane];
         for (int q = 1; q < SL; ++q) s += red[q * LW + lane];
         reinterpret_cast<T*>(a.q_lambda)[p * a.nk + kk] = s;
+    }
+}
+
+// Single-direction bundles (each ray with its own path, as in the
+// axisymmetric geometry): one warp marches one bundle over V x 32
+// wavelengths, lane l taking columns l, l + 32, ..., so each gather of a
+// segment is V coalesced row reads and the per-segment work (next cell,
+// path length, row address) is shared by V wavelengths.  The warp stages
+// the next cell's row address and the scaled length of 32 segments at a time
+// in shared memory (one coalesced read of the segment list), so no kappa / j
+// gather waits on a dependent load of the list; the last segment of a ray,
+// whose near node is its own cell, is taken outside the loop.  A point's
+// bundles are split over 2^lgG blocks (groups) and, within a block,
+// round-robin over its eight warps; each warp Kahan-sums its bundles, the
+// warps are added in a fixed order, and the groups' partial spectral fluxes
+// are added in group order by k_group_sum.  The last wavelength tile is
+// shifted back to end at nk (its columns below the tile are computed again
+// and not written), so every load is in bounds without a per-lane clamp; the
+// launcher takes V = 1 when nk < 32 V.
+template <class T> struct __align__(16) SegStage {
+    const char* row;   // kappa row of the segment's next cell
+    T ds;              // path length x direction scale
+};
+
+#ifndef RAPRAL_MARCH_UNROLL
+#define RAPRAL_MARCH_UNROLL 3
+#endif
+constexpr int kUnroll = RAPRAL_MARCH_UNROLL;
+#ifndef RAPRAL_MARCH_MINB
+#define RAPRAL_MARCH_MINB 4
+#endif
+template <class T, int V>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? RAPRAL_MARCH_MINB : 1)
+    k_march_rays(MarchArgs a, int lgG, T* __restrict__ part) {
+    if (*a.status) return;
+    constexpr int W = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // columns fit in int: nk <= 32 x 65535 (checked by the caller)
+    const int nk = (int)a.nk;
+    const int tile0 = (int)blockIdx.y * (32 * V);
+    const int base = (V > 1 && tile0 + 32 * V > nk) ? nk - 32 * V : tile0;
+    const int col0 = (V == 1 && base + lane >= nk) ? nk - 1 : base + lane;
+    // byte addressing: row of cell c at kbase + c ldb; this lane's kappa and
+    // j columns at offK, offJ from it
+    const char* kbase = reinterpret_cast<const char*>(a.kappa);
+    const int64_t ldb = a.ld * (int64_t)sizeof(T);
+    const int64_t offK = (int64_t)col0 * sizeof(T);
+    const int64_t offJ = (reinterpret_cast<const char*>(a.emis) - kbase) + offK;
+    __shared__ SegStage<T> stage_all[W][33];
+    SegStage<T>* stage = stage_all[warp];
+    T acc[V], comp[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = comp[v] = T(0);
+    // G = 2^lgG groups of point p = blockIdx.x >> lgG; group g takes every
+    // G-th run of W bundles, warp w the w-th bundle of each run
+    const unsigned p = blockIdx.x >> lgG, grp = blockIdx.x & ((1u << lgG) - 1u);
+    const int64_t b1 = a.point_off[p + 1];
+    for (int64_t b = a.point_off[p] + (int64_t)grp * W + warp; b < b1; b += (int64_t)W << lgG) {
+        const int64_t d0 = a.dir_off[b];
+        if (a.dir_off[b + 1] == d0) continue;
+        const T sc = dir_val<T>(a.dir_scale, a.dir_scale_f, d0);
+        T I[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) I[v] = T(0);
+        if (a.wall_row && a.bundle_wall[b]) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) I[v] = reinterpret_cast<const T*>(a.wall_row)[col0 + 32 * v];
+        }
+        const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
+        if (s1 > s0) {
+            T kc[V], jc[V], kf[V], jf[V];
+            {
+                const char* row = kbase + (int64_t)a.seg_cell[s0] * ldb;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    kc[v] = kf[v] = *reinterpret_cast<const T*>(row + offK + 32 * v * sizeof(T));
+                    jc[v] = jf[v] = *reinterpret_cast<const T*>(row + offJ + 32 * v * sizeof(T));
+                }
+            }
+            // every segment but the last has a next cell: stage (row of the
+            // next cell, scaled length) for 32 segments, read back by all lanes
+            for (int64_t g = s0; g < s1 - 1; g += 32) {
+                const int64_t mine = g + lane;
+                __syncwarp();
+                // entries past the chunk point at row 0 (a valid row), so the
+                // prefetch of entry j + 1 below never leaves the arrays
+                const bool in = mine < s1 - 1;
+                stage[lane].row = in ? kbase + (int64_t)a.seg_cell[mine + 1] * ldb : kbase;
+                stage[lane].ds = in ? seg_len<T>(a, mine) * sc : T(0);
+                if (lane == 0) stage[32].row = kbase;
+                __syncwarp();
+                const int n = s1 - 1 - g < 32 ? (int)(s1 - 1 - g) : 32;
+                T kx[V], jx[V];
+                {
+                    const char* r0 = stage[0].row;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        kx[v] = *reinterpret_cast<const T*>(r0 + offK + 32 * v * sizeof(T));
+                        jx[v] = *reinterpret_cast<const T*>(r0 + offJ + 32 * v * sizeof(T));
+                    }
+                }
+#pragma unroll kUnroll
+                for (int j = 0; j < n; ++j) {
+                    const T ds = stage[j].ds;
+                    const char* rn = stage[j + 1].row;
+                    T ky[V], jy[V];   // next segment's next cell, loaded a step ahead
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        ky[v] = *reinterpret_cast<const T*>(rn + offK + 32 * v * sizeof(T));
+                        jy[v] = *reinterpret_cast<const T*>(rn + offJ + 32 * v * sizeof(T));
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const T kn = T(0.5) * (kc[v] + kx[v]), jn = T(0.5) * (jc[v] + jx[v]);
+                        seg_step(I[v], kf[v], ds, jf[v], jn);
+                        kf[v] = kn; jf[v] = jn;
+                        kc[v] = kx[v]; jc[v] = jx[v];
+                        kx[v] = ky[v]; jx[v] = jy[v];
+                    }
+                }
+            }
+            {   // last segment: its near node is the cell's own value
+                const T ds = seg_len<T>(a, s1 - 1) * sc;
+#pragma unroll
+                for (int v = 0; v < V; ++v) seg_step(I[v], kf[v], ds, jf[v], jc[v]);
+            }
+        }
+        const T w = dir_val<T>(a.dir_weight, a.dir_weight_f, d0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int kk = base + lane + 32 * v;   // unclamped column
+            if (a.I_out && kk >= tile0 && kk < nk) reinterpret_cast<T*>(a.I_out)[d0 * a.nk + kk] = I[v];
+            const T y = w * I[v] - comp[v];
+            const T tt = acc[v] + y;
+            comp[v] = (tt - acc[v]) - y;
+            acc[v] = tt;
+        }
+    }
+    __shared__ T red[W][32 * V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) red[warp][lane + 32 * v] = acc[v];
+    __syncthreads();
+    T* dst = (lgG == 0 ? reinterpret_cast<T*>(a.q_lambda) : part) + (int64_t)blockIdx.x * a.nk;
+    for (int i = threadIdx.x; i < 32 * V; i += 256) {
+        const int kk = base + i;
+        if (kk < tile0 || kk >= nk) continue;
+        T s = red[0][i];
+        for (int q = 1; q < W; ++q) s += red[q][i];
+        dst[kk] = s;
+    }
+}
+
+// Planck intensity at the wall temperature for the columns of a range.
+template <class T>
+__global__ void k_planck_row(double lam_min, double h, int64_t k0, int64_t nk, double T_wall, Phys ph, T* row) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nk; k += (int64_t)gridDim.x * blockDim.x)
+        row[k] = (T)planck(lam_min + (double)(k0 + k) * h, T_wall, ph);
+}
+
+// q_lambda[p][k] = sum of the G bundle-group partials of point p, in group order.
+template <class T>
+__global__ void k_group_sum(const T* __restrict__ part, int G, int64_t P, int64_t nk, T* __restrict__ q,
+                            const int* status) {
+    if (*status) return;
+    const int64_t n = P * nk;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / nk, k = i - p * nk;
+        const T* src = part + p * G * nk + k;
+        T s = src[0];
+        for (int g = 1; g < G; ++g) s += src[g * nk];
+        q[i] = s;
     }
 }
 
@@ -383,8 +610,37 @@ cudaError_t march_sl(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk,
     return cudaGetLastError();
 }
 
+#ifndef RAPRAL_MARCH_V
+#define RAPRAL_MARCH_V 2
+#endif
+
+template <class T, int V>
+cudaError_t march_rays(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int G, void* part) {
+    if (V > 1 && nk < 32 * V) return march_rays<T, 1>(ctx, a, P, nk, G, part);
+    int lgG = 0;
+    while ((1 << lgG) < G) ++lgG;
+    MarchArgs b = a;
+    b.wall_row = nullptr;
+    if (a.T_wall > 0.0) {   // the wall row follows the group partials in the scratch
+        T* row = reinterpret_cast<T*>(part) + (G > 1 ? P * G * nk : 0);
+        k_planck_row<T><<<(unsigned)std::min<int64_t>(div_up(nk, 256), 1024), 256, 0, ctx->stream>>>(
+            a.lam_min, a.h, a.k0, nk, a.T_wall, a.ph, row);
+        b.wall_row = row;
+    }
+    dim3 g((unsigned)(P << lgG), div_up(nk, 32 * V));
+    k_march_rays<T, V><<<g, 256, 0, ctx->stream>>>(b, lgG, reinterpret_cast<T*>(part));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || G == 1) return e;
+    k_group_sum<T><<<(unsigned)std::min<int64_t>(div_up(P * nk, 256), 152 * 16), 256, 0, ctx->stream>>>(
+        reinterpret_cast<const T*>(part), G, P, nk, reinterpret_cast<T*>(a.q_lambda), a.status);
+    return cudaGetLastError();
+}
+
 template <class T>
-cudaError_t march_t(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxd, int maxb) {
+cudaError_t march_t(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxd, int maxb, int G,
+                    void* part) {
+    if (maxd <= 1 && maxb >= 8)
+        return march_rays<T, sizeof(T) == 4 ? RAPRAL_MARCH_V : 1>(ctx, a, P, nk, G, part);
     if (maxd <= 1) return march_sl<T, 1>(ctx, a, P, nk, maxb);
     if (maxd <= 17) return march_sl<T, 17>(ctx, a, P, nk, maxb);
     return march_sl<T, RAPRAL_MAX_DIRS>(ctx, a, P, nk, maxb);
@@ -400,8 +656,29 @@ cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t 
     return cudaGetLastError();
 }
 
-size_t march_scratch_bytes(const rapral_rays* r) {
-    return (size_t)(r->n_segments + 2 * r->n_dirs) * sizeof(float) + 1024;
+// Bundle groups per point for single-direction bundles (a power of two):
+// enough blocks share a wavelength tile (points x groups >= 1536, about two
+// waves of resident blocks) that the tiles in flight, and so the kappa / j
+// rows they gather, stay few enough for L2; each group keeps at least 32
+// bundles, and points x groups stays below 2^31.
+static int march_groups(const rapral_rays* r) {
+    if (r->max_dirs > 1 || r->max_bundles_per_point < 8 || r->n_points <= 0) return 1;
+    int G = 1;
+    while (G * r->n_points < 1536 && 2 * G * 32 <= r->max_bundles_per_point && G < 1024 &&
+           2 * G * r->n_points < (int64_t)1 << 31)
+        G *= 2;
+    return G;
+}
+
+static size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t march_scratch_bytes(const rapral_rays* r, int64_t nk, int precision) {
+    size_t bytes = 0;
+    if (precision == RAPRAL_FP32) bytes = round256((size_t)(r->n_segments + 2 * r->n_dirs + 128) * sizeof(float));
+    const int G = march_groups(r);
+    const size_t el = precision == RAPRAL_FP64 ? sizeof(double) : sizeof(float);
+    if (G > 1) bytes += (size_t)r->n_points * G * nk * el;
+    return bytes + nk * el + 256;   // + the wall's Planck row
 }
 
 cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis, int64_t ld,
@@ -411,14 +688,17 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
     a.point_off = r->point_off; a.seg_off = r->seg_off; a.seg_cell = r->seg_cell; a.seg_ds = r->seg_ds;
     a.dir_off = r->dir_off; a.dir_scale = r->dir_scale; a.dir_weight = r->dir_weight;
     a.seg_ds_f = nullptr; a.dir_scale_f = nullptr; a.dir_weight_f = nullptr;
-    a.bundle_wall = r->bundle_wall; a.T_wall = r->T_wall;
+    a.bundle_wall = r->bundle_wall; a.T_wall = r->T_wall; a.wall_row = nullptr;
     a.kappa = kappa; a.emis = emis; a.ld = ld;
     a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk;
     a.q_lambda = q_lambda; a.I_out = I_out; a.ph = ph; a.status = ctx->d_status;
+    const int G = march_groups(r);
     if (precision == RAPRAL_FP64)
-        return march_t<double>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
-    // FP32 copies of the path lengths, direction scales and weights
+        return march_t<double>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, scratch);
+    // FP32 copies of the path lengths, direction scales and weights, then the group partials
     float* f = reinterpret_cast<float*>(scratch);
+    void* part = reinterpret_cast<char*>(scratch) +
+                 round256((size_t)(r->n_segments + 2 * r->n_dirs + 128) * sizeof(float));
     float* fd = f + ((r->n_segments + 63) / 64) * 64;
     float* fw = fd + ((r->n_dirs + 63) / 64) * 64;
     if (r->n_segments > 0)
@@ -431,7 +711,7 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
             r->dir_weight, r->n_dirs, fw);
     }
     a.seg_ds_f = f; a.dir_scale_f = fd; a.dir_weight_f = fw;
-    return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point);
+    return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, part);
 }
 
 int64_t wall_flux_parts(int64_t nk) { return (nk + FLUX_SPAN - 1) / FLUX_SPAN; }

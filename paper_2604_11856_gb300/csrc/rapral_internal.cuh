@@ -231,9 +231,11 @@ cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const Ba
 
 // Rays
 cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells);
-// FP32 march needs march_scratch_bytes(r) of scratch for FP32 copies of the
-// ray lengths, direction scales and weights.
-size_t march_scratch_bytes(const rapral_rays* r);
+// The march needs march_scratch_bytes(r, nk, precision) of scratch (256-byte
+// aligned): FP32 copies of the ray lengths, direction scales and weights
+// (FP32 only), then per-group partial spectral fluxes where a point's
+// bundles are split over several blocks.
+size_t march_scratch_bytes(const rapral_rays* r, int64_t nk, int precision);
 cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kappa, const void* emis,
                          int64_t ld, const rapral_grid* g, double h, int64_t k0, int64_t nk, int precision,
                          void* q_lambda, void* I_out, const Phys& ph, void* scratch);

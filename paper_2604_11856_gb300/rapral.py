@@ -282,6 +282,14 @@ def grid_struct(g):
 # the C-ABI calls
 # ----------------------------------------------------------------------------
 
+def _row_stride(kappa, emis, nk):
+    ld = kappa.stride(0) if kappa.dim() == 2 and kappa.shape[0] > 1 else max(int(nk), kappa.shape[-1])
+    if kappa.dim() != 2 or kappa.stride(1) != 1 or emis.shape != kappa.shape or emis.stride() != kappa.stride() \
+            or kappa.shape[1] < nk:
+        raise ValueError("kappa / emis must be equal [C, >= nk] row-major tensors or column views")
+    return ld
+
+
 def populations(ctx, dsp, dcells):
     ctx.check(ctx.lib.rapral_populations(ctx.h, ct.byref(dsp.struct), ct.byref(dcells.struct),
                                          _ptr(dcells.lnpref)))
@@ -289,9 +297,9 @@ def populations(ctx, dsp, dcells):
 
 
 def spectral_coeffs(ctx, dsp, dlines, dcells, grid, k0, nk, precision, kappa, emis):
-    """kappa, emis: [C, ld] tensors of the precision's dtype (written columns 0..nk-1)."""
-    ld = kappa.shape[1]
-    assert emis.shape[1] == ld and kappa.is_contiguous() and emis.is_contiguous()
+    """kappa, emis: [C, >= nk] tensors (or column views of them) of the precision's dtype,
+    rows ld = stride(0) elements apart; columns 0..nk-1 are written."""
+    ld = _row_stride(kappa, emis, nk)
     g = grid_struct(grid)
     ctx.check(ctx.lib.rapral_spectral_coeffs(ctx.h, ct.byref(dsp.struct), ct.byref(dlines.struct),
                                              ct.byref(dcells.struct), ct.byref(g), int(k0), int(nk),
@@ -299,9 +307,12 @@ def spectral_coeffs(ctx, dsp, dlines, dcells, grid, k0, nk, precision, kappa, em
 
 
 def trace_rays(ctx, rays, n_cells, kappa, emis, grid, k0, nk, precision, q_lambda, I_out=None):
+    """kappa, emis as for spectral_coeffs (columns 0..nk-1 are read); q_lambda [P, nk] and
+    I_out [n_dirs, nk] contiguous."""
+    ld = _row_stride(kappa, emis, nk)
     g = grid_struct(grid)
     ctx.check(ctx.lib.rapral_trace_rays(ctx.h, ct.byref(rays.struct), int(n_cells), _ptr(kappa), _ptr(emis),
-                                        int(kappa.shape[1]), ct.byref(g), int(k0), int(nk), int(precision),
+                                        int(ld), ct.byref(g), int(k0), int(nk), int(precision),
                                         _ptr(q_lambda), _ptr(I_out)))
 
 
@@ -325,6 +336,33 @@ class DeviceRays:
     @property
     def n_dirs(self):
         return self.struct.n_dirs
+
+
+def rays_from_arrays(point_off, seg_off, seg_cell, seg_ds, dir_off, dir_scale, dir_weight, bundle_wall,
+                     T_wall, device):
+    """A caller-built ray set (host arrays in the rapral_rays layout) copied
+    to the device; the maxima of directions per bundle and bundles per point
+    are taken from the offsets."""
+    r = DeviceRays()
+    t = r.t
+    point_off = np.asarray(point_off, np.int64); dir_off = np.asarray(dir_off, np.int64)
+    t["point_off"] = _t(point_off, np.int64, device)
+    t["seg_off"] = _t(seg_off, np.int64, device)
+    t["seg_cell"] = _t(np.asarray(seg_cell).reshape(-1) if len(seg_cell) else np.zeros(1), np.int32, device)
+    t["seg_ds"] = _t(np.asarray(seg_ds).reshape(-1) if len(seg_ds) else np.zeros(1), np.float64, device)
+    t["dir_off"] = _t(dir_off, np.int64, device)
+    t["dir_scale"] = _t(dir_scale, np.float64, device)
+    t["dir_weight"] = _t(dir_weight, np.float64, device)
+    t["bundle_wall"] = _t(bundle_wall, np.int32, device)
+    s = r.struct
+    s.n_points, s.n_bundles = len(point_off) - 1, len(dir_off) - 1
+    s.n_segments, s.n_dirs = len(seg_cell), len(dir_scale)
+    s.max_dirs = int(np.diff(dir_off).max()) if len(dir_off) > 1 else 0
+    s.max_bundles_per_point = int(np.diff(point_off).max()) if len(point_off) > 1 else 0
+    for k in ("point_off", "seg_off", "seg_cell", "seg_ds", "dir_off", "dir_scale", "dir_weight", "bundle_wall"):
+        setattr(s, k, t[k].data_ptr())
+    s.T_wall = float(T_wall)
+    return r
 
 
 def slab_rays(ctx, geo, device):

@@ -103,9 +103,10 @@ def test_uniform_slab_fp32_flux(ctx):
     assert abs(q / ref["q"] - 1) <= TOL_Q
 
 
-def test_afterbody_small_fp32(ctx):
+@pytest.mark.parametrize("rays", [dict(), dict(n_points=2, n_mu=8, n_phi=16)], ids=["32rays", "128rays"])
+def test_afterbody_small_fp32(ctx, rays):
     from test_gpu_parity import small_afterbody
-    p = small_afterbody()
+    p = small_afterbody(**rays)
     dp = solver.DeviceProblem(p, ctx)
     out = solver.solve(dp, ctx, R.FP32)
     ctx.sync()

@@ -205,8 +205,12 @@ def test_axisym_segments_match_oracle(ctx):
             b += 1
 
 
-def test_afterbody_small_solve_fp64(ctx):
-    p = small_afterbody()
+@pytest.mark.parametrize("rays", [dict(), dict(n_points=2, n_mu=8, n_phi=16)], ids=["32rays", "128rays"])
+def test_afterbody_small_solve_fp64(ctx, rays):
+    """32 rays a point: one block per (point, wavelength tile); 128 rays a
+    point: the point's rays split over several blocks, whose partial
+    spectral fluxes are added in a fixed order."""
+    p = small_afterbody(**rays)
     dp = solver.DeviceProblem(p, ctx)
     out = solver.solve(dp, ctx, R.FP64, keep_coeffs=True)
     ctx.sync()
@@ -214,6 +218,72 @@ def test_afterbody_small_solve_fp64(ctx):
     qlam, q = oracle.solve_axisym_points(p, range(len(p.geometry.surf_x)), rk, re)
     _close(out["q_lambda"].cpu().numpy(), qlam, qlam, TOL64, "q_lambda")
     _close(out["q"].cpu().numpy(), q, q, TOL64, "q")
+
+
+@pytest.mark.parametrize("precision", [R.FP64, R.FP32])
+def test_march_wavelength_ranges_match_whole(ctx, precision):
+    """Marching a range of columns (views into the coefficient rows) gives
+    each column what the march of the whole grid gives it: the ranges cover
+    a single-lane tile (nk < 32), a partial second tile and the grid's last
+    columns, so the wavelength tiling and the shifted last tile change no
+    result."""
+    p = small_afterbody(n_points=4, n_mu=8, n_phi=16)
+    dp = solver.DeviceProblem(p, ctx)
+    n = p.grid.n
+    out = solver.solve(dp, ctx, precision, keep_coeffs=True, keep_intensity=True)
+    ctx.sync()
+    kap, em = out["kappa"], out["emis"]
+    ql_all = out["q_lambda"].double().cpu().numpy()
+    I_all = out["I"].double().cpu().numpy()
+    dt = kap.dtype
+    tol = 0.0 if precision == R.FP64 else 2.4e-7
+    for a, nk in [(0, 5), (13, 71), (4000, 1), (n - 70, 70), (777, 2500)]:
+        ql = torch.empty((dp.P, nk), dtype=dt, device=ctx.device)
+        I = torch.empty((dp.rays.n_dirs, nk), dtype=dt, device=ctx.device)
+        R.trace_rays(ctx, dp.rays, dp.C, kap[:, a:a + nk], em[:, a:a + nk], p.grid, a, nk, precision, ql, I)
+        ctx.sync()
+        for got, ref, what in ((ql, ql_all, "q_lambda"), (I, I_all, "I")):
+            g = got.double().cpu().numpy()
+            r = ref[:, a:a + nk]
+            err = np.max(np.abs(g - r) / np.maximum(np.abs(r), 1e-300))
+            assert err <= tol, (a, nk, what, err)
+
+
+@pytest.mark.parametrize("n_mu", [16, 64])
+@pytest.mark.parametrize("precision", [R.FP64, R.FP32])
+def test_single_direction_bundles_from_wall(ctx, n_mu, precision):
+    """A slab with a hot wall at its far end, every direction its own bundle
+    (as a caller-built ray set): the single-direction march, starting from
+    the wall's Planck intensity, agrees with the oracle's slab solve; with
+    64 bundles the point's bundles are split over two blocks."""
+    base = small_stagnation(n_cells=12, n_atomic=500, n_molecular=5000, n_grid=9001)
+    mu, w = synth.gauss_legendre_01(n_mu)
+    geo = synth.SlabGeometry(cell_order=base.geometry.cell_order, dx=base.geometry.dx, mu=mu, wmu=w,
+                             normal_ray=False, wall_start=True, T_wall=3000.0)
+    p = synth.Problem("wall slab", base.species, base.lines, base.cells, base.grid, geo)
+    ref = oracle.solve_slab(p)
+    m = len(geo.cell_order)
+    rays = R.rays_from_arrays(point_off=[0, n_mu], seg_off=np.arange(n_mu + 1) * m,
+                              seg_cell=np.tile(geo.cell_order, n_mu), seg_ds=np.tile(geo.dx, n_mu),
+                              dir_off=np.arange(n_mu + 1), dir_scale=1.0 / mu, dir_weight=2 * np.pi * w * mu,
+                              bundle_wall=np.ones(n_mu), T_wall=geo.T_wall, device=ctx.device)
+    dp = solver.DeviceProblem(p, ctx)
+    dt = torch.float64 if precision == R.FP64 else torch.float32
+    n = p.grid.n
+    kap = torch.empty((dp.C, n), dtype=dt, device=ctx.device); em = torch.empty_like(kap)
+    R.populations(ctx, dp.species, dp.cells)
+    R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, 0, n, precision, kap, em)
+    ql = torch.empty((1, n), dtype=dt, device=ctx.device)
+    I = torch.empty((n_mu, n), dtype=dt, device=ctx.device)
+    R.trace_rays(ctx, rays, dp.C, kap, em, p.grid, 0, n, precision, ql, I)
+    ctx.sync()
+    if precision == R.FP64:
+        _close(I.cpu().numpy(), ref["I_mu"], ref["I_mu"], TOL64, "I")
+        _close(ql.cpu().numpy()[0], ref["q_lambda"], ref["q_lambda"], TOL64, "q_lambda")
+    else:
+        g = ql.double().cpu().numpy()[0]
+        big = ref["q_lambda"] >= 1e-6 * ref["q_lambda"].max()
+        assert np.max(np.abs(g - ref["q_lambda"])[big] / ref["q_lambda"][big]) <= 1e-3
 
 
 # ------------------------------------------------------------------- errors
