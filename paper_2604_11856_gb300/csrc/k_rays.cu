@@ -2,15 +2,9 @@
 // march with the angular reduction, and the spectral flux integral
 // (Sec. 2.2.3).
 //
-// k_march: one block per (surface point, wavelength tile), points along x.  Threads are
-// (wavelength lane, bundle slice): lanes run over consecutive grid points so
-// every kappa / j gather of a segment is a coalesced row read; slices take the
-// point's bundles round-robin.  Per bundle the kernel walks the segments from
-// the far boundary, keeps the node values of the current face in registers,
-// and advances the intensity of every direction of the bundle (up to MAXD in
-// registers) with the far/near coefficients of the linear-emission integral.
-// The weighted directions are summed per thread; slices are combined in
-// shared memory in a fixed order, so results do not depend on timing.
+// k_march (below) marches the bundles of every surface point over a range of
+// wavelength columns and reduces them to the spectral flux at the point;
+// k_wall_flux_part / _sum integrate that over the range.
 #include <algorithm>
 
 #include "rapral_internal.cuh"
@@ -151,7 +145,7 @@ struct MarchArgs {
     const float* dir_weight_f;
     const int32_t* bundle_wall;
     double T_wall;
-    const void* wall_row;        // Planck intensity at T_wall per column (k_march_rays; null: T_wall = 0)
+    const void* wall_row;        // Planck intensity at T_wall per column (null: T_wall = 0)
     const void* kappa;
     const void* emis;
     int64_t ld;
@@ -182,131 +176,144 @@ __device__ __forceinline__ double planck(double lam_nm, double T, const Phys& ph
     return 1e-7 * 2.0 * ph.h * ph.c * ph.c / (1e4 * l2 * l2 * lcm * expm1(ph.h * ph.c / (lcm * ph.kB * T)));
 }
 
-template <class T, int MAXD, int SL>
-__global__ void __launch_bounds__(256) k_march(MarchArgs a) {
-    if (*a.status) return;
-    constexpr int LW = 256 / SL;        // wavelength lanes per block
-    const int lane = threadIdx.x % LW;
-    const int slice = threadIdx.x / LW;
-    const int64_t p = blockIdx.x;                           // points vary fastest: concurrent blocks share
-    const int64_t kk = (int64_t)blockIdx.y * LW + lane;     // a wavelength tile, whose kappa / j stay in L2
-    const bool active = kk < a.nk;
-    const int64_t kcol = active ? kk : a.nk - 1;
-    const T* Kt = reinterpret_cast<const T*>(a.kappa) + kcol;
-    const T* Jt = reinterpret_cast<const T*>(a.emis) + kcol;
-    T acc = T(0), comp = T(0);
-    for (int64_t b = a.point_off[p] + slice; b < a.point_off[p + 1]; b += SL) {
-        const int64_t d0 = a.dir_off[b];
-        const int nd = (int)(a.dir_off[b + 1] - d0);
-        T I[MAXD], sc[MAXD], isc[MAXD];
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-            sc[d] = d < nd ? dir_val<T>(a.dir_scale, a.dir_scale_f, d0 + d) : T(1);
-            isc[d] = recip(sc[d]);
-        }
-        T I0 = T(0);
-        if (a.bundle_wall[b]) I0 = (T)planck(a.lam_min + (double)(a.k0 + kcol) * a.h, a.T_wall, a.ph);
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) I[d] = I0;
-        const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
-        if (s1 > s0) {
-            int c = a.seg_cell[s0];
-            T kc = Kt[(int64_t)c * a.ld], jc = Jt[(int64_t)c * a.ld];   // current cell
-            T kf = kc, jf = jc;                                          // far node of the segment
-            for (int64_t i = s0; i < s1; ++i) {
-                T kn, jn;                 // near node
-                T kx = T(0), jx = T(0);   // next cell
-                if (i + 1 < s1) {
-                    const int cn = a.seg_cell[i + 1];
-                    kx = Kt[(int64_t)cn * a.ld];
-                    jx = Jt[(int64_t)cn * a.ld];
-                    kn = T(0.5) * (kc + kx);
-                    jn = T(0.5) * (jc + jx);
-                } else {
-                    kn = kc; jn = jc;
-                }
-                const T ds = seg_len<T>(a, i);
-                const T inv_k = recip(kf);
-                const T inv_ds = recip(ds);
-#pragma unroll
-                for (int d = 0; d < MAXD; ++d) {
-                    if (d < nd) {
-                        T e, ca, cb;
-                        seg_coeffs(kf, ds * sc[d], inv_k, inv_ds * isc[d], &e, &ca, &cb);
-                        I[d] = I[d] * e + ca * jf + cb * jn;
-                    }
-                }
-                kf = kn; jf = jn;
-                kc = kx; jc = jx;
-            }
-        }
-        T part = T(0);
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-            if (d < nd) {
-                part += dir_val<T>(a.dir_weight, a.dir_weight_f, d0 + d) * I[d];
-                if (a.I_out && active) reinterpret_cast<T*>(a.I_out)[(d0 + d) * a.nk + kk] = I[d];
-            }
-        }
-        // compensated sum over the point's bundles
-        const T y = part - comp;
-        const T tt = acc + y;
-        comp = (tt - acc) - y;
-        acc = tt;
-    }
-    if (SL == 1) {
-        if (active) reinterpret_cast<T*>(a.q_lambda)[p * a.nk + kk] = acc;
-        return;
-    }
-    __shared__ T red[256];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (slice == 0 && active) {
-        T s = red[lane];
-        for (int q = 1; q < SL; ++q) s += red[q * LW + lane];
-        reinterpret_cast<T*>(a.q_lambda)[p * a.nk + kk] = s;
-    }
-}
-
-// Single-direction bundles (each ray with its own path, as in the
-// axisymmetric geometry): one warp marches one bundle over V x 32
-// wavelengths, lane l taking columns l, l + 32, ..., so each gather of a
-// segment is V coalesced row reads and the per-segment work (next cell,
-// path length, row address) is shared by V wavelengths.  The warp stages
-// the next cell's row address and the scaled length of 32 segments at a time
-// in shared memory (one coalesced read of the segment list), so no kappa / j
-// gather waits on a dependent load of the list; the last segment of a ray,
-// whose near node is its own cell, is taken outside the loop.  A point's
-// bundles are split over 2^lgG blocks (groups) and, within a block,
-// round-robin over its eight warps; each warp Kahan-sums its bundles, the
-// warps are added in a fixed order, and the groups' partial spectral fluxes
-// are added in group order by k_group_sum.  The last wavelength tile is
-// shifted back to end at nk (its columns below the tile are computed again
-// and not written), so every load is in bounds without a per-lane clamp; the
-// launcher takes V = 1 when nk < 32 V.
+// The march of one bundle over the lane's V columns: staged segment list,
+// next-cell gathers one step ahead, all MAXD directions per segment.  A
+// bundle with nd < MAXD directions marches the others with scale 0, which
+// leaves their intensity at its start value (e = 1, zero source): no
+// per-direction check in the loop.  Returns the intensities in I[v][d].
 template <class T> struct __align__(16) SegStage {
     const char* row;   // kappa row of the segment's next cell
-    T ds;              // path length x direction scale
+    T ds;              // path length (x the direction scale for one-direction bundles)
 };
 
 #ifndef RAPRAL_MARCH_UNROLL
 #define RAPRAL_MARCH_UNROLL 3
 #endif
 constexpr int kUnroll = RAPRAL_MARCH_UNROLL;
+
+template <class T, int V, int MAXD>
+__device__ __forceinline__ void march_bundle(const MarchArgs& a, int64_t b, int64_t d0, int nd, SegStage<T>* stage,
+                                             int lane, const char* kbase, int64_t ldb, int64_t offK, int64_t offJ,
+                                             int col0, T (&I)[V][MAXD]) {
+    T sc[MAXD];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) sc[d] = d < nd ? dir_val<T>(a.dir_scale, a.dir_scale_f, d0 + d) : T(0);
+    // one direction: its scale goes into the staged length
+    const T stage_scale = MAXD == 1 ? sc[0] : T(1);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const T I0 = (a.wall_row && a.bundle_wall[b]) ? reinterpret_cast<const T*>(a.wall_row)[col0 + 32 * v] : T(0);
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) I[v][d] = I0;
+    }
+    const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
+    if (s1 <= s0) return;
+    T kc[V], jc[V], kf[V], jf[V];
+    {
+        const char* row = kbase + (int64_t)a.seg_cell[s0] * ldb;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            kc[v] = kf[v] = *reinterpret_cast<const T*>(row + offK + 32 * v * sizeof(T));
+            jc[v] = jf[v] = *reinterpret_cast<const T*>(row + offJ + 32 * v * sizeof(T));
+        }
+    }
+    // every segment but the last has a next cell: stage (row of the next
+    // cell, length) for 32 segments, read back by all lanes
+    for (int64_t g = s0; g < s1 - 1; g += 32) {
+        const int64_t mine = g + lane;
+        __syncwarp();
+        // entries past the chunk point at row 0 (a valid row), so the
+        // prefetch of entry j + 1 below never leaves the arrays
+        const bool in = mine < s1 - 1;
+        stage[lane].row = in ? kbase + (int64_t)a.seg_cell[mine + 1] * ldb : kbase;
+        stage[lane].ds = in ? seg_len<T>(a, mine) * stage_scale : T(0);
+        if (lane == 0) stage[32].row = kbase;
+        __syncwarp();
+        const int n = s1 - 1 - g < 32 ? (int)(s1 - 1 - g) : 32;
+        T kx[V], jx[V];
+        {
+            const char* r0 = stage[0].row;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                kx[v] = *reinterpret_cast<const T*>(r0 + offK + 32 * v * sizeof(T));
+                jx[v] = *reinterpret_cast<const T*>(r0 + offJ + 32 * v * sizeof(T));
+            }
+        }
+        constexpr int U = MAXD == 1 ? kUnroll : 1;   // bundles of many directions: registers go to I
+#pragma unroll U
+        for (int j = 0; j < n; ++j) {
+            const T ds = stage[j].ds;
+            const char* rn = stage[j + 1].row;
+            T ky[V], jy[V];   // next segment's next cell, loaded a step ahead
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                ky[v] = *reinterpret_cast<const T*>(rn + offK + 32 * v * sizeof(T));
+                jy[v] = *reinterpret_cast<const T*>(rn + offJ + 32 * v * sizeof(T));
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T kn = T(0.5) * (kc[v] + kx[v]), jn = T(0.5) * (jc[v] + jx[v]);
+#pragma unroll
+                for (int d = 0; d < MAXD; ++d) seg_step(I[v][d], kf[v], MAXD == 1 ? ds : ds * sc[d], jf[v], jn);
+                kf[v] = kn; jf[v] = jn;
+                kc[v] = kx[v]; jc[v] = jx[v];
+                kx[v] = ky[v]; jx[v] = jy[v];
+            }
+        }
+    }
+    {   // last segment: its near node is the cell's own value
+        const T ds = seg_len<T>(a, s1 - 1) * stage_scale;
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) seg_step(I[v][d], kf[v], MAXD == 1 ? ds : ds * sc[d], jf[v], jc[v]);
+    }
+}
+
+// k_march: the segment march with the angular reduction.  A block of eight
+// warps covers one (surface point, bundle group) and a tile of wavelength
+// columns; its warps are SL bundle slices x CW = 8 / SL column groups, and
+// lane l of a column group takes columns l, l + 32, ..., l + 32 (V - 1) of
+// the group's 32 V.  Each gather of a segment is then V coalesced row
+// reads, and the per-segment work (next cell, length, row address) is
+// shared by the V columns and the bundle's directions.  SL = 8 (many bundles
+// a point, as the axisymmetric rays): the eight warps take the bundles of
+// the group round-robin; SL = 1 (a few bundles of many directions, as the
+// tangent slab): all warps march every bundle over eight column groups.
+// A warp stages the next cell's row address and the length of 32 segments at
+// a time in shared memory (one coalesced read of the segment list), so no
+// kappa / j gather waits on a dependent load of the list, and loads the next
+// segment's values one step ahead; the last segment of a bundle, whose near
+// node is its own cell, is taken after the loop.  A point's bundles are
+// split over 2^lgG blocks (groups) so that enough blocks share a wavelength
+// tile for its kappa / j rows to stay in L2.  Each slice Kahan-sums its
+// bundles' weighted intensities, the slices are added in a fixed order, and
+// the groups' partial spectral fluxes are added in group order by
+// k_group_sum: results do not depend on timing.  The last wavelength tile is
+// shifted back to end at nk (columns below the tile are computed again and
+// not written), so every load is in bounds; with V = 1 and nk below the
+// tile a lane past nk reads column nk - 1 and writes nothing.
 #ifndef RAPRAL_MARCH_MINB
 #define RAPRAL_MARCH_MINB 4
 #endif
-template <class T, int V>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? RAPRAL_MARCH_MINB : 1)
-    k_march_rays(MarchArgs a, int lgG, T* __restrict__ part) {
+#ifndef RAPRAL_MARCH_MINB17
+#define RAPRAL_MARCH_MINB17 3
+#endif
+template <class T, int V, int MAXD, int SL>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && MAXD == 1 && V > 1)  ? RAPRAL_MARCH_MINB
+                                       : (sizeof(T) == 4 && MAXD == 17) ? RAPRAL_MARCH_MINB17
+                                                                        : 1)
+    k_march(MarchArgs a, int lgG, T* __restrict__ part) {
     if (*a.status) return;
-    constexpr int W = 8;
+    constexpr int W = 8, CW = W / SL, TW = CW * 32 * V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slice = warp / CW, cgrp = warp % CW;
     // columns fit in int: nk <= 32 x 65535 (checked by the caller)
     const int nk = (int)a.nk;
-    const int tile0 = (int)blockIdx.y * (32 * V);
-    const int base = (V > 1 && tile0 + 32 * V > nk) ? nk - 32 * V : tile0;
-    const int col0 = (V == 1 && base + lane >= nk) ? nk - 1 : base + lane;
+    const int tile0 = (int)blockIdx.y * TW;
+    const int base = (tile0 + TW > nk && nk >= TW) ? nk - TW : tile0;
+    const int colu = base + cgrp * 32 * V + lane;   // unclamped first column
+    const int col0 = colu < nk ? colu : nk - 1;     // only when V = 1 and nk < TW
     // byte addressing: row of cell c at kbase + c ldb; this lane's kappa and
     // j columns at offK, offJ from it
     const char* kbase = reinterpret_cast<const char*>(a.kappa);
@@ -319,100 +326,44 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? RAPRAL_MARCH_MINB : 1)
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = comp[v] = T(0);
     // G = 2^lgG groups of point p = blockIdx.x >> lgG; group g takes every
-    // G-th run of W bundles, warp w the w-th bundle of each run
+    // G-th run of SL bundles, slice s the s-th bundle of each run
     const unsigned p = blockIdx.x >> lgG, grp = blockIdx.x & ((1u << lgG) - 1u);
     const int64_t b1 = a.point_off[p + 1];
-    for (int64_t b = a.point_off[p] + (int64_t)grp * W + warp; b < b1; b += (int64_t)W << lgG) {
+    for (int64_t b = a.point_off[p] + (int64_t)grp * SL + slice; b < b1; b += (int64_t)SL << lgG) {
         const int64_t d0 = a.dir_off[b];
-        if (a.dir_off[b + 1] == d0) continue;
-        const T sc = dir_val<T>(a.dir_scale, a.dir_scale_f, d0);
-        T I[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) I[v] = T(0);
-        if (a.wall_row && a.bundle_wall[b]) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) I[v] = reinterpret_cast<const T*>(a.wall_row)[col0 + 32 * v];
-        }
-        const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
-        if (s1 > s0) {
-            T kc[V], jc[V], kf[V], jf[V];
-            {
-                const char* row = kbase + (int64_t)a.seg_cell[s0] * ldb;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    kc[v] = kf[v] = *reinterpret_cast<const T*>(row + offK + 32 * v * sizeof(T));
-                    jc[v] = jf[v] = *reinterpret_cast<const T*>(row + offJ + 32 * v * sizeof(T));
-                }
-            }
-            // every segment but the last has a next cell: stage (row of the
-            // next cell, scaled length) for 32 segments, read back by all lanes
-            for (int64_t g = s0; g < s1 - 1; g += 32) {
-                const int64_t mine = g + lane;
-                __syncwarp();
-                // entries past the chunk point at row 0 (a valid row), so the
-                // prefetch of entry j + 1 below never leaves the arrays
-                const bool in = mine < s1 - 1;
-                stage[lane].row = in ? kbase + (int64_t)a.seg_cell[mine + 1] * ldb : kbase;
-                stage[lane].ds = in ? seg_len<T>(a, mine) * sc : T(0);
-                if (lane == 0) stage[32].row = kbase;
-                __syncwarp();
-                const int n = s1 - 1 - g < 32 ? (int)(s1 - 1 - g) : 32;
-                T kx[V], jx[V];
-                {
-                    const char* r0 = stage[0].row;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        kx[v] = *reinterpret_cast<const T*>(r0 + offK + 32 * v * sizeof(T));
-                        jx[v] = *reinterpret_cast<const T*>(r0 + offJ + 32 * v * sizeof(T));
-                    }
-                }
-#pragma unroll kUnroll
-                for (int j = 0; j < n; ++j) {
-                    const T ds = stage[j].ds;
-                    const char* rn = stage[j + 1].row;
-                    T ky[V], jy[V];   // next segment's next cell, loaded a step ahead
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        ky[v] = *reinterpret_cast<const T*>(rn + offK + 32 * v * sizeof(T));
-                        jy[v] = *reinterpret_cast<const T*>(rn + offJ + 32 * v * sizeof(T));
-                    }
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const T kn = T(0.5) * (kc[v] + kx[v]), jn = T(0.5) * (jc[v] + jx[v]);
-                        seg_step(I[v], kf[v], ds, jf[v], jn);
-                        kf[v] = kn; jf[v] = jn;
-                        kc[v] = kx[v]; jc[v] = jx[v];
-                        kx[v] = ky[v]; jx[v] = jy[v];
-                    }
-                }
-            }
-            {   // last segment: its near node is the cell's own value
-                const T ds = seg_len<T>(a, s1 - 1) * sc;
-#pragma unroll
-                for (int v = 0; v < V; ++v) seg_step(I[v], kf[v], ds, jf[v], jc[v]);
-            }
-        }
-        const T w = dir_val<T>(a.dir_weight, a.dir_weight_f, d0);
+        const int nd = (int)(a.dir_off[b + 1] - d0);
+        if (nd == 0) continue;
+        T I[V][MAXD];
+        march_bundle<T, V, MAXD>(a, b, d0, nd, stage, lane, kbase, ldb, offK, offJ, col0, I);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const int kk = base + lane + 32 * v;   // unclamped column
-            if (a.I_out && kk >= tile0 && kk < nk) reinterpret_cast<T*>(a.I_out)[d0 * a.nk + kk] = I[v];
-            const T y = w * I[v] - comp[v];
+            const int kk = colu + 32 * v;
+            const bool own = kk >= tile0 && kk < nk;
+            T part_v = T(0);
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) {
+                if (d < nd) {
+                    part_v += dir_val<T>(a.dir_weight, a.dir_weight_f, d0 + d) * I[v][d];
+                    if (a.I_out && own) reinterpret_cast<T*>(a.I_out)[(d0 + d) * a.nk + kk] = I[v][d];
+                }
+            }
+            // compensated sum over the slice's bundles
+            const T y = part_v - comp[v];
             const T tt = acc[v] + y;
             comp[v] = (tt - acc[v]) - y;
             acc[v] = tt;
         }
     }
-    __shared__ T red[W][32 * V];
+    __shared__ T red[SL][TW];
 #pragma unroll
-    for (int v = 0; v < V; ++v) red[warp][lane + 32 * v] = acc[v];
+    for (int v = 0; v < V; ++v) red[slice][cgrp * 32 * V + lane + 32 * v] = acc[v];
     __syncthreads();
     T* dst = (lgG == 0 ? reinterpret_cast<T*>(a.q_lambda) : part) + (int64_t)blockIdx.x * a.nk;
-    for (int i = threadIdx.x; i < 32 * V; i += 256) {
+    for (int i = threadIdx.x; i < TW; i += 256) {
         const int kk = base + i;
         if (kk < tile0 || kk >= nk) continue;
         T s = red[0][i];
-        for (int q = 1; q < W; ++q) s += red[q][i];
+        for (int q = 1; q < SL; ++q) s += red[q][i];
         dst[kk] = s;
     }
 }
@@ -598,25 +549,13 @@ __global__ void k_axisym_fill(const double* xf, int32_t nx, const double* rf, in
     bundle_wall[b] = 0;
 }
 
-template <class T, int MAXD>
-cudaError_t march_sl(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxb) {
-    if (maxb >= 8) {
-        dim3 g((unsigned)P, div_up(nk, 32));
-        k_march<T, MAXD, 8><<<g, 256, 0, ctx->stream>>>(a);
-    } else {
-        dim3 g((unsigned)P, div_up(nk, 256));
-        k_march<T, MAXD, 1><<<g, 256, 0, ctx->stream>>>(a);
-    }
-    return cudaGetLastError();
-}
-
 #ifndef RAPRAL_MARCH_V
 #define RAPRAL_MARCH_V 2
 #endif
 
-template <class T, int V>
-cudaError_t march_rays(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int G, void* part) {
-    if (V > 1 && nk < 32 * V) return march_rays<T, 1>(ctx, a, P, nk, G, part);
+template <class T, int V, int MAXD, int SL>
+cudaError_t march_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int G, void* part) {
+    constexpr int TW = (8 / SL) * 32 * V;
     int lgG = 0;
     while ((1 << lgG) < G) ++lgG;
     MarchArgs b = a;
@@ -627,8 +566,8 @@ cudaError_t march_rays(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t n
             a.lam_min, a.h, a.k0, nk, a.T_wall, a.ph, row);
         b.wall_row = row;
     }
-    dim3 g((unsigned)(P << lgG), div_up(nk, 32 * V));
-    k_march_rays<T, V><<<g, 256, 0, ctx->stream>>>(b, lgG, reinterpret_cast<T*>(part));
+    dim3 g((unsigned)(P << lgG), div_up(nk, TW));
+    k_march<T, V, MAXD, SL><<<g, 256, 0, ctx->stream>>>(b, lgG, reinterpret_cast<T*>(part));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || G == 1) return e;
     k_group_sum<T><<<(unsigned)std::min<int64_t>(div_up(P * nk, 256), 152 * 16), 256, 0, ctx->stream>>>(
@@ -636,14 +575,24 @@ cudaError_t march_rays(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t n
     return cudaGetLastError();
 }
 
+// Eight bundle slices for eight or more bundles a point, else one; V > 1
+// columns a lane only for one-direction bundles in FP32 and ranges of at
+// least one tile.
 template <class T>
 cudaError_t march_t(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxd, int maxb, int G,
                     void* part) {
-    if (maxd <= 1 && maxb >= 8)
-        return march_rays<T, sizeof(T) == 4 ? RAPRAL_MARCH_V : 1>(ctx, a, P, nk, G, part);
-    if (maxd <= 1) return march_sl<T, 1>(ctx, a, P, nk, maxb);
-    if (maxd <= 17) return march_sl<T, 17>(ctx, a, P, nk, maxb);
-    return march_sl<T, RAPRAL_MAX_DIRS>(ctx, a, P, nk, maxb);
+    constexpr int VR = sizeof(T) == 4 ? RAPRAL_MARCH_V : 1;
+    if (maxb >= 8) {
+        if (maxd <= 1) {
+            if (VR > 1 && nk >= 32 * VR) return march_launch<T, VR, 1, 8>(ctx, a, P, nk, G, part);
+            return march_launch<T, 1, 1, 8>(ctx, a, P, nk, G, part);
+        }
+        if (maxd <= 17) return march_launch<T, 1, 17, 8>(ctx, a, P, nk, G, part);
+        return march_launch<T, 1, RAPRAL_MAX_DIRS, 8>(ctx, a, P, nk, G, part);
+    }
+    if (maxd <= 1) return march_launch<T, 1, 1, 1>(ctx, a, P, nk, G, part);
+    if (maxd <= 17) return march_launch<T, 1, 17, 1>(ctx, a, P, nk, G, part);
+    return march_launch<T, 1, RAPRAL_MAX_DIRS, 1>(ctx, a, P, nk, G, part);
 }
 
 }  // namespace
@@ -656,13 +605,13 @@ cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t 
     return cudaGetLastError();
 }
 
-// Bundle groups per point for single-direction bundles (a power of two):
+// Bundle groups per point where a point has eight or more bundles (a power of two):
 // enough blocks share a wavelength tile (points x groups >= 1536, about two
 // waves of resident blocks) that the tiles in flight, and so the kappa / j
 // rows they gather, stay few enough for L2; each group keeps at least 32
 // bundles, and points x groups stays below 2^31.
 static int march_groups(const rapral_rays* r) {
-    if (r->max_dirs > 1 || r->max_bundles_per_point < 8 || r->n_points <= 0) return 1;
+    if (r->max_bundles_per_point < 8 || r->n_points <= 0) return 1;
     int G = 1;
     while (G * r->n_points < 1536 && 2 * G * 32 <= r->max_bundles_per_point && G < 1024 &&
            2 * G * r->n_points < (int64_t)1 << 31)
