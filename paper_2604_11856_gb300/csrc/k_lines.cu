@@ -584,8 +584,10 @@ __device__ __forceinline__ float whiting_bracket(float u, float r, float omr, fl
     const float rd = rcp_approx(q4 * p1);
     const float num = fmaf(r, p1, -c16 * q4);                                // r(1+0.1v) - c16(1+4u^2)
     if (FAR) return num * rd;
-    const float g = u2 < 31.5f ? ex2_approx(-3.99915f * u2) : 0.0f;       // e^{-2.772 u^2}
-    const float e2 = v < 218.0f ? ex2_approx(-0.5770780f * v) : 0.0f;      // e^{-0.4 v}
+    // past u^2 = 31.5 and v = 218 the approximate ex2 returns 0 (flushed) or
+    // below 1.5e-38, so neither exponential needs a guard
+    const float g = ex2_approx(-3.99915f * u2);      // e^{-2.772 u^2}
+    const float e2 = ex2_approx(-0.5770780f * v);    // e^{-0.4 v}
     return fmaf(omr, g, fmaf(num, rd, c16 * e2));
 }
 
@@ -597,10 +599,36 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// One pair over the lane's points k = lane + 32 i of the tile: runs of 32
+// points outside the window part [lo, hi] are skipped (the test is the same
+// for the whole warp); in the others each lane adds its point if it lies in
+// the window.
+template <int PPT, bool FAR>
+__device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, float s, float ub, float ub_lo, float r,
+                                           float omr, float c16, float aj, float ak, float (&bj)[PPT],
+                                           float (&bk)[PPT]) {
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const float p0 = 32.0f * i;
+        if (p0 + 31.0f < lo || p0 > hi) continue;
+        const float k = lanef + p0;
+        // signed u at point k: one rounding of k s + ub (exact product), then
+        // the low part; relative to u itself, so the Gaussian core keeps FP32
+        // accuracy however far the tile start lies from the line centre
+        const float br = whiting_bracket<FAR>(fabsf(fmaf(k, s, ub) + ub_lo), r, omr, c16);
+        const bool in = k >= lo && k <= hi;
+        bj[i] = fmaf(in ? aj : 0.0f, br, bj[i]);
+        bk[i] = fmaf(in ? ak : 0.0f, br, bk[i]);
+    }
+}
+
 // Warp-level line sum: a warp owns one cell and the TW = 32 PPT points of
-// tile t (PPT consecutive points per lane); it stages 32 (line, cell) pairs
-// at a time in its own shared-memory slice (one per lane), then sweeps them
-// over its points.  Warps never wait for each other.
+// tile t, lane l the points l, l + 32, ..., l + 32 (PPT - 1); it stages 32
+// (line, cell) pairs at a time in its own shared-memory slice (one per lane),
+// then sweeps them over its points.  With the points interleaved, whether a
+// pair's window reaches the i-th run of 32 points is the same for the whole
+// warp, so runs outside the window are skipped without a masked evaluation.
+// Warps never wait for each other.
 template <int PPT>
 __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
                                               float2* smlp, float4* acc, int lane, int64_t* cnt) {
@@ -608,8 +636,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     const int kt0 = (int)(a.k0 + (int64_t)t * TW);
     const int kt1 = (int)min(a.k0 + (int64_t)(t + 1) * TW, a.k0 + a.nk) - 1;   // inclusive
     const float kt0f = (float)kt0, kt1f = (float)kt1;
-    const int lp0 = lane * PPT;            // lane's first point, relative to kt0
-    const float lpf = (float)lp0;
+    const float lanef = (float)lane;       // lane's first point, relative to kt0
     // compensated sums (Kahan) of the per-batch partial sums, kept in shared
     // memory (acc[i * 32 + lane] = (s_j, c_j, s_k, c_k)); inside a batch of at
     // most 32 lines the terms are added plainly in registers (error <= 31 u
@@ -651,39 +678,13 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
         __syncwarp();
         for (int q = 0; q < nv; ++q) {
             const float4 A = sm0[q];
-            const float i0 = fmaxf(A.x - lpf, 0.0f);
-            const float i1 = fminf(A.y - lpf, (float)(PPT - 1));
-            if (i0 > i1) continue;
             const float4 B = sm1[q];
+            const float lo = A.x, hi = A.y;             // window part in the tile
             const float s = fabsf(A.w), r = B.x, aj = B.z, ak = B.w;
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
-            const float x0 = fmaf(lpf, s, A.z) + B.y;   // signed u of the lane's first point
-            if (A.w < 0.0f) {                           // far wings only (uniform over the warp)
-                if (i0 == 0.0f && i1 == (float)(PPT - 1)) {
-#pragma unroll
-                    for (int i = 0; i < PPT; ++i) {
-                        const float br = whiting_bracket<true>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
-                        bj[i] = fmaf(aj, br, bj[i]);
-                        bk[i] = fmaf(ak, br, bk[i]);
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < PPT; ++i)
-                        if ((float)i >= i0 && (float)i <= i1) {
-                            const float br = whiting_bracket<true>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
-                            bj[i] = fmaf(aj, br, bj[i]);
-                            bk[i] = fmaf(ak, br, bk[i]);
-                        }
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < PPT; ++i)
-                    if ((float)i >= i0 && (float)i <= i1) {
-                        const float br = whiting_bracket<false>(fabsf(fmaf((float)i, s, x0)), r, omr, c16);
-                        bj[i] = fmaf(aj, br, bj[i]);
-                        bk[i] = fmaf(ak, br, bk[i]);
-                    }
-            }
+            const float ub = A.z, ub_lo = B.y;
+            if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            else sweep_pair<PPT, false>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
         }
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
@@ -699,7 +700,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     float* J = reinterpret_cast<float*>(a.emis) + c * a.ld - a.k0;
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
-        const int k = kt0 + lp0 + i;
+        const int k = kt0 + lane + 32 * i;
         const float4 v = acc[i * 32 + lane];
         if (k <= kt1) { K[k] = v.z; J[k] = v.x; }
     }
