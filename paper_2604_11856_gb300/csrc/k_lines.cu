@@ -706,10 +706,10 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     }
 }
 
-// Resident blocks per SM asked of the compiler: 32 warps per SM, so at most
-// 64 registers per thread (measured best against 24 and 20 warps).
+// Resident blocks per SM asked of the compiler: 24 warps per SM, so at most
+// 80 registers per thread (measured best against 32, 28 and 20 warps).
 #ifndef RAPRAL_LS_WARPS
-#define RAPRAL_LS_WARPS 32
+#define RAPRAL_LS_WARPS 24
 #endif
 #define RAPRAL_LS_BLOCKS(WPB) (RAPRAL_LS_WARPS / (WPB))
 
