@@ -57,6 +57,28 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (read + write) of one FP32 line-sum launch on the stagnation line
+# at full size (200 cells x 1e6 points, tiling 128 x 2), from a one-pass ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
+# with this SHA-1.  Other cell / point counts scale in proportion (the bytes are
+# the kappa / j rows written); a different source gives null.
+LINE_SUM_TRAFFIC = {"sha1": "e49ed04cfd7963832a76f374308fc5c84d152a4f", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 57_468_672 + 1_550_780_928}
+
+
+def line_sum_traffic(cells, grid_points):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_11856_gb300", "csrc", "k_lines.cu")
+    try:
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if digest != LINE_SUM_TRAFFIC["sha1"]:
+        return None
+    t = LINE_SUM_TRAFFIC
+    return t["bytes"] * (cells / t["cells"]) * (grid_points / t["grid_points"])
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -371,11 +393,13 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     if precision == R.FP32:
+        traffic = line_sum_traffic(C, K)
         xu_ops = 3 * stats["evaluations"] + stats["gauss_terms"] + stats["correction_terms"]
         peak = n_sm * 16 * sm_max / 1e9               # Gop/s: 16 XU lanes per SM per clock
         achieved = xu_ops / (k3_mean * 1e-3) / 1e9
         roof = {"bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)", "achieved": achieved, "peak": peak,
-                "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_algorithmic_bytes": C * K * 8,   # kappa and j written once, FP32
                 "kernel": "k_line_sum_f32", "kernel_ms": k3_mean, "evaluations": evals_per_step,
                 "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"}
     else:
