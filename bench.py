@@ -247,12 +247,40 @@ def run_afterbody(args):
             ms.append(a.elapsed_time(b))
     t = float(np.mean(ms)) * 1e-3
     nseg = dp.rays.struct.n_segments
+    # the march alone on one full chunk (its kappa / j computed first, untimed), L2
+    # flushed before each repetition: segment-wavelengths per second and the
+    # effective gather bandwidth (8 B of kappa + j per segment-wavelength)
+    nk = min(p.chunk, p.grid.n)
+    kap, em = bufs[0]
+    R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, 0, nk, R.FP32, kap, em)
+    qlam = torch.empty((dp.P, nk), dtype=torch.float32, device=ctx.device)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=ctx.device)
+    mm = []
+    for rep in range(4):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        R.trace_rays(ctx, dp.rays, dp.C, kap, em, p.grid, 0, nk, R.FP32, qlam)
+        b.record(ctx.stream)
+        ctx.sync()
+        if rep:
+            mm.append(a.elapsed_time(b))
+    tm = float(np.mean(mm)) * 1e-3
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gather = nseg * nk * 8 / tm / 1e9
+    march = {"kernel": "k_march (single-direction rays)", "chunk_points": nk, "kernel_ms": tm * 1e3,
+             "ray_lambda_segments_per_s": nseg * nk / tm, "gather_GBps_effective": gather,
+             "hbm_peak_GBps": hbm, "gather_over_hbm_peak": gather / hbm,
+             "unique_kappa_j_bytes": dp.C * nk * 8,
+             "note": "kappa / j rows are gathered from L2 (one DRAM pass per chunk): bound by issue, not HBM"}
     g = p.geometry
     desc = (f"afterbody {len(g.xf) - 1}x{len(g.rf) - 1} cells, {len(p.lines) // 1000}k lines, {p.grid.n:.0e} points "
             f"in {p.chunk}-point chunks, {len(g.surf_x)} points x {len(g.mu) * g.n_phi} rays")
     print(json.dumps({"workload": desc, "warmup": args.warmup, "steps": max(1, args.steps), "ms_per_solve": t * 1e3,
                       "cell_lambda_per_s": dp.C * p.grid.n / t, "ray_lambda_segments_per_s": nseg * p.grid.n / t,
-                      "segments": int(nseg), "q_mean_W_cm2": float(out["q"].mean().item()), "clocks": clk.summary()}))
+                      "segments": int(nseg), "q_mean_W_cm2": float(out["q"].mean().item()), "clocks": clk.summary(),
+                      "march": march}))
     return 0
 
 
