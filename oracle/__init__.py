@@ -96,6 +96,7 @@ def lib():
                                          vp, vp, vp]),
                 "orc_axisym_segments": (i64, [vp, i32, vp, i32, d, d, d, d, d, i64, vp, vp]),
                 "orc_march": (None, [i64, vp, vp, d, vp, vp, i64, i64, i32, d, P(_Grid), i64, d, vp]),
+                "orc_march_nodes": (None, [i64, vp, vp, vp, vp, i64, i64, i32, d, P(_Grid), i64, d, vp]),
                 "orc_spectral_integral": (d, [vp, P(_Grid), i64, i64]),
                 "orc_segment_coeffs": (None, [d, d, d, P(d), P(d)]),
                 "orc_num_threads": (ct.c_int, []),
@@ -253,6 +254,22 @@ def march(cells_far_to_near, ds, scale, kappa, emis, grid, k0=0, wall_start=Fals
     g = grid_struct(grid)
     lib().orc_march(cc.shape[0], _p(cc), _p(ds), float(scale), _p(kappa), _p(emis), nk, nk,
                     int(bool(wall_start)), float(T_wall), ct.byref(g), int(k0), float(thin), _p(out))
+    return out
+
+
+def march_nodes(nodes_far_to_near, ds, kappa, emis, grid, k0=0, wall_start=False, T_wall=0.0, thin=THIN_FP64):
+    """Intensity at the near end of one LOS whose kappa / j are given at its
+    len(ds) + 1 nodes (rows of the tables), for every column."""
+    nn = np.ascontiguousarray(nodes_far_to_near, np.int64)
+    ds = np.ascontiguousarray(ds, np.float64)
+    kappa = np.ascontiguousarray(kappa, np.float64)
+    emis = np.ascontiguousarray(emis, np.float64)
+    assert nn.shape[0] == ds.shape[0] + 1
+    nk = kappa.shape[1]
+    out = np.zeros(nk)
+    g = grid_struct(grid)
+    lib().orc_march_nodes(ds.shape[0], _p(nn), _p(ds), _p(kappa), _p(emis), nk, nk, int(bool(wall_start)),
+                          float(T_wall), ct.byref(g), int(k0), float(thin), _p(out))
     return out
 
 

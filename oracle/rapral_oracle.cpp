@@ -445,6 +445,28 @@ void orc_march(int64_t m, const int64_t* cell, const double* ds, double scale,
     }
 }
 
+// Sec. 2.2.3 march on LOS nodes: the tables hold kappa and j at the nodes
+// themselves (flow variables interpolated to the node, then the spectral
+// coefficients evaluated there).  Segment i runs from node[i] (far) to
+// node[i + 1] (near): kappa constant at the far node's value, j linear
+// between the two nodes, with the far/near coefficients of orc_segment_coeffs.
+void orc_march_nodes(int64_t m, const int64_t* node, const double* ds, const double* kappa, const double* emis,
+                     int64_t ld, int64_t nk, int32_t wall_start, double T_wall, const orc_grid* g, int64_t k0,
+                     double thin, double* I_out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nk; ++k) {
+        double I = wall_start ? orc_planck(grid_lam(g, k0 + k), T_wall) : 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            const double kap = kappa[node[i] * ld + k];
+            const double jf = emis[node[i] * ld + k], jn = emis[node[i + 1] * ld + k];
+            double a, b;
+            orc_segment_coeffs(kap, ds[i], thin, &a, &b);
+            I = I * std::exp(-kap * ds[i]) + a * jf + b * jn;
+        }
+        I_out[k] = I;
+    }
+}
+
 // Sec. 2.2.3 wall flux, spectral part: trapezoid rule on the uniform grid with
 // lam in um (1e-3 per nm); end weights are those of the whole grid, so chunks
 // of one grid add up to the full integral.
