@@ -48,8 +48,10 @@ def parse():
     ap.add_argument("--serve-fp64-requests", type=int, default=4)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
-    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch"], default="stagnation",
-                    help="stagnation line (the bench line); afterbody / batch: one-off measurements")
+    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci"], default="stagnation",
+                    help="stagnation line (the bench line); afterbody / batch / fibonacci: one-off measurements")
+    ap.add_argument("--fib-points", type=int, default=8, help="fibonacci workload: surface points")
+    ap.add_argument("--fib-los", type=int, default=128, help="fibonacci workload: Fibonacci directions per point")
     ap.add_argument("--ab-small", action="store_true",
                     help="afterbody workload at 100 x 50 cells, 20 points, 2e5 grid points (profiler captures)")
     ap.add_argument("--cells", type=int, default=200,
@@ -322,6 +324,62 @@ def run_batch(args):
     return 0
 
 
+def run_fibonacci(args):
+    """The paper's own angular path on the afterbody at 100 x 50 cells (2e5
+    points in 65,536-point chunks): Fibonacci lines of sight from
+    --fib-points surface points, flow variables at their nodes, kappa / j at
+    every node, the node march, and the flux from a 33 x 65 (phi, theta)
+    grid; FP32.  For comparison the same points with 16-mu x 32-azimuth rays
+    through per-cell coefficients."""
+    import torch
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver, synth
+    P = args.fib_points
+    p = synth.afterbody(nx=100, nr=50, n_points=P, n_grid=200_000)
+    ctx = R.Context(0)
+    sp = R.DeviceSpecies(p.species, ctx.device)
+    ln = R.DeviceLines(p.lines, ctx.device)
+    run = lambda: solver.solve_fibonacci(p, ctx, args.fib_los, 33, 65, R.FP32, chunk=p.chunk, species=sp, lines=ln)
+    for _ in range(max(1, args.warmup)):
+        out = run()
+    ctx.sync()
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(max(1, args.steps)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            out = run()
+            b.record(ctx.stream)
+            ctx.sync()
+            ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms)) * 1e-3
+    rays = out["rays"]
+    # the per-cell path on the same points: coefficients once per cell, shared by all rays
+    dp = solver.DeviceProblem(p, ctx, lines=ln, species=sp)
+    bufs = [(torch.empty((dp.C, p.chunk), dtype=torch.float32, device=ctx.device),
+             torch.empty((dp.C, p.chunk), dtype=torch.float32, device=ctx.device))]
+    solver.solve(dp, ctx, R.FP32, chunk=p.chunk, buffers=bufs)
+    ctx.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(ctx.stream)
+    cell = solver.solve(dp, ctx, R.FP32, chunk=p.chunk, buffers=bufs)
+    b.record(ctx.stream)
+    ctx.sync()
+    tc = a.elapsed_time(b) * 1e-3
+    print(json.dumps({
+        "workload": f"afterbody 100x50 cells, {len(p.lines) // 1000}k lines, {p.grid.n:.0e} points in "
+                    f"{p.chunk}-point chunks; {P} points x {args.fib_los} Fibonacci LOS ({rays.n_dirs // max(P, 1)} "
+                    f"leave the body), 33 x 65 (phi, theta) grid, FP32",
+        "warmup": args.warmup, "steps": max(1, args.steps), "ms_per_solve": t * 1e3,
+        "nodes": int(rays.n_nodes), "lines_of_sight": int(rays.n_dirs), "segments": int(rays.struct.n_segments),
+        "node_lambda_per_s": rays.n_nodes * p.grid.n / t,
+        "ray_lambda_segments_per_s": rays.struct.n_segments * p.grid.n / t,
+        "q_mean_W_cm2": float(out["q"].mean().item()), "clocks": clk.summary(),
+        "per_cell_path": {"rays": "16 mu x 32 azimuths", "ms_per_solve": tc * 1e3, "cells": dp.C,
+                          "q_mean_W_cm2": float(cell["q"].mean().item())}}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -330,6 +388,8 @@ def main():
         return run_afterbody(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "fibonacci":
+        return run_fibonacci(args)
     import torch
     import torch.distributed as dist
 

@@ -133,7 +133,7 @@ typedef struct {
  * 1 for a single line of sight) and carries its weight in the angular sum
  * q_lambda[p] = sum_dir weight * I_dir (Sec. 2.2.3).  Bundles of surface
  * point p are [point_off[p], point_off[p+1]).  The caller owns every array;
- * rapral_slab_rays / rapral_axisym_rays fill them. */
+ * rapral_slab_rays / rapral_axisym_rays / rapral_fibonacci_rays fill them. */
 typedef struct {
     int64_t n_bundles;          /* B                                          */
     int64_t n_points;           /* P                                          */
@@ -150,6 +150,14 @@ typedef struct {
     const double* dir_weight;   /* [n_dirs]                                   */
     const int32_t* bundle_wall; /* [B] 1: the far end is a wall at T_wall     */
     double T_wall;              /* K                                          */
+    /* 0: kappa / emis rows are cells, seg_cell names the cell of each
+     *    segment and node values are face averages of adjacent cells;
+     * 1: rows are LOS nodes (Sec. 2.2.3: flow variables interpolated to
+     *    the nodes, coefficients evaluated there): segment s of bundle b
+     *    runs from node s + b (far) to node s + b + 1 (near), kappa held at
+     *    the far node and j linear between the two; bundles of one
+     *    direction only. */
+    int32_t node_values;
 } rapral_rays;
 
 #define RAPRAL_MAX_SPECIES 32
@@ -395,6 +403,58 @@ RAPRAL_API int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx,
                        int64_t* seg_off, int64_t* n_segments, int32_t* seg_cell, double* seg_ds,
                        int64_t* point_off, int64_t* dir_off, double* dir_scale,
                        double* dir_weight, int32_t* bundle_wall, rapral_rays* rays);
+
+/* ----------------------------------------------- Fibonacci lines of sight -- */
+
+/* Lines of sight of the paper's own angular path (Sec. 2.2.3, Fibonacci
+ * sphere): from each surface point (surf_x[p], r_body = rf[0]) the n_los
+ * directions (r cos a, w, r sin a) with w = 1 - 2 (i - 1)/(n_los - 1),
+ * r = sqrt(1 - w^2), a = (i - 1)(sqrt(5) - 1) pi, i = 1 .. n_los, in the
+ * frame x along the axis, y the outward normal at the point, z completing
+ * it.  Only the V directions with w > 0 (leaving the body) are kept,
+ * V = floor(n_los / 2); point p owns bundles [p V, (p + 1) V), each one
+ * direction (scale 1, weight 1), los_index[b] = i - 1.  A line's nodes are
+ * where its projection onto the (x, r) plane crosses a cell face, plus its
+ * two ends: bundle b has seg_off[b+1] - seg_off[b] segments between nodes
+ * seg_off[b] + b (far boundary) .. seg_off[b+1] + b (the surface point),
+ * whose (x, r) go to node_x / node_r; seg_cell[s] = s + b (the far node)
+ * and the set has node_values = 1.  n_los in 2 .. 65536.
+ * Two calls as rapral_axisym_rays: with seg_cell == NULL it writes seg_off
+ * [B+1] (B = P V) and *n_segments (host; synchronises); the second call
+ * fills seg_cell / seg_ds [n_segments], point_off [P+1], dir_off [B+1],
+ * dir_scale / dir_weight / bundle_wall / los_index [B] and node_x / node_r
+ * [n_segments + B] (all device, caller-owned) and `rays`. */
+RAPRAL_API int rapral_fibonacci_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf,
+                       int32_t nr, const double* surf_x, int32_t n_points, int32_t n_los,
+                       int64_t* seg_off, int64_t* n_segments, int32_t* seg_cell, double* seg_ds,
+                       int64_t* point_off, int64_t* dir_off, double* dir_scale, double* dir_weight,
+                       int32_t* bundle_wall, int32_t* los_index, double* node_x, double* node_r,
+                       rapral_rays* rays);
+
+/* Flow variables at LOS nodes (Sec. 2.2.3, interpolation of the cell-centred
+ * flowfield to the nodes): inverse-distance weights 1/d^2 over the 2 x 2
+ * block of cell centres around (node_x, node_r), the block clamped to the
+ * grid; a node on a centre takes that cell's values.  `cells` are the
+ * grid's nx * nr cells numbered ix * nr + jr (lnpref not used).  Writes
+ * Ttr, Tve [n_nodes] and n [n_nodes][cells->n_cols] (device). */
+RAPRAL_API int rapral_los_node_states(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                       const rapral_cells* cells, int64_t n_nodes, const double* node_x,
+                       const double* node_r, double* Ttr, double* Tve, double* n);
+
+/* Wall flux from per-LOS results (Sec. 2.2.3 angular integral): for each
+ * point, S (the wavelength integral of a line's intensity, e.g. from
+ * rapral_wall_flux over the lines' intensities) is carried to the grid
+ * phi_q = (pi/2) q / (n_phi - 1), theta_t = 2 pi t / (n_theta - 1) (phi
+ * from the outward normal) by inverse-distance weights 1/|v - g|^2 over the
+ * point's 4 nearest line directions v (a grid direction on a line takes its
+ * S), then q[p] = sum_t sum_q (1/4)(S_{q,t} + S_{q+1,t} + S_{q,t+1} +
+ * S_{q+1,t+1}) (cos^2 phi_q - cos^2 phi_{q+1}) / 2 (theta_{t+1} - theta_t).
+ * point_off [P+1] (bundles of each point), los_index [B] and S [B] as from
+ * rapral_fibonacci_rays; q [P] FP64 is written (device).  n_phi, n_theta
+ * >= 2, n_phi n_theta <= 2^20. */
+RAPRAL_API int rapral_fibonacci_flux(rapral_ctx* ctx, int64_t n_points, const int64_t* point_off,
+                       const int32_t* los_index, int32_t n_los, const double* S, int32_t n_phi,
+                       int32_t n_theta, double* q);
 
 #ifdef __cplusplus
 }

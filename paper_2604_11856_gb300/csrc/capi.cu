@@ -49,6 +49,7 @@ static const char* check_name(int c) {
         case CHK_SEG_DS: return "segment length negative or not finite";
         case CHK_DIR: return "direction scale not positive";
         case CHK_TIMEOUT: return "bounded device wait expired";
+        case CHK_LOS_INDEX: return "line-of-sight index out of range";
         default: return "device check";
     }
 }
@@ -344,6 +345,11 @@ int rapral_trace_rays(rapral_ctx* ctx, const rapral_rays* rays, int64_t n_cells,
         !rays->bundle_wall || (rays->n_segments > 0 && (!rays->seg_cell || !rays->seg_ds)))
         return set_error(ctx, RAPRAL_EINVAL, "null ray array");
     if (rays->bundle_wall && !(rays->T_wall >= 0.0)) return set_error(ctx, RAPRAL_EINVAL, "T_wall");
+    if (rays->node_values != 0 && rays->node_values != 1) return set_error(ctx, RAPRAL_EINVAL, "node_values");
+    if (rays->node_values && rays->max_dirs > 1)
+        return set_error(ctx, RAPRAL_EINVAL, "node-valued rays need bundles of one direction");
+    if (rays->node_values && n_cells < rays->n_segments + rays->n_bundles)
+        return set_error(ctx, RAPRAL_EINVAL, "node-valued rays need n_segments + n_bundles rows");
     cudaSetDevice(ctx->device);
     const Phys ph = make_phys(ctx->codata);
     st = ws_reserve(ctx, march_scratch_bytes(rays, nk, precision));
@@ -394,7 +400,7 @@ int rapral_slab_rays(rapral_ctx* ctx, const int32_t* cell_order, const double* d
     rays->max_dirs = nd < RAPRAL_SLAB_DIRS ? nd : RAPRAL_SLAB_DIRS; rays->max_bundles_per_point = nb;
     rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
     rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
-    rays->bundle_wall = bundle_wall; rays->T_wall = T_wall;
+    rays->bundle_wall = bundle_wall; rays->T_wall = T_wall; rays->node_values = 0;
     return RAPRAL_OK;
 }
 
@@ -431,8 +437,75 @@ int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const doub
     rays->max_bundles_per_point = n_mu * n_phi;
     rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
     rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
-    rays->bundle_wall = bundle_wall; rays->T_wall = 0.0;
+    rays->bundle_wall = bundle_wall; rays->T_wall = 0.0; rays->node_values = 0;
     return RAPRAL_OK;
+}
+
+int rapral_fibonacci_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                          const double* surf_x, int32_t n_points, int32_t n_los, int64_t* seg_off,
+                          int64_t* n_segments, int32_t* seg_cell, double* seg_ds, int64_t* point_off,
+                          int64_t* dir_off, double* dir_scale, double* dir_weight, int32_t* bundle_wall,
+                          int32_t* los_index, double* node_x, double* node_r, rapral_rays* rays) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!xf || !rf || !surf_x || !seg_off || !n_segments) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (nx < 1 || nr < 1 || n_points < 0 || n_los < 2 || n_los > 65536)
+        return set_error(ctx, RAPRAL_EINVAL, "grid counts, or n_los not in 2 .. 65536");
+    if ((int64_t)nx * nr > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "too many cells");
+    cudaSetDevice(ctx->device);
+    const int64_t B = (int64_t)n_points * (n_los / 2);
+    cudaError_t e;
+    if (!seg_cell) {
+        e = launch_fib_count(ctx, xf, nx, rf, nr, surf_x, n_points, n_los, seg_off);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_pinned, seg_off + B, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_status(ctx, e, "Fibonacci ray count");
+        *n_segments = reinterpret_cast<int64_t*>(ctx->h_pinned)[0];
+        if (*n_segments + B > 2147483647LL) return set_error(ctx, RAPRAL_EINVAL, "more than 2^31 LOS nodes");
+        return RAPRAL_OK;
+    }
+    if (!seg_ds || !point_off || !dir_off || !dir_scale || !dir_weight || !bundle_wall || !los_index || !node_x ||
+        !node_r || !rays)
+        return set_error(ctx, RAPRAL_EINVAL, "null output array");
+    e = launch_fib_fill(ctx, xf, nx, rf, nr, surf_x, n_points, n_los, seg_off, seg_cell, seg_ds, point_off, dir_off,
+                        dir_scale, dir_weight, bundle_wall, los_index, node_x, node_r);
+    if (e != cudaSuccess) return cuda_status(ctx, e, "Fibonacci rays");
+    rays->n_bundles = B; rays->n_points = n_points; rays->n_segments = *n_segments; rays->n_dirs = B;
+    rays->max_dirs = 1;
+    rays->max_bundles_per_point = n_los / 2;
+    rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
+    rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
+    rays->bundle_wall = bundle_wall; rays->T_wall = 0.0; rays->node_values = 1;
+    return RAPRAL_OK;
+}
+
+int rapral_los_node_states(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                           const rapral_cells* cells, int64_t n_nodes, const double* node_x, const double* node_r,
+                           double* Ttr, double* Tve, double* n) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!xf || !rf || !cells || (n_nodes > 0 && (!node_x || !node_r || !Ttr || !Tve || !n)))
+        return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (nx < 1 || nr < 1 || n_nodes < 0) return set_error(ctx, RAPRAL_EINVAL, "grid or node counts");
+    if (cells->n_cells != (int64_t)nx * nr) return set_error(ctx, RAPRAL_EINVAL, "cells != nx * nr");
+    if (cells->n_cols < 1 || !cells->Ttr || !cells->Tve || !cells->n)
+        return set_error(ctx, RAPRAL_EINVAL, "cell arrays");
+    cudaSetDevice(ctx->device);
+    return cuda_status(ctx, launch_node_idw(ctx, xf, nx, rf, nr, cells, n_nodes, node_x, node_r, Ttr, Tve, n),
+                       "LOS node states");
+}
+
+int rapral_fibonacci_flux(rapral_ctx* ctx, int64_t n_points, const int64_t* point_off, const int32_t* los_index,
+                          int32_t n_los, const double* S, int32_t n_phi, int32_t n_theta, double* q) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!point_off || !los_index || !S || !q) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (n_points < 0 || n_los < 2 || n_los > 65536 || n_phi < 2 || n_theta < 2 ||
+        (int64_t)n_phi * n_theta > (1 << 20))
+        return set_error(ctx, RAPRAL_EINVAL, "counts out of range");
+    cudaSetDevice(ctx->device);
+    int st = ws_reserve(ctx, fib_flux_scratch_bytes(n_points, n_los, n_phi, n_theta));
+    if (st) return st;
+    return cuda_status(ctx, launch_fib_flux(ctx, n_points, point_off, los_index, n_los, S, n_phi, n_theta, q, ctx->ws),
+                       "Fibonacci flux");
 }
 
 }  // extern "C"

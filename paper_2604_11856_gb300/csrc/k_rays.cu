@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "rapral_internal.cuh"
+#include "geom.cuh"
 
 namespace {
 
@@ -191,6 +192,61 @@ template <class T> struct __align__(16) SegStage {
 #endif
 constexpr int kUnroll = RAPRAL_MARCH_UNROLL;
 
+// Node-valued rays (one direction): rows are the LOS nodes, segment s of
+// bundle b runs from node s + b to node s + b + 1, kappa held at the far
+// node, j linear between the nodes (the same coefficients).
+template <class T, int V>
+__device__ __forceinline__ void march_nodes(const MarchArgs& a, int64_t b, T sc, SegStage<T>* stage, int lane,
+                                            const char* kbase, int64_t ldb, int64_t offK, int64_t offJ,
+                                            T (&I)[V][1]) {
+    const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
+    if (s1 <= s0) return;
+    T kf[V], jf[V];
+    {
+        const char* row = kbase + (s0 + b) * ldb;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            kf[v] = *reinterpret_cast<const T*>(row + offK + 32 * v * sizeof(T));
+            jf[v] = *reinterpret_cast<const T*>(row + offJ + 32 * v * sizeof(T));
+        }
+    }
+    for (int64_t g = s0; g < s1; g += 32) {
+        const int64_t mine = g + lane;
+        __syncwarp();
+        const bool in = mine < s1;
+        stage[lane].row = in ? kbase + (mine + 1 + b) * ldb : kbase;
+        stage[lane].ds = in ? seg_len<T>(a, mine) * sc : T(0);
+        if (lane == 0) stage[32].row = kbase;
+        __syncwarp();
+        const int n = s1 - g < 32 ? (int)(s1 - g) : 32;
+        T kx[V], jx[V];
+        {
+            const char* r0 = stage[0].row;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                kx[v] = *reinterpret_cast<const T*>(r0 + offK + 32 * v * sizeof(T));
+                jx[v] = *reinterpret_cast<const T*>(r0 + offJ + 32 * v * sizeof(T));
+            }
+        }
+        for (int j = 0; j < n; ++j) {
+            const T ds = stage[j].ds;
+            const char* rn = stage[j + 1].row;
+            T ky[V], jy[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                ky[v] = *reinterpret_cast<const T*>(rn + offK + 32 * v * sizeof(T));
+                jy[v] = *reinterpret_cast<const T*>(rn + offJ + 32 * v * sizeof(T));
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                seg_step(I[v][0], kf[v], ds, jf[v], jx[v]);
+                kf[v] = kx[v]; jf[v] = jx[v];
+                kx[v] = ky[v]; jx[v] = jy[v];
+            }
+        }
+    }
+}
+
 template <class T, int V, int MAXD>
 __device__ __forceinline__ void march_bundle(const MarchArgs& a, int64_t b, int64_t d0, int nd, SegStage<T>* stage,
                                              int lane, const char* kbase, int64_t ldb, int64_t offK, int64_t offJ,
@@ -299,11 +355,12 @@ __device__ __forceinline__ void march_bundle(const MarchArgs& a, int64_t b, int6
 #ifndef RAPRAL_MARCH_MINB17
 #define RAPRAL_MARCH_MINB17 3
 #endif
-template <class T, int V, int MAXD, int SL>
+template <class T, int V, int MAXD, int SL, bool NODES = false>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && MAXD == 1 && V > 1)  ? RAPRAL_MARCH_MINB
                                        : (sizeof(T) == 4 && MAXD == 17) ? RAPRAL_MARCH_MINB17
                                                                         : 1)
     k_march(MarchArgs a, int lgG, T* __restrict__ part) {
+    static_assert(!NODES || MAXD == 1, "node-valued rays have one direction a bundle");
     if (*a.status) return;
     constexpr int W = 8, CW = W / SL, TW = CW * 32 * V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -334,7 +391,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && MAXD == 1 && V > 1)  ?
         const int nd = (int)(a.dir_off[b + 1] - d0);
         if (nd == 0) continue;
         T I[V][MAXD];
-        march_bundle<T, V, MAXD>(a, b, d0, nd, stage, lane, kbase, ldb, offK, offJ, col0, I);
+        if constexpr (NODES) {
+            const bool wall = a.wall_row && a.bundle_wall[b];
+#pragma unroll
+            for (int v = 0; v < V; ++v) I[v][0] = wall ? reinterpret_cast<const T*>(a.wall_row)[col0 + 32 * v] : T(0);
+            march_nodes<T, V>(a, b, dir_val<T>(a.dir_scale, a.dir_scale_f, d0), stage, lane, kbase, ldb, offK, offJ,
+                              I);
+        } else {
+            march_bundle<T, V, MAXD>(a, b, d0, nd, stage, lane, kbase, ldb, offK, offJ, col0, I);
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int kk = colu + 32 * v;
@@ -464,48 +529,6 @@ __global__ void k_slab_rays(const int32_t* cell_order, const double* dx, int32_t
     if (threadIdx.x == 0) { point_off[0] = 0; point_off[1] = nb; }
 }
 
-// Ray from the surface point (x0, rb): position x = x0 + t dx, radius
-// sqrt((rb + t dn)^2 + (t dt)^2) (non-decreasing for dn > 0).  Walks the
-// rectilinear (x, r) cells from the point outward, stepping to whichever face
-// (x or r) comes first; emits (cell, length) for every piece of positive
-// length.  With out_cell != nullptr the pieces are written backwards from
-// out_end - 1 (so the list runs from the far boundary to the point).
-__device__ int64_t walk_ray(const double* xf, int nx, const double* rf, int nr, double x0, double rb, double dx,
-                            double dn, double dt, int32_t* out_cell, double* out_ds, int64_t out_end) {
-    if (!(x0 >= xf[0] && x0 <= xf[nx])) return 0;
-    int lo = 0, hi = nx;   // largest ix with xf[ix] <= x0
-    while (hi - lo > 1) { int m = (lo + hi) >> 1; if (xf[m] <= x0) lo = m; else hi = m; }
-    int ix = lo;
-    if (x0 == xf[ix] && dx < 0.0) ix -= 1;
-    if (ix >= nx) ix = nx - 1;
-    int jr = 0;
-    const double A = dn * dn + dt * dt, B = 2.0 * rb * dn;
-    double t = 0.0;
-    int64_t n = 0;
-    const int guard = 2 * (nx + nr) + 8;
-    for (int it = 0; it < guard && ix >= 0 && ix < nx && jr < nr; ++it) {
-        double tx = INFINITY;
-        if (dx > 0.0) tx = (xf[ix + 1] - x0) / dx;
-        else if (dx < 0.0) tx = (xf[ix] - x0) / dx;
-        double tr = INFINITY;
-        if (A > 0.0) {
-            const double rr = rf[jr + 1];
-            const double cq = rb * rb - rr * rr;                 // <= 0
-            tr = (-2.0 * cq) / (B + sqrt(B * B - 4.0 * A * cq));  // cancellation-free root
-        }
-        const double tn = fmin(tx, tr);
-        const double len = tn - t;
-        if (len > 0.0) {
-            if (out_cell) { out_cell[out_end - 1 - n] = ix * nr + jr; out_ds[out_end - 1 - n] = len; }
-            ++n;
-            t = tn;
-        }
-        if (tx <= tr) ix += (dx > 0.0) ? 1 : -1;
-        if (tr <= tx) jr += 1;
-    }
-    return n;
-}
-
 __device__ __forceinline__ void ray_dir(int64_t b, int32_t n_mu, int32_t n_phi, const double* mu, int64_t* p,
                                         int* m, double* dx, double* dn, double* dt) {
     const int64_t per = (int64_t)n_mu * n_phi;
@@ -553,7 +576,7 @@ __global__ void k_axisym_fill(const double* xf, int32_t nx, const double* rf, in
 #define RAPRAL_MARCH_V 2
 #endif
 
-template <class T, int V, int MAXD, int SL>
+template <class T, int V, int MAXD, int SL, bool NODES = false>
 cudaError_t march_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int G, void* part) {
     constexpr int TW = (8 / SL) * 32 * V;
     int lgG = 0;
@@ -567,7 +590,7 @@ cudaError_t march_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t
         b.wall_row = row;
     }
     dim3 g((unsigned)(P << lgG), div_up(nk, TW));
-    k_march<T, V, MAXD, SL><<<g, 256, 0, ctx->stream>>>(b, lgG, reinterpret_cast<T*>(part));
+    k_march<T, V, MAXD, SL, NODES><<<g, 256, 0, ctx->stream>>>(b, lgG, reinterpret_cast<T*>(part));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || G == 1) return e;
     k_group_sum<T><<<(unsigned)std::min<int64_t>(div_up(P * nk, 256), 152 * 16), 256, 0, ctx->stream>>>(
@@ -580,8 +603,13 @@ cudaError_t march_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t
 // least one tile.
 template <class T>
 cudaError_t march_t(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int maxd, int maxb, int G,
-                    void* part) {
+                    void* part, bool nodes) {
     constexpr int VR = sizeof(T) == 4 ? RAPRAL_MARCH_V : 1;
+    if (nodes) {   // node-valued lines of sight: one direction a bundle (checked by the caller)
+        if (maxb < 8) return march_launch<T, 1, 1, 1, true>(ctx, a, P, nk, G, part);
+        if (VR > 1 && nk >= 32 * VR) return march_launch<T, VR, 1, 8, true>(ctx, a, P, nk, G, part);
+        return march_launch<T, 1, 1, 8, true>(ctx, a, P, nk, G, part);
+    }
     if (maxb >= 8) {
         if (maxd <= 1) {
             if (VR > 1 && nk >= 32 * VR) return march_launch<T, VR, 1, 8>(ctx, a, P, nk, G, part);
@@ -643,7 +671,8 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
     a.q_lambda = q_lambda; a.I_out = I_out; a.ph = ph; a.status = ctx->d_status;
     const int G = march_groups(r);
     if (precision == RAPRAL_FP64)
-        return march_t<double>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, scratch);
+        return march_t<double>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, scratch,
+                               r->node_values != 0);
     // FP32 copies of the path lengths, direction scales and weights, then the group partials
     float* f = reinterpret_cast<float*>(scratch);
     void* part = reinterpret_cast<char*>(scratch) +
@@ -660,7 +689,8 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
             r->dir_weight, r->n_dirs, fw);
     }
     a.seg_ds_f = f; a.dir_scale_f = fd; a.dir_weight_f = fw;
-    return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, part);
+    return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, part,
+                          r->node_values != 0);
 }
 
 int64_t wall_flux_parts(int64_t nk) { return (nk + FLUX_SPAN - 1) / FLUX_SPAN; }

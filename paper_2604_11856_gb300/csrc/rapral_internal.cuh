@@ -39,7 +39,7 @@ inline Phys make_phys(int codata) {
 enum { ST_CODE = 0, ST_CHECK = 1, ST_INDEX = 2 };
 enum {
     CHK_NONE = 0, CHK_CELL_T, CHK_CELL_N, CHK_LINE_SPECIES, CHK_LINE_LAM, CHK_LINE_G,
-    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT
+    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT, CHK_LOS_INDEX
 };
 
 // ------------------------------------------------------------- records ----
@@ -260,4 +260,20 @@ cudaError_t launch_axisym_fill(rapral_ctx* ctx, const double* xf, int32_t nx, co
 // Exclusive scan of int64 counts in place over [0, n] (n + 1 entries; the
 // last entry receives the total); single block.
 cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n);
+
+// Fibonacci lines of sight, node states and the angular flux (k_los.cu).
+cudaError_t launch_fib_count(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                             const double* surf_x, int32_t P, int32_t n_los, int64_t* seg_off);
+cudaError_t launch_fib_fill(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                            const double* surf_x, int32_t P, int32_t n_los, const int64_t* seg_off,
+                            int32_t* seg_cell, double* seg_ds, int64_t* point_off, int64_t* dir_off,
+                            double* dir_scale, double* dir_weight, int32_t* bundle_wall, int32_t* los_index,
+                            double* node_x, double* node_r);
+cudaError_t launch_node_idw(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,
+                            const rapral_cells* cells, int64_t n_nodes, const double* node_x, const double* node_r,
+                            double* Ttr, double* Tve, double* n);
+size_t fib_flux_scratch_bytes(int64_t P, int32_t n_los, int32_t n_phi, int32_t n_theta);
+cudaError_t launch_fib_flux(rapral_ctx* ctx, int64_t P, const int64_t* point_off, const int32_t* los_index,
+                            int32_t n_los, const double* S, int32_t n_phi, int32_t n_theta, double* q,
+                            void* scratch);
 cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n);

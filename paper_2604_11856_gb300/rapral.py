@@ -67,7 +67,8 @@ class Rays(ct.Structure):
                 ("n_dirs", ct.c_int64), ("max_dirs", ct.c_int32), ("max_bundles_per_point", ct.c_int32),
                 ("point_off", ct.c_void_p), ("seg_off", ct.c_void_p), ("seg_cell", ct.c_void_p),
                 ("seg_ds", ct.c_void_p), ("dir_off", ct.c_void_p), ("dir_scale", ct.c_void_p),
-                ("dir_weight", ct.c_void_p), ("bundle_wall", ct.c_void_p), ("T_wall", ct.c_double)]
+                ("dir_weight", ct.c_void_p), ("bundle_wall", ct.c_void_p), ("T_wall", ct.c_double),
+                ("node_values", ct.c_int32)]
 
 
 class BatchItem(ct.Structure):
@@ -120,6 +121,10 @@ def load(build_if_missing=True):
                                      P(Rays)]),
             "rapral_axisym_rays": (i, [vp, vp, i32, vp, i32, vp, i32, vp, vp, i32, i32, vp, P(i64), vp, vp, vp,
                                        vp, vp, vp, vp, P(Rays)]),
+            "rapral_fibonacci_rays": (i, [vp, vp, i32, vp, i32, vp, i32, i32, vp, P(i64), vp, vp, vp, vp, vp, vp,
+                                          vp, vp, vp, vp, P(Rays)]),
+            "rapral_los_node_states": (i, [vp, vp, i32, vp, i32, P(Cells), i64, vp, vp, vp, vp, vp]),
+            "rapral_fibonacci_flux": (i, [vp, i64, vp, vp, i32, vp, i32, i32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -339,7 +344,7 @@ class DeviceRays:
 
 
 def rays_from_arrays(point_off, seg_off, seg_cell, seg_ds, dir_off, dir_scale, dir_weight, bundle_wall,
-                     T_wall, device):
+                     T_wall, device, node_values=False):
     """A caller-built ray set (host arrays in the rapral_rays layout) copied
     to the device; the maxima of directions per bundle and bundles per point
     are taken from the offsets."""
@@ -362,6 +367,7 @@ def rays_from_arrays(point_off, seg_off, seg_cell, seg_ds, dir_off, dir_scale, d
     for k in ("point_off", "seg_off", "seg_cell", "seg_ds", "dir_off", "dir_scale", "dir_weight", "bundle_wall"):
         setattr(s, k, t[k].data_ptr())
     s.T_wall = float(T_wall)
+    s.node_values = int(bool(node_values))
     return r
 
 
@@ -393,6 +399,72 @@ def slab_rays(ctx, geo, device):
                                        _ptr(t["dir_scale"]), _ptr(t["dir_weight"]), _ptr(t["bundle_wall"]),
                                        ct.byref(r.struct)))
     return r
+
+
+def fibonacci_rays(ctx, geo, n_los, device, points=None):
+    """The paper's Fibonacci lines of sight (rapral_fibonacci_rays) from an
+    AxisymGeometry's surface points (or the selected ones): node-valued rays
+    with per-line los_index and the (x, r) of every node in t["node_x"],
+    t["node_r"]."""
+    r = DeviceRays()
+    t = r.t
+    sx = np.asarray(geo.surf_x) if points is None else np.asarray(geo.surf_x)[np.asarray(points)]
+    P = int(len(sx)); V = int(n_los) // 2
+    B = P * V
+    nx, nr = len(geo.xf) - 1, len(geo.rf) - 1
+    t["xf"] = _t(geo.xf, np.float64, device); t["rf"] = _t(geo.rf, np.float64, device)
+    t["surf_x"] = _t(sx, np.float64, device)
+    t["seg_off"] = torch.empty(B + 1, dtype=torch.int64, device=device)
+    nseg = ct.c_int64()
+    args0 = [ctx.h, _ptr(t["xf"]), nx, _ptr(t["rf"]), nr, _ptr(t["surf_x"]), P, int(n_los), _ptr(t["seg_off"]),
+             ct.byref(nseg)]
+    ctx.check(ctx.lib.rapral_fibonacci_rays(*args0, *([None] * 10), None))
+    n = int(nseg.value)
+    t["seg_cell"] = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    t["seg_ds"] = torch.empty(max(n, 1), dtype=torch.float64, device=device)
+    t["point_off"] = torch.empty(P + 1, dtype=torch.int64, device=device)
+    t["dir_off"] = torch.empty(B + 1, dtype=torch.int64, device=device)
+    for k in ("dir_scale", "dir_weight"):
+        t[k] = torch.empty(max(B, 1), dtype=torch.float64, device=device)
+    t["bundle_wall"] = torch.empty(max(B, 1), dtype=torch.int32, device=device)
+    t["los_index"] = torch.empty(max(B, 1), dtype=torch.int32, device=device)
+    t["node_x"] = torch.empty(max(n + B, 1), dtype=torch.float64, device=device)
+    t["node_r"] = torch.empty(max(n + B, 1), dtype=torch.float64, device=device)
+    ctx.check(ctx.lib.rapral_fibonacci_rays(*args0, _ptr(t["seg_cell"]), _ptr(t["seg_ds"]), _ptr(t["point_off"]),
+                                            _ptr(t["dir_off"]), _ptr(t["dir_scale"]), _ptr(t["dir_weight"]),
+                                            _ptr(t["bundle_wall"]), _ptr(t["los_index"]), _ptr(t["node_x"]),
+                                            _ptr(t["node_r"]), ct.byref(r.struct)))
+    r.n_los = int(n_los)
+    r.n_nodes = n + B
+    return r
+
+
+def los_node_states(ctx, geo, dgrid_cells, rays, S, device):
+    """Flow variables at the rays' nodes (rapral_los_node_states) from the
+    grid's DeviceCells; returns DeviceCells of the nodes (S species columns
+    of ln(N_s / Z_s) to be filled by populations)."""
+    nx, nr = len(geo.xf) - 1, len(geo.rf) - 1
+    N = rays.n_nodes
+    nc = dgrid_cells.struct.n_cols
+    tens = dict(Ttr=torch.empty(max(N, 1), dtype=torch.float64, device=device),
+                Tve=torch.empty(max(N, 1), dtype=torch.float64, device=device),
+                n=torch.empty((max(N, 1), nc), dtype=torch.float64, device=device))
+    ctx.check(ctx.lib.rapral_los_node_states(ctx.h, _ptr(rays.t["xf"]), nx, _ptr(rays.t["rf"]), nr,
+                                             ct.byref(dgrid_cells.struct), int(N), _ptr(rays.t["node_x"]),
+                                             _ptr(rays.t["node_r"]), _ptr(tens["Ttr"]), _ptr(tens["Tve"]),
+                                             _ptr(tens["n"])))
+    if N == 0:
+        tens = {k: v[:0] for k, v in tens.items()}
+    dc = DeviceCells(None, S, device, tensors=tens)
+    dc.struct.ne_col = dgrid_cells.struct.ne_col
+    return dc
+
+
+def fibonacci_flux(ctx, rays, S_los, n_phi, n_theta, q):
+    """q[p] from the per-line wavelength integrals S_los (rapral_fibonacci_flux)."""
+    ctx.check(ctx.lib.rapral_fibonacci_flux(ctx.h, int(rays.n_points), _ptr(rays.t["point_off"]),
+                                            _ptr(rays.t["los_index"]), int(rays.n_los), _ptr(S_los), int(n_phi),
+                                            int(n_theta), _ptr(q)))
 
 
 def axisym_rays(ctx, geo, device, points=None):

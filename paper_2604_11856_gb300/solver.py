@@ -179,3 +179,44 @@ def solve_host(problem, precision=R.FP64, chunk=None, ctx=None, device=None):
         q_host.copy_(res["q"], non_blocking=True)
     ctx.sync()
     return q_host.numpy().copy(), nbytes, q_host.numel() * 8
+
+
+def solve_fibonacci(problem, ctx, n_los, n_phi, n_theta, precision=R.FP64, chunk=None, points=None,
+                    species=None, lines=None):
+    """The paper's own angular path (Sec. 2.2.3) for an axisymmetric problem:
+    Fibonacci lines of sight from the surface points (or the selected ones),
+    flow variables interpolated to their nodes, kappa / j at the nodes, the
+    node march, the per-line wavelength integral S and the flux from S on a
+    uniform (phi, theta) grid.  Returns a dict with q [P] (FP64, device), S
+    [lines] (FP64, device), the rays and the node cells; with one chunk also
+    the intensities I [lines, n] and the node tables kappa / emis."""
+    dev = ctx.device
+    geo = problem.geometry
+    sp = species if species is not None else R.DeviceSpecies(problem.species, dev)
+    ln = lines if lines is not None else R.DeviceLines(problem.lines, dev)
+    gcells = R.DeviceCells(problem.cells, sp.S, dev)
+    rays = R.fibonacci_rays(ctx, geo, n_los, dev, points)
+    ncells = R.los_node_states(ctx, geo, gcells, rays, sp.S, dev)
+    R.populations(ctx, sp, ncells)
+    N, B, P = rays.n_nodes, rays.n_dirs, rays.n_points
+    n = problem.grid.n
+    chunk = n if not chunk else min(chunk, n)
+    dt = _dtype(precision)
+    kap = torch.empty((max(N, 1), chunk), dtype=dt, device=dev)
+    em = torch.empty_like(kap)
+    Ibuf = torch.empty(max(B, 1) * chunk, dtype=dt, device=dev)
+    qbuf = torch.empty(max(P, 1) * chunk, dtype=dt, device=dev)
+    S = torch.zeros(max(B, 1), dtype=torch.float64, device=dev)
+    for k0 in range(0, n, chunk):
+        nk = min(chunk, n - k0)
+        I = Ibuf[:B * nk].view(B, nk)
+        R.spectral_coeffs(ctx, sp, ln, ncells, problem.grid, k0, nk, precision, kap, em)
+        R.trace_rays(ctx, rays, N, kap, em, problem.grid, k0, nk, precision, qbuf[:P * nk].view(P, nk), I)
+        R.wall_flux(ctx, I, precision, problem.grid, k0, nk, B, S)
+    q = torch.empty(max(P, 1), dtype=torch.float64, device=dev)
+    R.fibonacci_flux(ctx, rays, S, n_phi, n_theta, q)
+    out = dict(q=q[:P], S=S[:B], rays=rays, node_cells=ncells)
+    if chunk == n:
+        out["I"] = Ibuf[:B * n].view(B, n)
+        out["kappa"], out["emis"] = kap[:N], em[:N]
+    return out
