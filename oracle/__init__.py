@@ -97,6 +97,11 @@ def lib():
                 "orc_axisym_segments": (i64, [vp, i32, vp, i32, d, d, d, d, d, i64, vp, vp]),
                 "orc_march": (None, [i64, vp, vp, d, vp, vp, i64, i64, i32, d, P(_Grid), i64, d, vp]),
                 "orc_march_nodes": (None, [i64, vp, vp, vp, vp, i64, i64, i32, d, P(_Grid), i64, d, vp]),
+                "orc_set_broadening": (None, [ct.c_int, ct.c_int, vp, ct.c_int, vp]),
+                "orc_stark_coeff_ionize": (d, [d, d, d]),
+                "orc_oscillator_strength": (d, [d, d, d, d]),
+                "orc_resonance_hwhm": (d, [d, d, d, d, d]),
+                "orc_vdw_hwhm": (d, [d, d, d, d, d, d]),
                 "orc_spectral_integral": (d, [vp, P(_Grid), i64, i64]),
                 "orc_segment_coeffs": (None, [d, d, d, P(d), P(d)]),
                 "orc_num_threads": (ct.c_int, []),
@@ -169,6 +174,38 @@ def grid_struct(g):
 # ----------------------------------------------------------------------------
 # steps of the path
 # ----------------------------------------------------------------------------
+
+# Sec. 2.2.1 full Lorentz broadening switches (see orc_set_broadening)
+BROAD_STARK_IONIZE, BROAD_RESONANCE, BROAD_VDW = 1, 2, 4
+
+
+def set_broadening(flags, E_ionize=None, column_mass=None):
+    """Turns the optional Lorentz terms on for every later call (flags 0: the
+    natural + Stark width with the lines' own Stark coefficients).  E_ionize:
+    per radiating species, cm^-1; column_mass: per density column, g/mol (0
+    for electrons)."""
+    E = np.ascontiguousarray(E_ionize if E_ionize is not None else np.zeros(0), np.float64)
+    M = np.ascontiguousarray(column_mass if column_mass is not None else np.zeros(0), np.float64)
+    lib().orc_set_broadening(int(flags), E.shape[0], _p(E) if E.size else None, M.shape[0],
+                             _p(M) if M.size else None)
+    set_broadening._keep = (E, M)
+
+
+def stark_coeff_ionize(lam0, Eu, Eion):
+    return lib().orc_stark_coeff_ionize(float(lam0), float(Eu), float(Eion))
+
+
+def oscillator_strength(lam0, A, gu, gl):
+    return lib().orc_oscillator_strength(float(lam0), float(A), float(gu), float(gl))
+
+
+def resonance_hwhm(lam0, A, gu, gl, N0):
+    return lib().orc_resonance_hwhm(float(lam0), float(A), float(gu), float(gl), float(N0))
+
+
+def vdw_hwhm(lam0, Ttr, N, M, No, Mo):
+    return lib().orc_vdw_hwhm(float(lam0), float(Ttr), float(N), float(M), float(No), float(Mo))
+
 
 def lnpref(problem):
     """ln N_s - ln Z_s, [C, S] (Sec. 2.1 Boltzmann distributions)."""

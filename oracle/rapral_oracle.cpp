@@ -98,9 +98,11 @@ static double kB = 1.380e-16;   // erg/K
 static double cL = 2.998e10;    // cm/s
 static double hP = 6.626e-27;   // erg s
 
+static double me_g = 9.109e-28, e_esu = 4.803e-10;   // electron mass (g) and charge (esu)
+
 void orc_set_codata(int on) {
-    if (on) { kB = 1.380649e-16; cL = 2.99792458e10; hP = 6.62607015e-27; }
-    else    { kB = 1.380e-16;    cL = 2.998e10;      hP = 6.626e-27; }
+    if (on) { kB = 1.380649e-16; cL = 2.99792458e10; hP = 6.62607015e-27; me_g = 9.1093837e-28; e_esu = 4.80320471e-10; }
+    else    { kB = 1.380e-16;    cL = 2.998e10;      hP = 6.626e-27;      me_g = 9.109e-28;     e_esu = 4.803e-10; }
 }
 double orc_c2(void) { return hP * cL / kB; }   // second radiation constant, cm K
 double orc_const(int which) { return which == 0 ? kB : which == 1 ? cL : hP; }
@@ -177,8 +179,52 @@ double orc_stark_hwhm(double lamS0, double Tve, double ne) {
 }
 // Sec. 2.2.1: natural broadening constant.
 static const double LAM_N = 5.9e-6;
-// Sec. 2.2.1: Lorentz HWHM = natural + Stark (+ resonance + van der Waals, not taken).
+// Sec. 2.2.1: Lorentz HWHM = natural + Stark (+ resonance + van der Waals when
+// orc_set_broadening turns them on).
 double orc_lorentz_hwhm(double lamS) { return LAM_N + lamS; }
+
+// Sec. 2.2.1 full Lorentz broadening, off by default (flags 0):
+//   1: Stark coefficient of atomic lines from the ionisation gap,
+//      lamS0 = 1.69e3 lam^2 / dE^2.623, dE = max(E_ionize - E_u, E_ionize^H / 25);
+//   2: resonance broadening of atomic lines whose lower level is the ground
+//      level, lamR = 4.3e-28 lam f_lu N_0 (g_l/g_u)^0.5 lam^2 with the
+//      oscillator strength f_lu = m_e c (lam 1e-7)^2 g_u A / (8 pi^2 e^2 g_l)
+//      and N_0 the species' ground-level density;
+//   4: van der Waals broadening of atomic lines,
+//      lamW = lam^2 [6.65e-29 N (2 T_t/M)^0.5 + 2.925e-29 N_o (2 T_t/M_o)^0.5],
+//      N, M the radiating species' density and molar mass, N_o the summed
+//      density of the other heavy particles (every density column but the
+//      species' own and those of molar mass 0, the electrons) and M_o their
+//      density-weighted mean molar mass.
+static int BROAD_FLAGS = 0;
+static double BROAD_EION[64];      // per radiating species, cm^-1
+static int BROAD_NCOL = 0;
+static double BROAD_COLMASS[64];   // per density column, g/mol (0: electrons)
+static const double E_IONIZE_H = 109678.77;   // cm^-1
+
+void orc_set_broadening(int flags, int S, const double* E_ion, int ncol, const double* col_mass) {
+    BROAD_FLAGS = flags;
+    for (int s = 0; s < S && s < 64; ++s) BROAD_EION[s] = E_ion ? E_ion[s] : 0.0;
+    BROAD_NCOL = ncol < 64 ? ncol : 64;
+    for (int c = 0; c < BROAD_NCOL; ++c) BROAD_COLMASS[c] = col_mass ? col_mass[c] : 0.0;
+}
+double orc_stark_coeff_ionize(double lam0, double Eu, double Eion) {
+    const double dE = std::max(Eion - Eu, E_IONIZE_H / 25.0);
+    return 1.69e3 * lam0 * lam0 / std::pow(dE, 2.623);
+}
+double orc_oscillator_strength(double lam0, double A, double gu, double gl) {
+    const double lcm = lam0 * 1e-7;
+    return me_g * cL * lcm * lcm / (8.0 * M_PI * M_PI * e_esu * e_esu) * gu / gl * A;
+}
+double orc_resonance_hwhm(double lam0, double A, double gu, double gl, double N0) {
+    const double f = orc_oscillator_strength(lam0, A, gu, gl);
+    return 4.3e-28 * lam0 * f * N0 * std::sqrt(gl / gu) * lam0 * lam0;
+}
+double orc_vdw_hwhm(double lam0, double Ttr, double N, double M, double No, double Mo) {
+    double w = 6.65e-29 * N * std::sqrt(2.0 * Ttr / M);
+    if (No > 0.0) w += 2.925e-29 * No * std::sqrt(2.0 * Ttr / Mo);
+    return w * lam0 * lam0;
+}
 // Sec. 2.2.1: Voigt HWHM.
 double orc_voigt_hwhm(double lamL, double lamG) {
     const double d = (lamL - lamG) / (lamL + lamG);
@@ -202,12 +248,40 @@ double orc_whiting_phi(double dlam, double lamL, double lamV) {
 //   Sec. 2.2.1: kappa0 = j0 / B with B in population form at the line centre (Sec. 2.2).
 typedef struct { double Sj, Sk, lamG, lamL, lamV; } orc_line_state;
 
-static void line_widths(const orc_species* sp, const orc_lines* ln, const orc_cells* cells,
+// Ground-level weight of an atomic species: the summed g of its levels at E = 0.
+static double ground_weight(const orc_species* sp, int s) {
+    double g = 0.0;
+    for (int64_t k = sp->atom_off[s]; k < sp->atom_off[s + 1]; ++k)
+        if (sp->atom_E[k] == 0.0) g += sp->atom_g[k];
+    return g;
+}
+
+static void line_widths(const orc_species* sp, const orc_lines* ln, const orc_cells* cells, const double* lnpref,
                         int64_t l, int64_t c, orc_line_state* st) {
     const int s = ln->species[l];
     const double ne = cells->n[c * cells->ncol + cells->ne_col];
+    const bool atom = sp->kind[s] == 0;
     st->lamG = orc_doppler_hwhm(ln->lam0[l], cells->Ttr[c], sp->mass[s]);
-    st->lamL = orc_lorentz_hwhm(orc_stark_hwhm(ln->lamS0[l], cells->Tve[c], ne));
+    const double lamS0 = (BROAD_FLAGS & 1) && atom ? orc_stark_coeff_ionize(ln->lam0[l], ln->Eu_el[l], BROAD_EION[s])
+                                                  : ln->lamS0[l];
+    double lamL = orc_lorentz_hwhm(orc_stark_hwhm(lamS0, cells->Tve[c], ne));
+    if ((BROAD_FLAGS & 2) && atom && ln->El_el[l] == 0.0 && ln->El_v[l] == 0.0 && ln->El_j[l] == 0.0) {
+        const double g0 = ground_weight(sp, s);
+        const double N0 = g0 > 0.0 ? std::exp(lnpref[c * sp->S + s] + std::log(g0)) : 0.0;
+        lamL += orc_resonance_hwhm(ln->lam0[l], ln->A[l], ln->gu[l], ln->gl[l], N0);
+    }
+    if ((BROAD_FLAGS & 4) && atom) {
+        const int col = sp->dens_col[s];
+        const double N = cells->n[c * cells->ncol + col];
+        double No = 0.0, NoM = 0.0;
+        for (int k = 0; k < cells->ncol && k < BROAD_NCOL; ++k) {
+            if (k == col || !(BROAD_COLMASS[k] > 0.0)) continue;
+            No += cells->n[c * cells->ncol + k];
+            NoM += cells->n[c * cells->ncol + k] * BROAD_COLMASS[k];
+        }
+        lamL += orc_vdw_hwhm(ln->lam0[l], cells->Ttr[c], N, sp->mass[s], No, No > 0.0 ? NoM / No : 1.0);
+    }
+    st->lamL = lamL;
     st->lamV = orc_voigt_hwhm(st->lamL, st->lamG);
 }
 
@@ -234,7 +308,7 @@ static void line_strengths(const orc_species* sp, const orc_lines* ln, const orc
 static orc_line_state line_state(const orc_species* sp, const orc_lines* ln, const orc_cells* cells,
                                  const double* lnpref, int64_t l, int64_t c) {
     orc_line_state st;
-    line_widths(sp, ln, cells, l, c, &st);
+    line_widths(sp, ln, cells, lnpref, l, c, &st);
     line_strengths(sp, ln, cells, lnpref, l, c, &st);
     return st;
 }
@@ -320,7 +394,7 @@ void orc_coeffs_at(const orc_species* sp, const orc_lines* ln, const orc_cells* 
         double sj = 0, cj = 0, sk = 0, ck = 0, sa = 0;
         for (int64_t l = 0; l < ln->L; ++l) {
             orc_line_state st;
-            line_widths(sp, ln, cells, l, c, &st);
+            line_widths(sp, ln, cells, lnpref, l, c, &st);
             if (!orc_in_window(lk, ln->lam0[l], st.lamV)) continue;
             line_strengths(sp, ln, cells, lnpref, l, c, &st);
             const double phi = orc_whiting_phi(std::fabs(lk - ln->lam0[l]), st.lamL, st.lamV);

@@ -40,6 +40,12 @@ RAD_KIND = np.array([0, 0, 0, 0, 1, 1, 1, 1], dtype=np.int32)  # 0 atom, 1 diato
 RAD_MASS = np.array([14.0, 16.0, 14.0, 16.0, 28.0, 32.0, 30.0, 28.0])  # g/mol
 RAD_DENSITY_COL = np.array([FLOW_SPECIES.index(s) for s in RAD_SPECIES], dtype=np.int32)
 ATOM_GROUND_G = {"N": 4.0, "O": 9.0, "N+": 9.0, "O+": 4.0}  # ground-term weights
+# Ionisation energies of the radiating species, cm^-1 (N I, O I, N II, O II
+# from their ground terms; molecules 0: the full-broadening options use atoms
+# only) and molar masses of the flow columns, g/mol (electrons 0), for the
+# optional Stark-from-ionisation-gap and van der Waals widths (Sec. 2.2.1).
+RAD_E_IONIZE = np.array([117225.7, 109837.02, 238750.2, 283270.9, 0.0, 0.0, 0.0, 0.0])
+FLOW_MASS = np.array([28.0, 32.0, 30.0, 14.0, 16.0, 28.0, 32.0, 30.0, 14.0, 16.0, 0.0])
 
 # Molecular electronic states: (name, Lambda).  The first entry is the ground state.
 MOL_STATES = {
