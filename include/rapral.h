@@ -404,6 +404,31 @@ RAPRAL_API int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx,
                        int64_t* point_off, int64_t* dir_off, double* dir_scale,
                        double* dir_weight, int32_t* bundle_wall, rapral_rays* rays);
 
+/* ------------------------------------------------ optional Lorentz terms -- */
+
+#define RAPRAL_BROAD_STARK_IONIZE 1   /* atomic Stark coefficient from the ionisation gap */
+#define RAPRAL_BROAD_RESONANCE 2      /* resonance broadening of atomic ground-level lines */
+#define RAPRAL_BROAD_VDW 4            /* van der Waals broadening of atomic lines         */
+
+/* The full Lorentz width of Sec. 2.2.1 for later rapral_spectral_coeffs /
+ * rapral_batch_create calls of this context (flags 0, the default: natural +
+ * Stark with the lines' own Stark coefficients).  For atomic lines:
+ *   RAPRAL_BROAD_STARK_IONIZE: lamS0 = 1.69e3 lam0^2 / dE^2.623 (nm) with
+ *     dE = max(E_ionize - E_u, 109678.77 / 25) cm^-1, replacing lines.lamS0;
+ *   RAPRAL_BROAD_RESONANCE: lines whose lower level is at E = 0 gain
+ *     lamR = 4.3e-28 lam0 f N_0 (g_l/g_u)^0.5 lam0^2, f = m_e c (lam0 1e-7)^2
+ *     g_u A / (8 pi^2 e^2 g_l), N_0 = n_s g_0 / Z_s the ground-level density
+ *     (g_0: the summed weight of the species' levels at E = 0);
+ *   RAPRAL_BROAD_VDW: lamW = lam0^2 (6.65e-29 N (2 T_tr / M)^0.5 +
+ *     2.925e-29 N_o (2 T_tr / M_o)^0.5), N, M the species' density and molar
+ *     mass, N_o the summed density of every other density column of positive
+ *     molar mass and M_o their density-weighted mean molar mass.
+ * E_ionize [n_species] (cm^-1) and column_mass [n_cols] (g/mol, 0 for
+ * electrons) are host arrays, copied; n_species <= 32, n_cols <= 32.  The
+ * allocation-free coefficient call does not use these terms. */
+RAPRAL_API int rapral_set_broadening(rapral_ctx* ctx, int32_t flags, int32_t n_species, const double* E_ionize,
+                       int32_t n_cols, const double* column_mass);
+
 /* ----------------------------------------------- Fibonacci lines of sight -- */
 
 /* Lines of sight of the paper's own angular path (Sec. 2.2.3, Fibonacci

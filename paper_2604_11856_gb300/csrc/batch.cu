@@ -29,6 +29,7 @@ struct BatchReq {
 struct rapral_batch {
     int n = 0;
     int tile_w = 128, wpb = 4;
+    bool broad = false;           // the optional Lorentz terms were planned in
     std::vector<BatchReq> req;
     char* ws = nullptr;           // records, tile ranges, offsets of every request
     int* csr = nullptr;           // tile lists of every request
@@ -74,7 +75,8 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     if (!B) return RAPRAL_ENOMEM;
     B->n = n_items;
     B->tile_w = ctx->tile_w ? ctx->tile_w : 128;
-    B->wpb = B->tile_w == 512 ? 4 : ctx->cells_per_block;
+    B->wpb = (B->tile_w == 512 || broad_terms(&ctx->broad)) ? 4 : ctx->cells_per_block;
+    B->broad = broad_terms(&ctx->broad);
     const int W = B->tile_w;
     B->req.resize(n_items);
     // phase 1 sizes
@@ -95,8 +97,9 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         need = arena_need(need, C * sizeof(CellPrep));
         need = arena_need(need, L * sizeof(int2));
         need = arena_need(need, (T + 1) * sizeof(int));
-        need = arena_need(need, 4 * sizeof(unsigned long long));
+        need = arena_need(need, (RAPRAL_DMAX_SLOTS + 2) * sizeof(unsigned long long));
         need = arena_need(need, 4 * sizeof(int));
+        if (broad_terms(&ctx->broad)) need = broad_need(need, L, C, r.sp.n_species);
         need = arena_need(need, 0);
     }
     cudaError_t e = cudaMalloc(&B->ws, need);
@@ -109,6 +112,9 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     std::vector<LinePrep*> lps(n_items);
     std::vector<LineF32*> lfs(n_items);
     std::vector<CellPrep*> cps(n_items);
+    struct BroadTabs { double2* lb = nullptr; float2* lb32 = nullptr; double2* cb = nullptr; float2* cb32 = nullptr;
+                       double* g0 = nullptr; };
+    std::vector<BroadTabs> btabs(n_items);
     const Phys ph = make_phys(ctx->codata);
     static const int one = 1;
     int* h_tot = nullptr;
@@ -124,18 +130,26 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         pl.k0 = r.k0; pl.nk = r.nk; pl.tile_w = W; pl.n_tiles = T;
         pl.line_tiles = ar.take<int2>(L);
         pl.tile_off = ar.take<int>(T + 1);
-        unsigned long long* dmax = ar.take<unsigned long long>(4);
-        pl.wmax = dmax + 2;
+        unsigned long long* dmax = ar.take<unsigned long long>(RAPRAL_DMAX_SLOTS + 2);
+        pl.wmax = dmax + RAPRAL_DMAX_SLOTS;
         pl.sorted_flag = ar.take<int>(4);
+        const bool bt = broad_terms(&ctx->broad);
+        BroadTabs& bb = btabs[i];
+        if (bt) {
+            bb.lb = ar.take<double2>(L); bb.lb32 = ar.take<float2>(L);
+            bb.cb = ar.take<double2>((size_t)C * r.sp.n_species); bb.cb32 = ar.take<float2>((size_t)C * r.sp.n_species);
+            bb.g0 = ar.take<double>(RAPRAL_MAX_SPECIES);
+        }
         e = cudaMemcpyAsync(pl.sorted_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(pl.wmax, 0, sizeof(unsigned long long), ctx->stream);
         if (e == cudaSuccess) e = launch_validate_cells(ctx, &r.cells);
         if (e == cudaSuccess) e = launch_validate_lines(ctx, &r.ln, r.sp.n_species);
         if (e == cudaSuccess) e = launch_validate_rays(ctx, &r.rays, C);
         if (e == cudaSuccess) e = launch_line_prep(ctx, &r.sp, &r.ln, r.grid.lam_min, r.h, ph, lps[i], lfs[i],
-                                                  pl.sorted_flag);
+                                                  pl.sorted_flag, &ctx->broad, bb.lb, bb.lb32);
         if (e == cudaSuccess) e = launch_cell_prep(ctx, &r.cells, ph, cps[i], dmax);
-        if (e == cudaSuccess) e = launch_bin_bounds(ctx, &r.ln, lps[i], cps[i], dmax, r.h, &pl);
+        if (e == cudaSuccess && bt) e = launch_broad_cells(ctx, &r.sp, &r.cells, ctx->broad, bb.g0, bb.cb, bb.cb32, dmax);
+        if (e == cudaSuccess) e = launch_bin_bounds(ctx, &r.ln, lps[i], cps[i], dmax, r.h, &pl, bb.lb);
         if (e == cudaSuccess) e = launch_bin_count(ctx, &r.ln, &r.grid, r.h, &pl);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_tot + i, pl.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
@@ -158,6 +172,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         a.lp = lps[i]; a.lf = lfs[i]; a.cp = cps[i]; a.lnpref = r.cells.lnpref; a.S = r.sp.n_species; a.C = r.cells.n_cells;
         a.tile_off = plans[i].tile_off; a.tile_lines = plans[i].tile_lines;
         a.lam_min = r.grid.lam_min; a.h = r.h; a.k0 = r.k0; a.nk = r.nk; a.ld = r.ld; a.tile_w = W;
+        a.lb = btabs[i].lb; a.lb32 = btabs[i].lb32; a.cb = btabs[i].cb; a.cb32 = btabs[i].cb32;
         a.kappa = r.kappa; a.emis = r.emis; a.status = ctx->d_status; a.stats = ctx->d_stats; a.count = ctx->count_work;
         hitems[i].unit_off = units;
         hitems[i].n_groups = (r.cells.n_cells + B->wpb - 1) / B->wpb;
@@ -175,7 +190,8 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_items, hitems.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice,
                             ctx->stream);
-    if (e == cudaSuccess) e = launch_line_sum_batch(ctx, W, B->wpb, nullptr, 0, 0, nullptr, &B->blocks, false);
+    if (e == cudaSuccess)
+        e = launch_line_sum_batch(ctx, W, B->wpb, nullptr, 0, 0, nullptr, &B->blocks, false, B->broad);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (h_tot) cudaFreeHost(h_tot);
     if (e != cudaSuccess) {
@@ -200,7 +216,7 @@ int rapral_batch_run(rapral_ctx* ctx, rapral_batch* B) {
     if (ctx->ev_before && e == cudaSuccess) e = cudaEventRecord(ctx->ev_before, ctx->stream);
     if (e == cudaSuccess)
         e = launch_line_sum_batch(ctx, B->tile_w, B->wpb, B->d_items, B->n, B->total_units, B->d_counter, nullptr,
-                                  true);
+                                  true, B->broad);
     if (ctx->ev_after && e == cudaSuccess) e = cudaEventRecord(ctx->ev_after, ctx->stream);
     for (int i = 0; i < B->n && e == cudaSuccess; ++i) {
         const BatchReq& r = B->req[i];

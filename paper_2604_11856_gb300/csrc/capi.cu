@@ -196,7 +196,7 @@ int rapral_workspace_bytes(int64_t n_lines, int64_t n_cells, int64_t nk, size_t*
     b = arena_need(b, (size_t)n_lines * sizeof(int2));
     b = arena_need(b, (size_t)n_cells * sizeof(CellPrep));
     b = arena_need(b, (size_t)(tiles + 1) * sizeof(int));
-    b = arena_need(b, 64);
+    b = arena_need(b, (RAPRAL_DMAX_SLOTS + 2) * sizeof(unsigned long long) + 64);
     b = arena_need(b, (size_t)(3 * n_lines + tiles) * sizeof(int));
     *bytes = b + b / 4 + (1u << 20);
     return RAPRAL_OK;
@@ -271,8 +271,10 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     need = arena_need(need, C * sizeof(CellPrep));
     need = arena_need(need, L * sizeof(int2));
     need = arena_need(need, (T + 1) * sizeof(int));
-    need = arena_need(need, 4 * sizeof(unsigned long long));
+    need = arena_need(need, (RAPRAL_DMAX_SLOTS + 2) * sizeof(unsigned long long));
     need = arena_need(need, 4 * sizeof(int));
+    const bool bt = broad_terms(&ctx->broad);
+    if (bt) need = broad_need(need, L, C, sp->n_species);
     const size_t phase1 = need;
     need = arena_need(need, (size_t)(3 * L + T) * sizeof(int));   // first guess of the tile lists
     st = ws_reserve(ctx, need);
@@ -285,17 +287,26 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     plan.k0 = k0; plan.nk = nk; plan.tile_w = W; plan.n_tiles = T;
     plan.line_tiles = ar.take<int2>(L);
     plan.tile_off = ar.take<int>(T + 1);
-    unsigned long long* dmax = ar.take<unsigned long long>(4);
-    plan.wmax = dmax + 2;
+    unsigned long long* dmax = ar.take<unsigned long long>(RAPRAL_DMAX_SLOTS + 2);
+    plan.wmax = dmax + RAPRAL_DMAX_SLOTS;
     plan.sorted_flag = ar.take<int>(4);
+    double2* lb = nullptr; float2* lb32 = nullptr; double2* cb = nullptr; float2* cb32 = nullptr;
+    double* g0 = nullptr;
+    if (bt) {
+        lb = ar.take<double2>(L); lb32 = ar.take<float2>(L);
+        cb = ar.take<double2>((size_t)C * sp->n_species); cb32 = ar.take<float2>((size_t)C * sp->n_species);
+        g0 = ar.take<double>(RAPRAL_MAX_SPECIES);
+    }
     const int one = 1;
     e = cudaMemcpyAsync(plan.sorted_flag, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(plan.wmax, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = launch_validate_cells(ctx, cells);
     if (e == cudaSuccess) e = launch_validate_lines(ctx, ln, sp->n_species);
-    if (e == cudaSuccess) e = launch_line_prep(ctx, sp, ln, g->lam_min, h, ph, lp, lf, plan.sorted_flag);
+    if (e == cudaSuccess)
+        e = launch_line_prep(ctx, sp, ln, g->lam_min, h, ph, lp, lf, plan.sorted_flag, &ctx->broad, lb, lb32);
     if (e == cudaSuccess) e = launch_cell_prep(ctx, cells, ph, cp, dmax);
-    if (e == cudaSuccess) e = launch_bin_bounds(ctx, ln, lp, cp, dmax, h, &plan);
+    if (e == cudaSuccess && bt) e = launch_broad_cells(ctx, sp, cells, ctx->broad, g0, cb, cb32, dmax);
+    if (e == cudaSuccess) e = launch_bin_bounds(ctx, ln, lp, cp, dmax, h, &plan, lb);
     if (e == cudaSuccess) e = launch_bin_count(ctx, ln, g, h, &plan);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_pinned, plan.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
@@ -320,6 +331,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     a.tile_off = plan.tile_off; a.tile_lines = plan.tile_lines;
     a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk; a.ld = ld; a.tile_w = W;
     a.kappa = kappa; a.emis = emis; a.status = ctx->d_status; a.stats = ctx->d_stats; a.count = ctx->count_work;
+    a.lb = lb; a.lb32 = lb32; a.cb = cb; a.cb32 = cb32;
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");
 }
@@ -438,6 +450,36 @@ int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const doub
     rays->point_off = point_off; rays->seg_off = seg_off; rays->seg_cell = seg_cell; rays->seg_ds = seg_ds;
     rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
     rays->bundle_wall = bundle_wall; rays->T_wall = 0.0; rays->node_values = 0;
+    return RAPRAL_OK;
+}
+
+int rapral_set_broadening(rapral_ctx* ctx, int32_t flags, int32_t n_species, const double* E_ionize,
+                          int32_t n_cols, const double* column_mass) {
+    if (!ctx) return RAPRAL_EINVAL;
+    const int all = RAPRAL_BROAD_STARK_IONIZE | RAPRAL_BROAD_RESONANCE | RAPRAL_BROAD_VDW;
+    if (flags & ~all) return set_error(ctx, RAPRAL_EINVAL, "unknown broadening flags %d", flags);
+    if (n_species < 0 || n_species > RAPRAL_MAX_SPECIES || n_cols < 0 || n_cols > RAPRAL_MAX_COLS)
+        return set_error(ctx, RAPRAL_EINVAL, "at most %d species and %d density columns", RAPRAL_MAX_SPECIES,
+                         RAPRAL_MAX_COLS);
+    if ((flags & RAPRAL_BROAD_STARK_IONIZE) && (!E_ionize || n_species == 0))
+        return set_error(ctx, RAPRAL_EINVAL, "the Stark option needs the species' ionisation energies");
+    if ((flags & RAPRAL_BROAD_VDW) && (!column_mass || n_cols == 0))
+        return set_error(ctx, RAPRAL_EINVAL, "the van der Waals option needs the columns' molar masses");
+    BroadArgs b{};
+    b.flags = flags;
+    b.S = n_species;
+    b.ncol = n_cols;
+    for (int s = 0; s < n_species; ++s) {
+        if (E_ionize && !(E_ionize[s] >= 0.0 && std::isfinite(E_ionize[s])))
+            return set_error(ctx, RAPRAL_EINVAL, "ionisation energy of species %d", s);
+        b.Eion[s] = E_ionize ? E_ionize[s] : 0.0;
+    }
+    for (int c = 0; c < n_cols; ++c) {
+        if (column_mass && !(column_mass[c] >= 0.0 && std::isfinite(column_mass[c])))
+            return set_error(ctx, RAPRAL_EINVAL, "molar mass of column %d", c);
+        b.colmass[c] = column_mass ? column_mass[c] : 0.0;
+    }
+    ctx->broad = b;
     return RAPRAL_OK;
 }
 

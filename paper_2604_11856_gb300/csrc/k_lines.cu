@@ -40,9 +40,10 @@ __global__ void k_validate_lines(rapral_lines ln, int32_t S, int* status) {
     if (!(ln.A[l] >= 0.0) || !isfinite(ln.A[l])) fail(status, CHK_LINE_A, l);
 }
 
-__global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, double lam_min, double h, Phys ph,
-                            LinePrep* __restrict__ out, LineF32* __restrict__ out32, int* sorted_flag,
-                            const int* status) {
+__global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, const int32_t* __restrict__ kind,
+                            double lam_min, double h, Phys ph, LinePrep* __restrict__ out,
+                            LineF32* __restrict__ out32, int* sorted_flag, BroadArgs br, double2* lb,
+                            float2* lb32, const int* status) {
     if (*status) return;
     int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (l >= ln.n_lines) return;
@@ -65,6 +66,22 @@ __global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, do
     p.dEr = p.Er_u - p.Er_l;
     p.cD = RAPRAL_DOPPLER_HALF * lam0 / sqrt(mass[s]);
     p.lamS0 = ln.lamS0[l];
+    const bool atom = kind[s] == 0;
+    if ((br.flags & RAPRAL_BROAD_STARK_IONIZE) && atom) {   // Stark coefficient from the ionisation gap
+        const double dE = fmax(br.Eion[s] - ln.Eu_el[l], RAPRAL_E_IONIZE_H / 25.0);
+        p.lamS0 = 1.69e3 * lam0 * lam0 / pow(dE, 2.623);
+    }
+    if (lb) {   // per-line factors of the resonance and van der Waals widths
+        double cR = 0.0, cW = 0.0;
+        if ((br.flags & RAPRAL_BROAD_RESONANCE) && atom && ln.El_el[l] == 0.0 && ln.El_v[l] == 0.0 &&
+            ln.El_j[l] == 0.0) {
+            const double f = ph.me * ph.c * lcm * lcm / (8.0 * M_PI * M_PI * ph.e * ph.e) * ln.gu[l] / ln.gl[l] * A;
+            cR = 4.3e-28 * lam0 * f * sqrt(ln.gl[l] / ln.gu[l]) * lam0 * lam0;
+        }
+        if ((br.flags & RAPRAL_BROAD_VDW) && atom) cW = lam0 * lam0;
+        lb[l] = make_double2(cR, cW);
+        lb32[l] = make_float2((float)cR, (float)cW);
+    }
     p.tpos = (lam0 - lam_min) / h;
     p.dEve_f = (float)p.dEve;
     p.dEr_f = (float)p.dEr;
@@ -99,7 +116,7 @@ __global__ void k_line_prep(rapral_lines ln, const double* __restrict__ mass, do
 // never exceeds 1), both at their largest over the request's cells.
 __global__ void k_bin_bounds(const LinePrep* __restrict__ lp, int64_t L, const unsigned long long* __restrict__ dmax,
                              double h, int64_t k0, int64_t nk, int tile_w, int2* __restrict__ line_tiles,
-                             unsigned long long* wmax, const int* status) {
+                             unsigned long long* wmax, const double2* lb, const int* status) {
     if (*status) return;
     int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (l >= L) return;
@@ -107,7 +124,12 @@ __global__ void k_bin_bounds(const LinePrep* __restrict__ lp, int64_t L, const u
     const double stcmax = __longlong_as_double((long long)dmax[1]);
     const LinePrep p = lp[l];
     const double lamG = p.cD * sqrtTmax;
-    const double lamL = RAPRAL_LAM_NATURAL + p.lamS0 * stcmax;
+    double lamL = RAPRAL_LAM_NATURAL + p.lamS0 * stcmax;
+    if (lb) {   // resonance / van der Waals terms at their largest over the cells
+        const double2 c = lb[l];
+        lamL += c.x * __longlong_as_double((long long)dmax[2 + 2 * p.species]) +
+                c.y * __longlong_as_double((long long)dmax[3 + 2 * p.species]);
+    }
     const double w = RAPRAL_WINDOW * (lamL + lamG) * (1.0 + 1e-9) / h + 2.0;   // grid points
     atomicMax(wmax, (unsigned long long)__double_as_longlong(w));
     const double lo = fmax(ceil(p.tpos - w), (double)k0);
@@ -262,6 +284,19 @@ struct __align__(16) PairF64 {
     int klo, khi, pad0, pad1;
 };
 
+// Lorentz HWHM of line l in cell c in FP64: natural + Stark, plus the
+// optional resonance and van der Waals terms.
+__device__ __forceinline__ double lorentz64(const LineSumArgs& a, const LinePrep& L, const CellPrep& cp, int64_t l,
+                                            int64_t c) {
+    double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
+    if (a.lb) {
+        const double2 x = a.lb[l], y = a.cb[c * a.S + L.species];
+        lamL += x.x * y.x;
+        lamL += x.y * y.y;
+    }
+    return lamL;
+}
+
 template <int PPT>
 __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
     if (*a.status) return;
@@ -291,7 +326,7 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 const double x = L.dEve * cp.bve + L.dEr * cp.btr;
                 const double Sk = exp(L.lnAk + lnNu) * expm1(x);
                 const double lamG = L.cD * cp.sqrtT;
-                const double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
+                const double lamL = lorentz64(a, L, cp, l, c);
                 const double lamV = voigt_hwhm(lamL, lamG);
                 const double r = lamL / lamV;
                 const double pre = 1e3 / (2.0 * lamV * (1.065 + 0.447 * r + 0.058 * r * r));
@@ -398,10 +433,18 @@ __device__ __forceinline__ bool in_window64(int64_t k, double lam_min, double h,
 
 // Exact edges near the FP32 estimates (the estimate is within a fraction of a
 // grid point of the truth).
-__device__ __noinline__ void exact_edges(const LinePrep& L, const CellPrep& cp, double lam_min, double h, int64_t* klo,
-                            int64_t* khi) {
+__device__ __noinline__ void exact_edges(const LinePrep* __restrict__ Lp, const CellPrep* __restrict__ cpp,
+                                         const double2* lb, const double2* cbrow, double lam_min, double h,
+                                         int64_t* klo, int64_t* khi) {
+    const LinePrep& L = *Lp;
+    const CellPrep& cp = *cpp;
     const double lamG = L.cD * cp.sqrtT;
-    const double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
+    double lamL = RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc;
+    if (lb) {   // the optional resonance / van der Waals terms, as lorentz64
+        const double2 x = *lb, y = cbrow[L.species];
+        lamL += x.x * y.x;
+        lamL += x.y * y.y;
+    }
     const double w100 = RAPRAL_WINDOW * voigt_hwhm(lamL, lamG);
     int64_t k = *khi + 2;
     while (k > *khi - 3 && !in_window64(k, lam_min, h, L.lam0, w100)) --k;
@@ -476,14 +519,18 @@ struct PairF32 {
     float r, aj, ak;
 };
 
-__device__ __forceinline__ bool setup_pair_f32(const LineF32& L, const CellPrep& cp, float2 lp, int line,
-                                               const LinePrep* lp64, double lam_min, double h, float hf, float inv_hf,
-                                               int kt0, float kt0f, float kt1f, bool count, PairF32* P,
-                                               int64_t* cnt) {
+template <bool BR>
+__device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF32& L, const CellPrep& cp, float2 lp,
+                                               float2 cb, int line, int64_t c, float hf, float inv_hf, int kt0,
+                                               float kt0f, float kt1f, bool count, PairF32* P, int64_t* cnt) {
     if (!(lp.x > -INFINITY)) return false;
     // widths first: most candidates of a tile list miss the tile in a given cell
     const float lamG = L.cD * cp.sqrtT_f;
-    const float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc_f;
+    float lamL = (float)RAPRAL_LAM_NATURAL + L.lamS0 * cp.stc_f;
+    if (BR) {   // resonance / van der Waals terms: c_R N_0 + c_W W
+        const float2 x = a.lb32[line];
+        lamL = fmaf(x.y, cb.y, fmaf(x.x, cb.x, lamL));
+    }
     const float sum = lamL + lamG;
     {   // lamV <= lamL + lamG: cheap rejection before the Voigt fit
         const float wmax = (float)RAPRAL_WINDOW * sum * inv_hf * 1.0001f + 1.0f;
@@ -504,13 +551,15 @@ __device__ __forceinline__ bool setup_pair_f32(const LineF32& L, const CellPrep&
     // the Voigt fit, ex2 and the sin series; wpts and the sums to a few more
     // roundings).  Only an edge that lies inside this tile and within m of a
     // grid point is decided again in FP64.
-    const float m = 1.5e-6f * wpts + 1e-6f;
+    // (with the optional terms lamL carries two more roundings: a wider margin)
+    const float m = (BR ? 2e-6f : 1.5e-6f) * wpts + 1e-6f;
     const float span = kt1f - kt0f;
     const bool lo_in = lo_rel >= -1.0f && lo_rel <= span + 1.0f;
     const bool hi_in = hi_rel >= -1.0f && hi_rel <= span + 1.0f;
     if ((hi_in && (hi - fhi < m || fhi + 1.0f - hi < m)) || (lo_in && (clo - lo < m || lo - (clo - 1.0f) < m))) {
         int64_t klo = (int64_t)L.kc + (int64_t)clo, khi = (int64_t)L.kc + (int64_t)fhi;
-        exact_edges(lp64[line], cp, lam_min, h, &klo, &khi);
+        exact_edges(a.lp + line, a.cp + c, BR ? a.lb + line : nullptr, BR ? a.cb + c * a.S : nullptr, a.lam_min, a.h,
+                    &klo, &khi);
         lo_rel = (float)(klo - kt0);
         hi_rel = (float)(khi - kt0);
     }
@@ -629,9 +678,9 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
 // pair's window reaches the i-th run of 32 points is the same for the whole
 // warp, so runs outside the window are skipped without a masked evaluation.
 // Warps never wait for each other.
-template <int PPT>
+template <int PPT, bool BR>
 __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
-                                              float2* smlp, float4* acc, int lane, int64_t* cnt) {
+                                              float2* smlp, float2* smcb, float4* acc, int lane, int64_t* cnt) {
     constexpr int TW = 32 * PPT;
     const int kt0 = (int)(a.k0 + (int64_t)t * TW);
     const int kt1 = (int)min(a.k0 + (int64_t)(t + 1) * TW, a.k0 + a.nk) - 1;   // inclusive
@@ -654,6 +703,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     if (lane < a.S) {   // the cell's ln(N_s / Z_s) as float-float pairs
         const double v = a.lnpref[c * a.S + lane];
         smlp[lane] = v > -INFINITY ? ff_from(v) : make_float2(-INFINITY, 0.0f);
+        if (BR) smcb[lane] = a.cb32[c * a.S + lane];   // (N_0, W) of the optional terms
     }
     __syncwarp();
     const int beg = a.tile_off[t], end = a.tile_off[t + 1];
@@ -664,7 +714,8 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
         if (lane < nb) {
             const int l = a.tile_lines[b + lane];
             const LineF32 L = a.lf[l];
-            valid = setup_pair_f32(L, cp, smlp[L.species], l, a.lp, a.lam_min, a.h, hf, inv_hf, kt0, kt0f, kt1f,
+            valid = setup_pair_f32<BR>(a, L, cp, smlp[L.species], BR ? smcb[L.species] : make_float2(0.f, 0.f), l,
+                                       c, hf, inv_hf, kt0, kt0f, kt1f,
                                    count, &P, cnt);
         }
         // compact the pairs that reach the tile to the front of the staging area
@@ -713,7 +764,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
 #endif
 #define RAPRAL_LS_BLOCKS(WPB) (RAPRAL_LS_WARPS / (WPB))
 
-template <int PPT, int WPB>
+template <int PPT, int WPB, bool BR = false>
 __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f32(LineSumArgs a) {
     if (*a.status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -722,9 +773,10 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
     __shared__ float4 sm0[WPB][32];   // klo, khi, kc (int bits), s
     __shared__ float4 sm1[WPB][32];   // u0, r, aj, ak
     __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
+    __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float4 acc[WPB][32 * PPT];
     int64_t cnt[4] = {0, 0, 0, 0};
-    warp_tile_f32<PPT>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], acc[warp], lane, cnt);
+    warp_tile_f32<PPT, BR>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
     if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
@@ -732,7 +784,7 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
 // units (request, tile, group of WPB cells) from one atomic counter until the
 // list is exhausted; units of a request are ordered tile by tile so blocks
 // working at the same time share a tile's line list in L2.
-template <int PPT, int WPB>
+template <int PPT, int WPB, bool BR = false>
 __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_batch(const BatchItem* __restrict__ items,
                                                                        int n_items, int64_t total,
                                                                        unsigned long long* counter,
@@ -742,6 +794,7 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_ba
     __shared__ float4 sm0[WPB][32];
     __shared__ float4 sm1[WPB][32];
     __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
+    __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float4 acc[WPB][32 * PPT];
     __shared__ long long unit_s;
     int64_t cnt[4] = {0, 0, 0, 0};
@@ -760,7 +813,8 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_ba
         const int64_t local = u - it.unit_off;
         const int t = (int)(local / it.n_groups);
         const int64_t c = (local - (int64_t)t * it.n_groups) * WPB + warp;
-        if (c < it.a.C) warp_tile_f32<PPT>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], acc[warp], lane, cnt);
+        if (c < it.a.C)
+            warp_tile_f32<PPT, BR>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
         __syncwarp();
     }
     if (items[0].a.count) block_count(stats, cnt[0], cnt[1], cnt[2], cnt[3]);
@@ -776,20 +830,22 @@ cudaError_t launch_validate_lines(rapral_ctx* ctx, const rapral_lines* ln, int32
 
 cudaError_t launch_line_prep(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
                              double lam_min, double h, const Phys& ph, LinePrep* out, LineF32* out32,
-                             int* sorted_flag) {
+                             int* sorted_flag, const BroadArgs* br, double2* lb, float2* lb32) {
     if (ln->n_lines == 0) return cudaSuccess;
-    k_line_prep<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(*ln, sp->mass, lam_min, h, ph, out, out32,
-                                                                   sorted_flag, ctx->d_status);
+    BroadArgs b = br ? *br : BroadArgs{};
+    if (!broad_terms(br)) lb = nullptr, lb32 = nullptr;
+    k_line_prep<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(*ln, sp->mass, sp->kind, lam_min, h, ph, out,
+                                                                   out32, sorted_flag, b, lb, lb32, ctx->d_status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_bounds(rapral_ctx* ctx, const rapral_lines* ln, const LinePrep* lp, const CellPrep* cp,
-                              const unsigned long long* d_max, double h, BinPlan* plan) {
+                              const unsigned long long* d_max, double h, BinPlan* plan, const double2* lb) {
     (void)cp;
     if (ln->n_lines == 0) return cudaSuccess;
     k_bin_bounds<<<div_up(ln->n_lines, 256), 256, 0, ctx->stream>>>(lp, ln->n_lines, d_max, h, plan->k0, plan->nk,
                                                                     plan->tile_w, plan->line_tiles, plan->wmax,
-                                                                    ctx->d_status);
+                                                                    lb, ctx->d_status);
     return cudaGetLastError();
 }
 
@@ -846,7 +902,18 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
         }
         return cudaGetLastError();
     }
-    // FP32: warp-level kernel, WPB cells per block
+    // FP32: warp-level kernel, WPB cells per block; with the optional
+    // resonance / van der Waals terms four cells a block
+    if (a.lb32) {
+        dim3 gb(div_up(a.C, 4), grid.y);
+        switch (a.tile_w) {
+            case 128: k_line_sum_f32<4, 4, true><<<gb, 128, 0, ctx->stream>>>(a); break;
+            case 256: k_line_sum_f32<8, 4, true><<<gb, 128, 0, ctx->stream>>>(a); break;
+            case 512: k_line_sum_f32<16, 4, true><<<gb, 128, 0, ctx->stream>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int wpb = a.tile_w == 512 ? 4 : ctx->cells_per_block;
     dim3 g32(div_up(a.C, wpb), grid.y);
 #define RAPRAL_LS32(PPT, WPB) k_line_sum_f32<PPT, WPB><<<g32, 32 * WPB, 0, ctx->stream>>>(a)
@@ -862,24 +929,32 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
     return cudaGetLastError();
 }
 
-template <int PPT, int WPB>
+template <int PPT, int WPB, bool BR = false>
 static cudaError_t batch_launch(rapral_ctx* ctx, const BatchItem* items, int n, int64_t total,
                                 unsigned long long* counter, int* blocks_out, bool launch) {
     int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_batch<PPT, WPB>, 32 * WPB, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_batch<PPT, WPB, BR>, 32 * WPB, 0);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int blocks = max(1, per_sm) * sms;
     if (blocks_out) *blocks_out = blocks;
     if (!launch) return cudaSuccess;
-    k_line_sum_batch<PPT, WPB><<<blocks, 32 * WPB, 0, ctx->stream>>>(items, n, total, counter, ctx->d_stats,
-                                                                     ctx->d_status);
+    k_line_sum_batch<PPT, WPB, BR><<<blocks, 32 * WPB, 0, ctx->stream>>>(items, n, total, counter, ctx->d_stats,
+                                                                         ctx->d_status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const BatchItem* items, int n, int64_t total,
-                                  unsigned long long* counter, int* blocks_out, bool launch) {
+                                  unsigned long long* counter, int* blocks_out, bool launch, bool broad) {
+    if (broad) {   // the optional Lorentz terms: four cells a block (the plan's group size)
+        if (wpb != 4) return cudaErrorInvalidValue;
+        if (tile_w == 128) return batch_launch<4, 4, true>(ctx, items, n, total, counter, blocks_out, launch);
+        if (tile_w == 256) return batch_launch<8, 4, true>(ctx, items, n, total, counter, blocks_out, launch);
+        if (tile_w == 512) return batch_launch<16, 4, true>(ctx, items, n, total, counter, blocks_out, launch);
+        return cudaErrorInvalidValue;
+    }
     if (tile_w == 128 && wpb == 2) return batch_launch<4, 2>(ctx, items, n, total, counter, blocks_out, launch);
     if (tile_w == 128 && wpb == 4) return batch_launch<4, 4>(ctx, items, n, total, counter, blocks_out, launch);
     if (tile_w == 128 && wpb == 8) return batch_launch<4, 8>(ctx, items, n, total, counter, blocks_out, launch);

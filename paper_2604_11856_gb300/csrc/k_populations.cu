@@ -89,7 +89,68 @@ __global__ void k_cell_prep(const double* __restrict__ Ttr, const double* __rest
     atomicMax(&dmax[1], (unsigned long long)__double_as_longlong(p.stc));
 }
 
+// Ground-level weight of each atomic species: the summed g of its levels at
+// E = 0 (0 for molecules).
+__global__ void k_ground_weights(rapral_species sp, double* g0) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= sp.n_species) return;
+    double g = 0.0;
+    if (sp.kind[s] == RAPRAL_ATOM)
+        for (int64_t k = sp.atom_off[s]; k < sp.atom_off[s + 1]; ++k)
+            if (sp.atom_E[k] == 0.0) g += sp.atom_g[k];
+    g0[s] = g;
+}
+
+// Per (cell, atomic species): ground-level density N_0 = n_s g_0 / Z_s and
+// the van der Waals factor W = 6.65e-29 N (2T/M)^0.5 + 2.925e-29 N_o (2T/M_o)^0.5
+// (the other heavy particles in column order); zeros for molecules or for
+// terms that are off.  Largest values over the cells per species in dmax.
+__global__ void k_cell_broad(rapral_species sp, rapral_cells cells, BroadArgs br, const double* __restrict__ g0,
+                             double2* __restrict__ cb, float2* __restrict__ cb32, unsigned long long* dmax,
+                             const int* status) {
+    if (*status) return;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= cells.n_cells) return;
+    const int S = sp.n_species, nc = cells.n_cols;
+    const double T = cells.Ttr[c];
+    const double* n = cells.n + c * nc;
+    for (int s = 0; s < S; ++s) {
+        double N0 = 0.0, W = 0.0;
+        if (sp.kind[s] == RAPRAL_ATOM) {
+            if ((br.flags & RAPRAL_BROAD_RESONANCE) && g0[s] > 0.0)
+                N0 = exp(cells.lnpref[c * S + s] + log(g0[s]));
+            if (br.flags & RAPRAL_BROAD_VDW) {
+                const int col = sp.density_col[s];
+                double No = 0.0, NoM = 0.0;
+                for (int k = 0; k < nc && k < br.ncol; ++k) {
+                    if (k == col || !(br.colmass[k] > 0.0)) continue;
+                    No += n[k];
+                    NoM += n[k] * br.colmass[k];
+                }
+                W = 6.65e-29 * n[col] * sqrt(2.0 * T / sp.mass[s]);
+                if (No > 0.0) W += 2.925e-29 * No * sqrt(2.0 * T / (NoM / No));
+            }
+        }
+        cb[c * S + s] = make_double2(N0, W);
+        cb32[c * S + s] = make_float2((float)N0, (float)W);
+        atomicMax(&dmax[2 + 2 * s], (unsigned long long)__double_as_longlong(N0));
+        atomicMax(&dmax[3 + 2 * s], (unsigned long long)__double_as_longlong(W));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_broad_cells(rapral_ctx* ctx, const rapral_species* sp, const rapral_cells* cells,
+                               const BroadArgs& br, double* g0, double2* cb, float2* cb32, unsigned long long* d_max) {
+    const int S = sp->n_species;
+    cudaError_t e = cudaMemsetAsync(d_max + 2, 0, 2 * (size_t)S * sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return e;
+    k_ground_weights<<<1, 32, 0, ctx->stream>>>(*sp, g0);
+    if (cells->n_cells == 0) return cudaGetLastError();
+    k_cell_broad<<<div_up(cells->n_cells, 128), 128, 0, ctx->stream>>>(*sp, *cells, br, g0, cb, cb32, d_max,
+                                                                       ctx->d_status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_validate_cells(rapral_ctx* ctx, const rapral_cells* cells) {
     k_validate_cells<<<div_up(cells->n_cells, 256), 256, 0, ctx->stream>>>(

@@ -40,41 +40,11 @@ __device__ __forceinline__ float ex2f_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ void seg_coeffs(float kap, float s, float inv_k, float inv_s, float* e, float* ca,
-                                           float* cb) {
-    const float dtau = kap * s;
-    *e = ex2f_approx(-1.44269504f * dtau);
-    if (fabsf(dtau) < (float)RAPRAL_THIN_F32) {
-        const float t = dtau;
-        // a/s = 1/2 - t/3 + t^2/8 - t^3/30 + t^4/144 - t^5/840 + t^6/5760
-        float pa = fmaf(t, 1.0f / 5760.0f, -1.0f / 840.0f);
-        pa = fmaf(t, pa, 1.0f / 144.0f);
-        pa = fmaf(t, pa, -1.0f / 30.0f);
-        pa = fmaf(t, pa, 0.125f);
-        pa = fmaf(t, pa, -1.0f / 3.0f);
-        pa = fmaf(t, pa, 0.5f);
-        // b/s = 1/2 - t/6 + t^2/24 - t^3/120 + t^4/720 - t^5/5040 + t^6/40320
-        float pb = fmaf(t, 1.0f / 40320.0f, -1.0f / 5040.0f);
-        pb = fmaf(t, pb, 1.0f / 720.0f);
-        pb = fmaf(t, pb, -1.0f / 120.0f);
-        pb = fmaf(t, pb, 1.0f / 24.0f);
-        pb = fmaf(t, pb, -1.0f / 6.0f);
-        pb = fmaf(t, pb, 0.5f);
-        *ca = s * pa;
-        *cb = s * pb;
-    } else {
-        const float f = (1.0f - *e) * (inv_k * inv_s);   // (1 - e) / dtau
-        *ca = (f - *e) * inv_k;
-        *cb = (1.0f - f) * inv_k;
-    }
-}
-
 __device__ __forceinline__ float recip(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // The same coefficients for one direction per segment: the closed form takes
 // a single reciprocal, of dtau, inside its branch (1/kappa = s / dtau).

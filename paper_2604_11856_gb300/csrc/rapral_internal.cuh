@@ -17,15 +17,30 @@
 struct Phys {
     double kB, c, h;
     double c2;        // h c / k, cm K
+    double me, e;     // electron mass (g) and charge (esu), for oscillator strengths
 };
 
 inline Phys make_phys(int codata) {
     Phys p;
-    if (codata) { p.kB = 1.380649e-16; p.c = 2.99792458e10; p.h = 6.62607015e-27; }
-    else        { p.kB = 1.380e-16;    p.c = 2.998e10;      p.h = 6.626e-27; }
+    if (codata) {
+        p.kB = 1.380649e-16; p.c = 2.99792458e10; p.h = 6.62607015e-27; p.me = 9.1093837e-28; p.e = 4.80320471e-10;
+    } else {
+        p.kB = 1.380e-16; p.c = 2.998e10; p.h = 6.626e-27; p.me = 9.109e-28; p.e = 4.803e-10;
+    }
     p.c2 = p.h * p.c / p.kB;
     return p;
 }
+
+// Optional Lorentz terms of Sec. 2.2.1 (rapral_set_broadening): flags
+// RAPRAL_BROAD_*, per-species ionisation energies and per-column molar masses.
+#define RAPRAL_MAX_COLS 32
+#define RAPRAL_E_IONIZE_H 109678.77      // hydrogen ionisation energy, cm^-1
+struct BroadArgs {
+    int flags;
+    int S, ncol;
+    double Eion[RAPRAL_MAX_SPECIES];
+    double colmass[RAPRAL_MAX_COLS];
+};
 
 // Sec. 2.2.1 constants.
 #define RAPRAL_LAM_NATURAL 5.9e-6        // natural HWHM, nm
@@ -132,6 +147,7 @@ struct rapral_ctx {
     unsigned long long* d_stats = nullptr;   // [4] line-sum work counters
     int count_work = 1;                      // counters on (rapral_set_counters)
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing events
+    BroadArgs broad = {};                    // optional Lorentz terms (flags 0: off)
     char err[512] = {0};
 };
 
@@ -173,11 +189,23 @@ cudaError_t launch_validate_cells(rapral_ctx* ctx, const rapral_cells* cells);
 cudaError_t launch_populations(rapral_ctx* ctx, const rapral_species* sp, const rapral_cells* cells,
                                double* lnpref, const Phys& ph);
 cudaError_t launch_validate_lines(rapral_ctx* ctx, const rapral_lines* ln, int32_t n_species);
+// br: optional Lorentz terms (nullptr or flags 0: none); with resonance or van
+// der Waals terms, lb / lb32 [L] receive per-line (c_R, c_W), the width
+// gaining c_R N_0 + c_W W over the (cell, species) values of launch_broad_cells.
 cudaError_t launch_line_prep(rapral_ctx* ctx, const rapral_species* sp, const rapral_lines* ln,
                              double lam_min, double h, const Phys& ph, LinePrep* out, LineF32* out32,
-                             int* sorted_flag);
+                             int* sorted_flag, const BroadArgs* br = nullptr, double2* lb = nullptr,
+                             float2* lb32 = nullptr);
 cudaError_t launch_cell_prep(rapral_ctx* ctx, const rapral_cells* cells, const Phys& ph, CellPrep* out,
-                             unsigned long long* d_max /*[2]*/);
+                             unsigned long long* d_max /*[2 + 2 S]*/);
+// Per (cell, species): ground-level density N_0 and van der Waals factor W
+// (cb / cb32 [C][S]); their largest values over the cells go to
+// d_max[2 + 2 s], d_max[3 + 2 s].  Needs the cells' lnpref.  g0: scratch [S].
+cudaError_t launch_broad_cells(rapral_ctx* ctx, const rapral_species* sp, const rapral_cells* cells,
+                               const BroadArgs& br, double* g0, double2* cb, float2* cb32,
+                               unsigned long long* d_max);
+// Whether the resonance or van der Waals terms are on.
+inline bool broad_terms(const BroadArgs* br) { return br && (br->flags & (RAPRAL_BROAD_RESONANCE | RAPRAL_BROAD_VDW)); }
 
 // Binning of lines into spectral tiles of the range [k0, k0 + nk).
 struct BinPlan {
@@ -191,7 +219,8 @@ struct BinPlan {
     unsigned long long* wmax;    // [1] largest window half-width, grid points (double bits)
 };
 cudaError_t launch_bin_bounds(rapral_ctx* ctx, const rapral_lines* ln, const LinePrep* lp, const CellPrep* cp,
-                              const unsigned long long* d_max, double h, BinPlan* plan);
+                              const unsigned long long* d_max, double h, BinPlan* plan,
+                              const double2* lb = nullptr);
 cudaError_t launch_bin_count(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
                              BinPlan* plan);
 cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
@@ -214,7 +243,25 @@ struct LineSumArgs {
     const int* status;
     unsigned long long* stats;   // [4] evaluations, gauss, correction, pairs
     int count;                   // accumulate the work counters (costs conversions per pair)
+    // optional resonance / van der Waals terms (null: none): per line (c_R, c_W),
+    // per (cell, species) (N_0, W)
+    const double2* lb = nullptr;
+    const float2* lb32 = nullptr;
+    const double2* cb = nullptr;
+    const float2* cb32 = nullptr;
 };
+
+// Workspace of the optional resonance / van der Waals terms of one request:
+// per-line factors, per-(cell, species) values, ground weights, and the
+// maxima (after sqrt(T_tr) and the Stark factor) for the binning bound.
+#define RAPRAL_DMAX_SLOTS (2 + 2 * RAPRAL_MAX_SPECIES)
+inline size_t broad_need(size_t need, int64_t L, int64_t C, int S) {
+    need = arena_need(need, (size_t)L * sizeof(double2));
+    need = arena_need(need, (size_t)L * sizeof(float2));
+    need = arena_need(need, (size_t)C * S * sizeof(double2));
+    need = arena_need(need, (size_t)C * S * sizeof(float2));
+    return arena_need(need, RAPRAL_MAX_SPECIES * sizeof(double));
+}
 cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision, int64_t n_tiles);
 
 // One request of a batched (persistent) line sum: its arguments and the
@@ -227,7 +274,7 @@ struct BatchItem {
 // Launches the persistent FP32 line sum over all units (or only reports the
 // grid size when `launch` is false).
 cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const BatchItem* items, int n, int64_t total,
-                                  unsigned long long* counter, int* blocks_out, bool launch);
+                                  unsigned long long* counter, int* blocks_out, bool launch, bool broad);
 
 // Rays
 cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells);

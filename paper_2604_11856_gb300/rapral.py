@@ -26,6 +26,9 @@ _lib = None
 _lock = threading.Lock()
 
 
+BROAD_STARK_IONIZE, BROAD_RESONANCE, BROAD_VDW = 1, 2, 4   # rapral_set_broadening flags
+
+
 class RapralError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
@@ -125,6 +128,7 @@ def load(build_if_missing=True):
                                           vp, vp, vp, vp, P(Rays)]),
             "rapral_los_node_states": (i, [vp, vp, i32, vp, i32, P(Cells), i64, vp, vp, vp, vp, vp]),
             "rapral_fibonacci_flux": (i, [vp, i64, vp, vp, i32, vp, i32, i32, vp]),
+            "rapral_set_broadening": (i, [vp, i32, i32, vp, i32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -156,6 +160,16 @@ class Context:
     def check(self, rc):
         if rc != OK:
             raise RapralError(rc, self.lib.rapral_last_error(self.h).decode())
+
+    def set_broadening(self, flags, E_ionize=None, column_mass=None):
+        """Optional Lorentz terms (BROAD_* flags) for later coefficient calls:
+        E_ionize per radiating species (cm^-1), column_mass per density column
+        (g/mol, 0 for electrons)."""
+        E = np.ascontiguousarray(E_ionize if E_ionize is not None else np.zeros(0), np.float64)
+        M = np.ascontiguousarray(column_mass if column_mass is not None else np.zeros(0), np.float64)
+        self.check(self.lib.rapral_set_broadening(self.h, int(flags), E.shape[0],
+                                                  E.ctypes.data_as(ct.c_void_p) if E.size else None, M.shape[0],
+                                                  M.ctypes.data_as(ct.c_void_p) if M.size else None))
 
     def set_stream(self, stream):
         self.stream = stream
