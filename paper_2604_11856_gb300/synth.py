@@ -641,3 +641,33 @@ def served_requests(seed=1004, n_requests=2000, rate=100.0, pool=None, scale=1.0
         reqs.append(dict(t=float(t[i]), slab=slab, problem=Problem(
             f"req_{i}", species, lines_all, cells, Grid(50.0, 2000.0, K), geo, meta=dict(index=i))))
     return reqs
+
+
+def cr_model(seed=1005, species="N", n_levels=20, n_lumped=0, radiative_fraction=0.5):
+    """Synthetic collisional-radiative level model of an atomic radiator
+    (Sec. 2.1 QSS populations; the paper's rate databases are not available):
+    a ground level with the species' ground-term weight and n_levels - 1
+    excited levels uniform in 15-95 % of the ionisation energy (plus
+    n_lumped levels above them that only enter the closure), weights 2-20;
+    every level pair is a transition with upward Arrhenius rates
+    C T^n e^{-theta/T}: heavy-particle impact C log-uniform 1e10-1e13
+    cm^3/mol/s, electron impact 1e13-1e16, n uniform 0-0.5; a fraction of
+    the pairs radiate with A log-uniform 1e4-1e8 s^-1 at lam = 1e7 / dE nm;
+    electron-impact ionisation of each level C log-uniform 1e12-1e14, n = 0.5."""
+    rng = np.random.default_rng(seed)
+    s = RAD_SPECIES.index(species)
+    E_ion = float(RAD_E_IONIZE[s])
+    n_all = n_levels + n_lumped
+    E = np.concatenate([[0.0], np.sort(rng.uniform(0.15, 0.95, n_all - 1)) * E_ion])
+    g = np.concatenate([[ATOM_GROUND_G[species]], rng.integers(2, 21, n_all - 1).astype(np.float64)])
+    lo, up = np.triu_indices(n_levels, k=1)
+    T = lo.shape[0]
+    lu = lambda a, b, n: 10.0 ** rng.uniform(np.log10(a), np.log10(b), n)
+    A = np.where(rng.uniform(size=T) < radiative_fraction, lu(1e4, 1e8, T), 0.0)
+    ion = {"N": "N+", "O": "O+"}.get(species)
+    return dict(l=n_levels, E=E, g=g, lo=lo.astype(np.int32), up=up.astype(np.int32),
+                hp_C=lu(1e10, 1e13, T), hp_n=rng.uniform(0.0, 0.5, T), e_C=lu(1e13, 1e16, T),
+                e_n=rng.uniform(0.0, 0.5, T), A=A, lam=1e7 / (E[up] - E[lo]),
+                ii_C=lu(1e12, 1e14, n_levels), ii_n=np.full(n_levels, 0.5), E_ion=E_ion,
+                g_ion=float(ATOM_GROUND_G[ion]) if ion else 1.0, col=int(RAD_DENSITY_COL[s]),
+                ion_col=FLOW_SPECIES.index(ion) if ion else -1)
