@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--serve-fp64-requests", type=int, default=4)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
-    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci"], default="stagnation",
-                    help="stagnation line (the bench line); afterbody / batch / fibonacci: one-off measurements")
+    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci", "qss"], default="stagnation",
+                    help="stagnation line (the bench line); afterbody / batch / fibonacci / qss: one-off measurements")
     ap.add_argument("--fib-points", type=int, default=8, help="fibonacci workload: surface points")
     ap.add_argument("--fib-los", type=int, default=128, help="fibonacci workload: Fibonacci directions per point")
     ap.add_argument("--ab-small", action="store_true",
@@ -324,6 +324,44 @@ def run_batch(args):
     return 0
 
 
+def run_qss(args):
+    """QSS collisional-radiative populations of atomic N and O (32 solved +
+    4 lumped levels each, 496 transitions) in every cell of the 400 x 200
+    afterbody: one FP64 LU-solved system per (cell, atom)."""
+    import torch
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import synth
+    p = synth.afterbody(n_points=2, n_grid=11)
+    ctx = R.Context(0)
+    models = [R.DeviceCrModel(synth.cr_model(species=s, n_levels=32, n_lumped=4, seed=1005 + i), ctx.device)
+              for i, s in enumerate(("N", "O"))]
+    dc = R.DeviceCells(p.cells, 8, ctx.device)
+    C = len(p.cells.Ttr)
+    outs = [torch.empty((C, m.l), dtype=torch.float64, device=ctx.device) for m in models]
+    run = lambda: [R.qss_populations(ctx, m, dc, o) for m, o in zip(models, outs)]
+    for _ in range(max(1, args.warmup)):
+        run()
+    ctx.sync()
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(max(1, args.steps)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            run()
+            b.record(ctx.stream)
+            ctx.sync()
+            ms.append(a.elapsed_time(b))
+    t = float(np.mean(ms)) * 1e-3
+    systems = C * len(models)
+    l = models[0].l
+    # LU of an l x l system: 2 l^3 / 3 flops (the rate assembly, 2 pow + 2 exp a transition, not counted)
+    print(json.dumps({"workload": f"QSS populations, {C} afterbody cells x 2 atoms (N, O), {l} levels + 4 lumped, "
+                                  f"{l * (l - 1) // 2} transitions, FP64", "warmup": args.warmup,
+                      "steps": max(1, args.steps), "ms_per_solve": t * 1e3, "systems_per_s": systems / t,
+                      "lu_gflops": systems * 2.0 * l ** 3 / 3.0 / t / 1e9, "clocks": clk.summary()}))
+    return 0
+
+
 def run_fibonacci(args):
     """The paper's own angular path on the afterbody at 100 x 50 cells (2e5
     points in 65,536-point chunks): Fibonacci lines of sight from
@@ -390,6 +428,8 @@ def main():
         return run_batch(args)
     if args.workload == "fibonacci":
         return run_fibonacci(args)
+    if args.workload == "qss":
+        return run_qss(args)
     import torch
     import torch.distributed as dist
 

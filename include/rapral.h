@@ -429,6 +429,50 @@ RAPRAL_API int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx,
 RAPRAL_API int rapral_set_broadening(rapral_ctx* ctx, int32_t flags, int32_t n_species, const double* E_ionize,
                        int32_t n_cols, const double* column_mass);
 
+/* ------------------------------------- QSS collisional-radiative populations -- */
+
+/* Level model of one atomic radiator for the quasi-steady-state populations
+ * of Sec. 2.1 (all arrays device, caller-owned).  Levels 0 .. n_levels-1 are
+ * solved (0: ground); levels n_levels .. n_levels_all-1 only enter the
+ * closure, in Boltzmann equilibrium with level n_levels-1 at T_ve.
+ * Transition t joins levels lo[t] < up[t] < n_levels with upward Arrhenius
+ * rates C T^n e^{-theta/T} (cm^3/mol/s; theta the level gap in K) for heavy-
+ * particle impact (hp_C, hp_n; at T_tr) and electron impact (e_C, e_n; at
+ * T_ve), downward rates by detailed balance k_down = k_up Q_lo / Q_up with
+ * Q_i = g_i e^{-hc E_i / k T}, and spontaneous emission A (s^-1) at lam (nm),
+ * which escapes (factor 1) at lam >= 200 nm and is trapped (0) below.  Level
+ * i is ionised by electrons at ii_C[i] T_ve^{ii_n[i]} e^{-hc (E_ionize - E_i)/kT_ve}
+ * and refilled by three-body recombination k_up Q_i / (Q_+ Q_e),
+ * Q_+ = g_ion e^{-hc E_ionize / k T_ve}, Q_e = 2 (2 pi m_e k T_ve / h^2)^1.5. */
+typedef struct {
+    int32_t n_levels;            /* l, 2 .. 32                                 */
+    int32_t n_levels_all;        /* l* >= l                                    */
+    const double* E;             /* [l*] cm^-1                                 */
+    const double* g;             /* [l*]                                       */
+    int32_t n_trans;             /* <= 496                                     */
+    const int32_t* lo;           /* [n_trans]                                  */
+    const int32_t* up;           /* [n_trans]                                  */
+    const double *hp_C, *hp_n;   /* [n_trans]                                  */
+    const double *e_C, *e_n;     /* [n_trans]                                  */
+    const double* A;             /* [n_trans] s^-1                             */
+    const double* lam;           /* [n_trans] nm                               */
+    const double *ii_C, *ii_n;   /* [l] (entry 0 unused)                       */
+    double E_ionize;             /* cm^-1                                      */
+    double g_ion;                /* ground weight of the ion                  */
+    int32_t col;                 /* density column of the atom                */
+    int32_t ion_col;             /* density column of its ion, -1: none       */
+} rapral_cr_model;
+
+/* Quasi-steady-state level populations (Sec. 2.1): per cell, 0 = gains -
+ * losses for levels 1 .. l-1 (heavy-particle and electron impact excitation
+ * and de-excitation, radiative decay, ionisation and recombination; N_M the
+ * summed density of every column but the electrons') and the closure
+ * sum_i N_i (with the lumped levels) = the atom's density, solved by LU with
+ * partial pivoting.  Writes n_out [C][l] (device, cm^-3).  Transition
+ * indices out of range or a singular system: RAPRAL_EINVAL at the next sync. */
+RAPRAL_API int rapral_qss_populations(rapral_ctx* ctx, const rapral_cr_model* model, const rapral_cells* cells,
+                       double* n_out);
+
 /* ----------------------------------------------- Fibonacci lines of sight -- */
 
 /* Lines of sight of the paper's own angular path (Sec. 2.2.3, Fibonacci

@@ -50,6 +50,8 @@ static const char* check_name(int c) {
         case CHK_DIR: return "direction scale not positive";
         case CHK_TIMEOUT: return "bounded device wait expired";
         case CHK_LOS_INDEX: return "line-of-sight index out of range";
+        case CHK_CR_TRANS: return "level-model transition indices out of range";
+        case CHK_CR_SINGULAR: return "singular QSS rate matrix";
         default: return "device check";
     }
 }
@@ -451,6 +453,27 @@ int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx, const doub
     rays->dir_off = dir_off; rays->dir_scale = dir_scale; rays->dir_weight = dir_weight;
     rays->bundle_wall = bundle_wall; rays->T_wall = 0.0; rays->node_values = 0;
     return RAPRAL_OK;
+}
+
+int rapral_qss_populations(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, double* n_out) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!m || !cells || !n_out) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (m->n_levels < 2 || m->n_levels > 32 || m->n_levels_all < m->n_levels || m->n_trans < 0 ||
+        m->n_trans > 32 * 31 / 2)
+        return set_error(ctx, RAPRAL_EINVAL,
+                         "level model needs 2 <= n_levels <= 32, n_levels_all >= n_levels, n_trans <= 496");
+    if (!m->E || !m->g || !m->ii_C || !m->ii_n ||
+        (m->n_trans > 0 && (!m->lo || !m->up || !m->hp_C || !m->hp_n || !m->e_C || !m->e_n || !m->A || !m->lam)))
+        return set_error(ctx, RAPRAL_EINVAL, "null level-model array");
+    if (cells->n_cells < 0 || cells->n_cols < 1 || cells->ne_col < 0 || cells->ne_col >= cells->n_cols ||
+        m->col < 0 || m->col >= cells->n_cols || m->ion_col >= cells->n_cols)
+        return set_error(ctx, RAPRAL_EINVAL, "density columns");
+    if (!(m->E_ionize > 0.0) || !(m->g_ion > 0.0)) return set_error(ctx, RAPRAL_EINVAL, "ionisation energy or ion weight");
+    if (cells->n_cells == 0) return RAPRAL_OK;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_validate_cells(ctx, cells);
+    if (e == cudaSuccess) e = launch_qss(ctx, m, cells, n_out, make_phys(ctx->codata));
+    return cuda_status(ctx, e, "QSS populations");
 }
 
 int rapral_set_broadening(rapral_ctx* ctx, int32_t flags, int32_t n_species, const double* E_ionize,

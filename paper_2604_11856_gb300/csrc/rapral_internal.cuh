@@ -54,7 +54,7 @@ struct BroadArgs {
 enum { ST_CODE = 0, ST_CHECK = 1, ST_INDEX = 2 };
 enum {
     CHK_NONE = 0, CHK_CELL_T, CHK_CELL_N, CHK_LINE_SPECIES, CHK_LINE_LAM, CHK_LINE_G,
-    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT, CHK_LOS_INDEX
+    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT, CHK_LOS_INDEX, CHK_CR_TRANS, CHK_CR_SINGULAR
 };
 
 // ------------------------------------------------------------- records ----
@@ -307,6 +307,10 @@ cudaError_t launch_axisym_fill(rapral_ctx* ctx, const double* xf, int32_t nx, co
 // Exclusive scan of int64 counts in place over [0, n] (n + 1 entries; the
 // last entry receives the total); single block.
 cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n);
+
+// QSS collisional-radiative populations (k_qss.cu).
+cudaError_t launch_qss(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, double* n_out,
+                       const Phys& ph);
 
 // Fibonacci lines of sight, node states and the angular flux (k_los.cu).
 cudaError_t launch_fib_count(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,

@@ -74,6 +74,14 @@ class Rays(ct.Structure):
                 ("node_values", ct.c_int32)]
 
 
+class CrModel(ct.Structure):
+    _fields_ = [("n_levels", ct.c_int32), ("n_levels_all", ct.c_int32), ("E", ct.c_void_p), ("g", ct.c_void_p),
+                ("n_trans", ct.c_int32), ("lo", ct.c_void_p), ("up", ct.c_void_p), ("hp_C", ct.c_void_p),
+                ("hp_n", ct.c_void_p), ("e_C", ct.c_void_p), ("e_n", ct.c_void_p), ("A", ct.c_void_p),
+                ("lam", ct.c_void_p), ("ii_C", ct.c_void_p), ("ii_n", ct.c_void_p), ("E_ionize", ct.c_double),
+                ("g_ion", ct.c_double), ("col", ct.c_int32), ("ion_col", ct.c_int32)]
+
+
 class BatchItem(ct.Structure):
     _fields_ = [("species", ct.c_void_p), ("lines", ct.c_void_p), ("cells", ct.c_void_p), ("grid", ct.c_void_p),
                 ("rays", ct.c_void_p), ("k0", ct.c_int64), ("nk", ct.c_int64), ("kappa", ct.c_void_p),
@@ -129,6 +137,7 @@ def load(build_if_missing=True):
             "rapral_los_node_states": (i, [vp, vp, i32, vp, i32, P(Cells), i64, vp, vp, vp, vp, vp]),
             "rapral_fibonacci_flux": (i, [vp, i64, vp, vp, i32, vp, i32, i32, vp]),
             "rapral_set_broadening": (i, [vp, i32, i32, vp, i32, vp]),
+            "rapral_qss_populations": (i, [vp, P(CrModel), P(Cells), vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -413,6 +422,34 @@ def slab_rays(ctx, geo, device):
                                        _ptr(t["dir_scale"]), _ptr(t["dir_weight"]), _ptr(t["bundle_wall"]),
                                        ct.byref(r.struct)))
     return r
+
+
+class DeviceCrModel:
+    """A level model (a dict of host arrays as made by synth.cr_model) on the
+    device, with its rapral_cr_model struct."""
+
+    def __init__(self, model, device):
+        m = model
+        t = {k: _t(m[k], np.float64, device) for k in ("E", "g", "hp_C", "hp_n", "e_C", "e_n", "A", "lam", "ii_C",
+                                                          "ii_n")}
+        t["lo"] = _t(m["lo"], np.int32, device)
+        t["up"] = _t(m["up"], np.int32, device)
+        self.t = t
+        s = CrModel()
+        s.n_levels, s.n_levels_all = int(m["l"]), int(len(m["E"]))
+        s.n_trans = int(len(m["lo"]))
+        for k, v in t.items():
+            setattr(s, k, v.data_ptr())
+        s.E_ionize, s.g_ion = float(m["E_ion"]), float(m["g_ion"])
+        s.col, s.ion_col = int(m["col"]), int(m["ion_col"])
+        self.struct = s
+        self.l = s.n_levels
+
+
+def qss_populations(ctx, dmodel, dcells, out):
+    """QSS level populations [C, l] (rapral_qss_populations) into `out`."""
+    ctx.check(ctx.lib.rapral_qss_populations(ctx.h, ct.byref(dmodel.struct), ct.byref(dcells.struct), _ptr(out)))
+    return out
 
 
 def fibonacci_rays(ctx, geo, n_los, device, points=None):
