@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(32 * QW) k_qss(rapral_cr_model m, rapral_cells
         Qv[w][lane] = m.g[lane] * exp(-ph.c2 * m.E[lane] / Tve);
     }
     __syncwarp();
+    const double lnTtr = log(Ttr), lnTve = log(Tve), iTtr = 1.0 / Ttr, iTve = 1.0 / Tve;
     // transition rates per particle of the lower (up) / upper (down) level;
     // every warp checks every transition before any indexed use
     bool bad = false;
@@ -50,10 +51,11 @@ __global__ void __launch_bounds__(32 * QW) k_qss(rapral_cr_model m, rapral_cells
             bad = true;
             continue;
         }
+        // C T^n e^{-theta/T} as C e^{n ln T - theta/T}: one exp a rate
         const double theta = ph.c2 * (m.E[j] - m.E[i]);
-        const double kh_up = m.hp_C[t] * pow(Ttr, m.hp_n[t]) * exp(-theta / Ttr);
+        const double kh_up = m.hp_C[t] * exp(m.hp_n[t] * lnTtr - theta * iTtr);
         const double kh_dn = kh_up * Qh[w][i] / Qh[w][j];
-        const double ke_up = m.e_C[t] * pow(Tve, m.e_n[t]) * exp(-theta / Tve);
+        const double ke_up = m.e_C[t] * exp(m.e_n[t] * lnTve - theta * iTve);
         const double ke_dn = ke_up * Qv[w][i] / Qv[w][j];
         const double rad = m.A[t] * (m.lam[t] >= 200.0 ? 1.0 : 0.0);
         rate_up[w][t] = (kh_up * nM + ke_up * ne) / N_AVOGADRO;
