@@ -60,12 +60,12 @@ def parse():
 
 
 # DRAM bytes (read + write) of one FP32 line-sum launch on the stagnation line
-# at full size (200 cells x 1e6 points, tiling 128 x 2), from a one-pass ncu
+# at full size (200 cells x 1e6 points, tiling 128 x 4), from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
 # with this SHA-1.  Other cell / point counts scale in proportion (the bytes are
 # the kappa / j rows written); a different source gives null.
-LINE_SUM_TRAFFIC = {"sha1": "e49ed04cfd7963832a76f374308fc5c84d152a4f", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 57_468_672 + 1_550_780_928}
+LINE_SUM_TRAFFIC = {"sha1": "9ebc7e589ded42aa49fc9b26160a3be0251eede1", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 57_973_504 + 1_550_695_424}
 
 
 def line_sum_traffic(cells, grid_points):
