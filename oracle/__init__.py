@@ -98,6 +98,7 @@ def lib():
                 "orc_march": (None, [i64, vp, vp, d, vp, vp, i64, i64, i32, d, P(_Grid), i64, d, vp]),
                 "orc_march_nodes": (None, [i64, vp, vp, vp, vp, i64, i64, i32, d, P(_Grid), i64, d, vp]),
                 "orc_set_broadening": (None, [ct.c_int, ct.c_int, vp, ct.c_int, vp]),
+                "orc_set_departures": (None, [i64, vp, vp, vp]),
                 "orc_stark_coeff_ionize": (d, [d, d, d]),
                 "orc_oscillator_strength": (d, [d, d, d, d]),
                 "orc_resonance_hwhm": (d, [d, d, d, d, d]),
@@ -189,6 +190,22 @@ def set_broadening(flags, E_ionize=None, column_mass=None):
     lib().orc_set_broadening(int(flags), E.shape[0], _p(E) if E.size else None, M.shape[0],
                              _p(M) if M.size else None)
     set_broadening._keep = (E, M)
+
+
+def set_departures(ln_b=None, lev_u=None, lev_l=None):
+    """Departure coefficients for every later call: ln_b [C][S][n_lev] (ln of
+    N / N_Boltzmann per collisional-radiative level), lev_u / lev_l [L] the
+    level index of each line's upper / lower level (-1: Boltzmann).  No
+    argument: off."""
+    if ln_b is None:
+        lib().orc_set_departures(0, None, None, None)
+        set_departures._keep = None
+        return
+    b = np.ascontiguousarray(ln_b, np.float64)
+    u = np.ascontiguousarray(lev_u, np.int32)
+    lo = np.ascontiguousarray(lev_l, np.int32)
+    lib().orc_set_departures(b.shape[2], _p(b), _p(u), _p(lo))
+    set_departures._keep = (b, u, lo)
 
 
 def stark_coeff_ionize(lam0, Eu, Eion):

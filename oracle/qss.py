@@ -101,3 +101,17 @@ def solve_cells(model, cells, ion_col=None):
         R, b = rate_matrix(model, cells.Ttr[c], cells.Tve[c], n_M, n_e, n_ion, float(dens[col]))
         out[c] = np.linalg.solve(R, b)
     return out
+
+
+def departures(model, cells, lnpref, s, n_qss, n_lev=None):
+    """ln b_i = ln N_i(QSS) - ln N_i(Boltzmann) of the model's levels for
+    species s in every cell, with N_i(Boltzmann) = exp(lnpref[c][s] + ln g_i
+    - c2 E_i / T_ve) (the main path's populations); returns [C, n_lev]
+    (zero past the model's levels)."""
+    l = int(model["l"])
+    n_lev = l if n_lev is None else n_lev
+    out = np.zeros((len(cells.Tve), n_lev))
+    for c in range(len(cells.Tve)):
+        lnB = lnpref[c, s] + np.log(model["g"][:l]) - C2 * model["E"][:l] / cells.Tve[c]
+        out[c, :l] = np.log(n_qss[c]) - lnB
+    return out

@@ -285,13 +285,31 @@ static void line_widths(const orc_species* sp, const orc_lines* ln, const orc_ce
     st->lamV = orc_voigt_hwhm(st->lamL, st->lamG);
 }
 
+// Sec. 2.1 non-Boltzmann populations (off by default): departure coefficients
+// b = N / N_Boltzmann of the collisional-radiative levels, ln b per
+// [cell][species][level]; a line whose upper (lower) level has a level index
+// >= 0 takes N_u b_u (N_l b_l).
+static int64_t DEP_NLEV = 0;
+static const double* DEP_LNB = nullptr;
+static const int32_t* DEP_LEV_U = nullptr;
+static const int32_t* DEP_LEV_L = nullptr;
+void orc_set_departures(int64_t n_lev, const double* ln_b, const int32_t* lev_u, const int32_t* lev_l) {
+    DEP_NLEV = n_lev; DEP_LNB = ln_b; DEP_LEV_U = lev_u; DEP_LEV_L = lev_l;
+}
+static double departure(const orc_species* sp, int64_t c, int s, const int32_t* lev, int64_t l) {
+    if (!DEP_LNB || !lev || lev[l] < 0) return 0.0;
+    return DEP_LNB[(c * sp->S + s) * DEP_NLEV + lev[l]];
+}
+
 static void line_strengths(const orc_species* sp, const orc_lines* ln, const orc_cells* cells,
                            const double* lnpref, int64_t l, int64_t c, orc_line_state* st) {
     const int s = ln->species[l];
     const double Ttr = cells->Ttr[c], Tve = cells->Tve[c];
     const double lp = lnpref[c * sp->S + s];
-    const double lnNu = orc_ln_level_pop(lp, ln->gu[l], ln->Eu_el[l], ln->Eu_v[l], ln->Eu_j[l], Tve, Ttr);
-    const double lnNl = orc_ln_level_pop(lp, ln->gl[l], ln->El_el[l], ln->El_v[l], ln->El_j[l], Tve, Ttr);
+    const double lnNu = orc_ln_level_pop(lp, ln->gu[l], ln->Eu_el[l], ln->Eu_v[l], ln->Eu_j[l], Tve, Ttr) +
+                        departure(sp, c, s, DEP_LEV_U, l);
+    const double lnNl = orc_ln_level_pop(lp, ln->gl[l], ln->El_el[l], ln->El_v[l], ln->El_j[l], Tve, Ttr) +
+                        departure(sp, c, s, DEP_LEV_L, l);
     const double Nu = std::exp(lnNu);
     const double lcm = ln->lam0[l] * 1e-7;
     st->Sj = 1e-7 * (hP * cL / (4.0 * M_PI)) * Nu * ln->A[l] / lcm;

@@ -671,3 +671,30 @@ def cr_model(seed=1005, species="N", n_levels=20, n_lumped=0, radiative_fraction
                 ii_C=lu(1e12, 1e14, n_levels), ii_n=np.full(n_levels, 0.5), E_ion=E_ion,
                 g_ion=float(ATOM_GROUND_G[ion]) if ion else 1.0, col=int(RAD_DENSITY_COL[s]),
                 ion_col=FLOW_SPECIES.index(ion) if ion else -1)
+
+
+def cr_lines(model, species, base=None, seed=1006):
+    """Lines of a collisional-radiative model's radiating transitions (A > 0,
+    centre 50-2000 nm) for the atomic radiator `species`, merged with an
+    optional base line list and sorted by centre; returns (Lines, lev_u,
+    lev_l) with the model-level index of every line's upper / lower level
+    (-1 for the base lines)."""
+    rng = np.random.default_rng(seed)
+    s = RAD_SPECIES.index(species)
+    keep = np.nonzero((model["A"] > 0) & (model["lam"] >= 50.0) & (model["lam"] <= 2000.0))[0]
+    n = len(keep)
+    lo, up = model["lo"][keep], model["up"][keep]
+    z = np.zeros(n)
+    new = Lines(lam0=model["lam"][keep].astype(np.float64), A=model["A"][keep].astype(np.float64),
+                lamS0=10.0 ** rng.uniform(-4, -1, n), species=np.full(n, s, np.int32),
+                Eu_el=model["E"][up].astype(np.float64), Eu_v=z.copy(), Eu_j=z.copy(), gu=model["g"][up].astype(np.float64),
+                El_el=model["E"][lo].astype(np.float64), El_v=z.copy(), El_j=z.copy(), gl=model["g"][lo].astype(np.float64))
+    lev_u, lev_l = up.astype(np.int32), lo.astype(np.int32)
+    if base is not None:
+        new = Lines(**{k: np.concatenate([getattr(base, k), getattr(new, k)]) for k in Lines.__dataclass_fields__})
+        m = len(base)
+        lev_u = np.concatenate([np.full(m, -1, np.int32), lev_u])
+        lev_l = np.concatenate([np.full(m, -1, np.int32), lev_l])
+    order = np.argsort(new.lam0, kind="stable")
+    new = Lines(**{k: np.ascontiguousarray(getattr(new, k)[order]) for k in Lines.__dataclass_fields__})
+    return new, lev_u[order], lev_l[order]
