@@ -473,6 +473,33 @@ typedef struct {
 RAPRAL_API int rapral_qss_populations(rapral_ctx* ctx, const rapral_cr_model* model, const rapral_cells* cells,
                        double* n_out);
 
+/* Departure coefficients b = N / N^B of the model's levels (Sec. 2.1: the
+ * QSS populations replace the Boltzmann populations of the main path for the
+ * levels they solve).  For radiator `species` of n_species, writes
+ * ln_b[(c n_species + species) n_lev + i] = ln n_qss[c][i] - (lnpref[c][species]
+ * + ln g_i - hc E_i / k T_ve) for i < n_levels and 0 for n_levels <= i < n_lev;
+ * other species' rows are left as they are.  n_qss [C][n_levels] is
+ * rapral_qss_populations' output, cells->lnpref rapral_populations'; all
+ * arrays device.  Errors: EINVAL (sizes; device: a population <= 0, at the
+ * next sync). */
+RAPRAL_API int rapral_qss_departures(rapral_ctx* ctx, const rapral_cr_model* model, const rapral_cells* cells,
+                                     int32_t species, int32_t n_species, const double* n_qss, double* ln_b,
+                                     int32_t n_lev);
+
+/* Non-Boltzmann level populations in later rapral_spectral_coeffs calls of
+ * this context (Sec. 2.1): a line whose upper (lower) level has index
+ * lev_u[l] >= 0 (lev_l[l] >= 0) takes N_u b_u (N_l b_l), with ln b read from
+ * ln_b [n_cells][n_species][n_lev]; -1 keeps the Boltzmann population.  The
+ * emission scales by b_u, the absorption by b_u (N_l b_l g_u / (N_u b_u g_l)
+ * - 1) (stimulated emission from the departed populations).  All arrays are
+ * device and caller-owned; they must stay valid while set.  A coefficient
+ * call whose cell, species or line counts differ from these returns EINVAL;
+ * an index outside [-1, n_lev) fails that call at its sync.  ln_b NULL turns
+ * the departures off.  The batch and allocation-free paths do not use them. */
+RAPRAL_API int rapral_set_departures(rapral_ctx* ctx, int32_t n_lev, const double* ln_b, int64_t n_cells,
+                                     int32_t n_species, const int32_t* lev_u, const int32_t* lev_l,
+                                     int64_t n_lines);
+
 /* ----------------------------------------------- Fibonacci lines of sight -- */
 
 /* Lines of sight of the paper's own angular path (Sec. 2.2.3, Fibonacci

@@ -52,6 +52,8 @@ static const char* check_name(int c) {
         case CHK_LOS_INDEX: return "line-of-sight index out of range";
         case CHK_CR_TRANS: return "level-model transition indices out of range";
         case CHK_CR_SINGULAR: return "singular QSS rate matrix";
+        case CHK_CR_POP: return "QSS population not positive: no departure coefficient";
+        case CHK_DEP_LEVEL: return "line level index outside the departure table";
         default: return "device check";
     }
 }
@@ -248,6 +250,11 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
         return set_error(ctx, RAPRAL_EINVAL, "cell array sizes");
     if (sp->n_species < 1 || sp->n_species > RAPRAL_MAX_SPECIES) return set_error(ctx, RAPRAL_EINVAL, "species count");
     if (cells->n_cells > 0 && !cells->lnpref) return set_error(ctx, RAPRAL_EINVAL, "cells.lnpref is null");
+    if (ctx->dep_lnb && (ctx->dep_C != cells->n_cells || ctx->dep_S != sp->n_species || ctx->dep_L != ln->n_lines))
+        return set_error(ctx, RAPRAL_EINVAL,
+                         "departure table of %lld cells, %d species, %lld lines; call has %lld, %d, %lld",
+                         (long long)ctx->dep_C, ctx->dep_S, (long long)ctx->dep_L, (long long)cells->n_cells,
+                         sp->n_species, (long long)ln->n_lines);
     cudaSetDevice(ctx->device);
     const int64_t C = cells->n_cells, L = ln->n_lines;
     const size_t esz = precision == RAPRAL_FP64 ? 8 : 4;
@@ -304,6 +311,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     if (e == cudaSuccess) e = cudaMemsetAsync(plan.wmax, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = launch_validate_cells(ctx, cells);
     if (e == cudaSuccess) e = launch_validate_lines(ctx, ln, sp->n_species);
+    if (e == cudaSuccess && ctx->dep_lnb) e = launch_check_levels(ctx, ctx->dep_u, ctx->dep_l, L, ctx->dep_nlev);
     if (e == cudaSuccess)
         e = launch_line_prep(ctx, sp, ln, g->lam_min, h, ph, lp, lf, plan.sorted_flag, &ctx->broad, lb, lb32);
     if (e == cudaSuccess) e = launch_cell_prep(ctx, cells, ph, cp, dmax);
@@ -312,8 +320,12 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     if (e == cudaSuccess) e = launch_bin_count(ctx, ln, g, h, &plan);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_pinned, plan.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    // the device checks ran before: on a failed one the counts were never written
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->h_pinned + 4, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_status(ctx, e, "line binning");
+    if (ctx->h_pinned[4 + ST_CODE]) return read_status(ctx);
     const int64_t total = ctx->h_pinned[0];
     // phase 2: tile lists
     need = arena_need(phase1, (size_t)(total + 1) * sizeof(int));
@@ -334,6 +346,9 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     a.lam_min = g->lam_min; a.h = h; a.k0 = k0; a.nk = nk; a.ld = ld; a.tile_w = W;
     a.kappa = kappa; a.emis = emis; a.status = ctx->d_status; a.stats = ctx->d_stats; a.count = ctx->count_work;
     a.lb = lb; a.lb32 = lb32; a.cb = cb; a.cb32 = cb32;
+    if (ctx->dep_lnb) {
+        a.dep_lnb = ctx->dep_lnb; a.dep_u = ctx->dep_u; a.dep_l = ctx->dep_l; a.dep_nlev = ctx->dep_nlev;
+    }
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");
 }
@@ -474,6 +489,39 @@ int rapral_qss_populations(rapral_ctx* ctx, const rapral_cr_model* m, const rapr
     cudaError_t e = launch_validate_cells(ctx, cells);
     if (e == cudaSuccess) e = launch_qss(ctx, m, cells, n_out, make_phys(ctx->codata));
     return cuda_status(ctx, e, "QSS populations");
+}
+
+int rapral_qss_departures(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, int32_t species,
+                          int32_t n_species, const double* n_qss, double* ln_b, int32_t n_lev) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!m || !cells || !n_qss || !ln_b) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (m->n_levels < 1 || m->n_levels > 32 || !m->E || !m->g) return set_error(ctx, RAPRAL_EINVAL, "level model");
+    if (n_species < 1 || n_species > RAPRAL_MAX_SPECIES || species < 0 || species >= n_species)
+        return set_error(ctx, RAPRAL_EINVAL, "species %d of %d", species, n_species);
+    if (n_lev < m->n_levels) return set_error(ctx, RAPRAL_EINVAL, "n_lev %d < n_levels %d", n_lev, m->n_levels);
+    if (cells->n_cells < 0) return set_error(ctx, RAPRAL_EINVAL, "cell count");
+    if (cells->n_cells == 0) return RAPRAL_OK;
+    if (!cells->Tve || !cells->lnpref) return set_error(ctx, RAPRAL_EINVAL, "cells need Tve and lnpref");
+    cudaSetDevice(ctx->device);
+    return cuda_status(ctx, launch_qss_departures(ctx, m, cells, species, n_species, n_qss, ln_b, n_lev,
+                                                  make_phys(ctx->codata)),
+                       "departure coefficients");
+}
+
+int rapral_set_departures(rapral_ctx* ctx, int32_t n_lev, const double* ln_b, int64_t n_cells, int32_t n_species,
+                          const int32_t* lev_u, const int32_t* lev_l, int64_t n_lines) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!ln_b) {
+        ctx->dep_lnb = nullptr; ctx->dep_u = ctx->dep_l = nullptr;
+        ctx->dep_nlev = ctx->dep_S = 0; ctx->dep_C = ctx->dep_L = 0;
+        return RAPRAL_OK;
+    }
+    if (!lev_u || !lev_l) return set_error(ctx, RAPRAL_EINVAL, "null level index array");
+    if (n_lev < 1 || n_cells < 0 || n_lines < 0 || n_species < 1 || n_species > RAPRAL_MAX_SPECIES)
+        return set_error(ctx, RAPRAL_EINVAL, "departure table sizes");
+    ctx->dep_lnb = ln_b; ctx->dep_u = lev_u; ctx->dep_l = lev_l;
+    ctx->dep_nlev = n_lev; ctx->dep_S = n_species; ctx->dep_C = n_cells; ctx->dep_L = n_lines;
+    return RAPRAL_OK;
 }
 
 int rapral_set_broadening(rapral_ctx* ctx, int32_t flags, int32_t n_species, const double* E_ionize,

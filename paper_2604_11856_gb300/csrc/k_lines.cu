@@ -320,10 +320,17 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
             const LinePrep L = a.lp[l];
             PairF64 P;
             P.klo = 1; P.khi = 0;
-            const double lnNu = a.lnpref[c * a.S + L.species] + L.lngu - (L.Eve_u * cp.bve + L.Er_u * cp.btr);
+            double du = 0.0, dl = 0.0;   // departure coefficients (ln b) of the line's levels
+            if (a.dep_lnb) {
+                const double* row = a.dep_lnb + (c * a.S + L.species) * a.dep_nlev;
+                const int iu = a.dep_u[l], il = a.dep_l[l];
+                if (iu >= 0) du = row[iu];
+                if (il >= 0) dl = row[il];
+            }
+            const double lnNu = a.lnpref[c * a.S + L.species] + L.lngu - (L.Eve_u * cp.bve + L.Er_u * cp.btr) + du;
             const double Sj = exp(L.lnAj + lnNu);
             if (Sj > 0.0) {
-                const double x = L.dEve * cp.bve + L.dEr * cp.btr;
+                const double x = L.dEve * cp.bve + L.dEr * cp.btr + (dl - du);
                 const double Sk = exp(L.lnAk + lnNu) * expm1(x);
                 const double lamG = L.cD * cp.sqrtT;
                 const double lamL = lorentz64(a, L, cp, l, c);
@@ -519,10 +526,12 @@ struct PairF32 {
     float r, aj, ak;
 };
 
-template <bool BR>
+// FL: bit 0 the optional Lorentz terms, bit 1 the departure coefficients.
+template <int FL>
 __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF32& L, const CellPrep& cp, float2 lp,
                                                float2 cb, int line, int64_t c, float hf, float inv_hf, int kt0,
                                                float kt0f, float kt1f, bool count, PairF32* P, int64_t* cnt) {
+    constexpr bool BR = (FL & 1) != 0, DEP = (FL & 2) != 0;
     if (!(lp.x > -INFINITY)) return false;
     // widths first: most candidates of a tile list miss the tile in a given cell
     const float lamG = L.cD * cp.sqrtT_f;
@@ -568,8 +577,17 @@ __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF
     if (lo_rel > hi_rel) return false;
     // strengths: ln S_j = lnAj + ln g_u + ln(N_s/Z_s) - (E_el + E_V)_u c2/T_ve - E_J,u c2/T_tr
     // and x = ln(N_l g_u / (N_u g_l)) = dE_ve c2/T_ve + dE_J c2/T_tr, in float-float
-    const float2 yj = ff_add(ff_add(L.lnAjg, lp), ff_neg(ff_add(ff_mul(L.Eve_u, cp.bve_ff), ff_mul(L.Er_u, cp.btr_ff))));
-    const float2 x = ff_add(ff_mul(L.dEve, cp.bve_ff), ff_mul(L.dEr, cp.btr_ff));
+    float2 yj = ff_add(ff_add(L.lnAjg, lp), ff_neg(ff_add(ff_mul(L.Eve_u, cp.bve_ff), ff_mul(L.Er_u, cp.btr_ff))));
+    float2 x = ff_add(ff_mul(L.dEve, cp.bve_ff), ff_mul(L.dEr, cp.btr_ff));
+    if (DEP) {   // departure coefficients: ln N_u += ln b_u, x += ln b_l - ln b_u
+        const int iu = a.dep_u[line], il = a.dep_l[line];
+        if (iu >= 0 || il >= 0) {
+            const double* row = a.dep_lnb + ((int64_t)c * a.S + L.species) * a.dep_nlev;
+            const double du = iu >= 0 ? row[iu] : 0.0, dl = il >= 0 ? row[il] : 0.0;
+            yj = ff_add(yj, ff_from(du));
+            x = ff_add(x, ff_from(dl - du));
+        }
+    }
     const float Sj = exp_ff(yj);
     float2 yk = ff_add(yj, L.dAkj);
     float fk;
@@ -678,7 +696,7 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
 // pair's window reaches the i-th run of 32 points is the same for the whole
 // warp, so runs outside the window are skipped without a masked evaluation.
 // Warps never wait for each other.
-template <int PPT, bool BR>
+template <int PPT, int FL>
 __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
                                               float2* smlp, float2* smcb, float4* acc, int lane, int64_t* cnt) {
     constexpr int TW = 32 * PPT;
@@ -703,7 +721,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     if (lane < a.S) {   // the cell's ln(N_s / Z_s) as float-float pairs
         const double v = a.lnpref[c * a.S + lane];
         smlp[lane] = v > -INFINITY ? ff_from(v) : make_float2(-INFINITY, 0.0f);
-        if (BR) smcb[lane] = a.cb32[c * a.S + lane];   // (N_0, W) of the optional terms
+        if (FL & 1) smcb[lane] = a.cb32[c * a.S + lane];   // (N_0, W) of the optional terms
     }
     __syncwarp();
     const int beg = a.tile_off[t], end = a.tile_off[t + 1];
@@ -714,7 +732,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
         if (lane < nb) {
             const int l = a.tile_lines[b + lane];
             const LineF32 L = a.lf[l];
-            valid = setup_pair_f32<BR>(a, L, cp, smlp[L.species], BR ? smcb[L.species] : make_float2(0.f, 0.f), l,
+            valid = setup_pair_f32<FL>(a, L, cp, smlp[L.species], (FL & 1) ? smcb[L.species] : make_float2(0.f, 0.f), l,
                                        c, hf, inv_hf, kt0, kt0f, kt1f,
                                    count, &P, cnt);
         }
@@ -764,7 +782,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
 #endif
 #define RAPRAL_LS_BLOCKS(WPB) (RAPRAL_LS_WARPS / (WPB))
 
-template <int PPT, int WPB, bool BR = false>
+template <int PPT, int WPB, int FL = 0>
 __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f32(LineSumArgs a) {
     if (*a.status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -776,7 +794,7 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
     __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float4 acc[WPB][32 * PPT];
     int64_t cnt[4] = {0, 0, 0, 0};
-    warp_tile_f32<PPT, BR>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
+    warp_tile_f32<PPT, FL>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
     if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
@@ -814,7 +832,8 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_ba
         const int t = (int)(local / it.n_groups);
         const int64_t c = (local - (int64_t)t * it.n_groups) * WPB + warp;
         if (c < it.a.C)
-            warp_tile_f32<PPT, BR>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
+            warp_tile_f32<PPT, BR ? 1 : 0>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane,
+                                           cnt);
         __syncwarp();
     }
     if (items[0].a.count) block_count(stats, cnt[0], cnt[1], cnt[2], cnt[3]);
@@ -904,14 +923,18 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
     }
     // FP32: warp-level kernel, WPB cells per block; with the optional
     // resonance / van der Waals terms four cells a block
-    if (a.lb32) {
+    const int fl = (a.lb32 ? 1 : 0) | (a.dep_lnb ? 2 : 0);
+    if (fl) {
         dim3 gb(div_up(a.C, 4), grid.y);
-        switch (a.tile_w) {
-            case 128: k_line_sum_f32<4, 4, true><<<gb, 128, 0, ctx->stream>>>(a); break;
-            case 256: k_line_sum_f32<8, 4, true><<<gb, 128, 0, ctx->stream>>>(a); break;
-            case 512: k_line_sum_f32<16, 4, true><<<gb, 128, 0, ctx->stream>>>(a); break;
-            default: return cudaErrorInvalidValue;
-        }
+#define RAPRAL_LSF(FL)                                                                   \
+    switch (a.tile_w) {                                                                  \
+        case 128: k_line_sum_f32<4, 4, FL><<<gb, 128, 0, ctx->stream>>>(a); break;      \
+        case 256: k_line_sum_f32<8, 4, FL><<<gb, 128, 0, ctx->stream>>>(a); break;      \
+        case 512: k_line_sum_f32<16, 4, FL><<<gb, 128, 0, ctx->stream>>>(a); break;     \
+        default: return cudaErrorInvalidValue;                                           \
+    }
+        if (fl == 1) { RAPRAL_LSF(1) } else if (fl == 2) { RAPRAL_LSF(2) } else { RAPRAL_LSF(3) }
+#undef RAPRAL_LSF
         return cudaGetLastError();
     }
     const int wpb = a.tile_w == 512 ? 4 : ctx->cells_per_block;

@@ -134,6 +134,39 @@ __global__ void __launch_bounds__(32 * QW) k_qss(rapral_cr_model m, rapral_cells
     if (lane < l) n_out[c * l + lane] = b[lane];
 }
 
+// Departure coefficients of the model's levels (Sec. 2.1): ln b_i = ln N_i -
+// ln N_i^B with the Boltzmann population of the main path, ln N_i^B =
+// lnpref + ln g_i - c2 E_i / T_ve.  One thread per (cell, level slot); slots
+// past the model's levels hold 0 (b = 1).
+__global__ void k_qss_departures(const double* __restrict__ E, const double* __restrict__ g, int l,
+                                 const double* __restrict__ Tve, const double* __restrict__ lnpref,
+                                 const double* __restrict__ n_qss, int64_t C, int s, int S, int n_lev, double c2,
+                                 double* __restrict__ ln_b, int* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C * n_lev) return;
+    const int64_t c = i / n_lev;
+    const int k = (int)(i - c * n_lev);
+    double v = 0.0;
+    if (k < l) {
+        const double N = n_qss[c * l + k];
+        if (!(N > 0.0)) {
+            fail(status, CHK_CR_POP, c);
+            v = 0.0;
+        } else {
+            v = log(N) - (lnpref[c * S + s] + log(g[k]) - c2 * E[k] / Tve[c]);
+        }
+    }
+    ln_b[(c * S + s) * n_lev + k] = v;
+}
+
+__global__ void k_check_levels(const int32_t* __restrict__ u, const int32_t* __restrict__ lo, int64_t L, int n_lev,
+                               int* status) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    const int a = u[l], b = lo[l];
+    if (a < -1 || a >= n_lev || b < -1 || b >= n_lev) fail(status, CHK_DEP_LEVEL, l);
+}
+
 }  // namespace
 
 cudaError_t launch_qss(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, double* n_out,
@@ -141,5 +174,22 @@ cudaError_t launch_qss(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_c
     if (cells->n_cells == 0) return cudaSuccess;
     if (m->n_trans > QMAXT || m->n_levels > QMAXL) return cudaErrorInvalidValue;
     k_qss<<<div_up(cells->n_cells, QW), 32 * QW, 0, ctx->stream>>>(*m, *cells, ph, n_out, ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qss_departures(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, int32_t s,
+                                  int32_t S, const double* n_qss, double* ln_b, int32_t n_lev, const Phys& ph) {
+    const int64_t n = cells->n_cells * n_lev;
+    if (n == 0) return cudaSuccess;
+    k_qss_departures<<<div_up(n, 256), 256, 0, ctx->stream>>>(m->E, m->g, m->n_levels, cells->Tve, cells->lnpref,
+                                                             n_qss, cells->n_cells, s, S, n_lev, ph.c2, ln_b,
+                                                             ctx->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_levels(rapral_ctx* ctx, const int32_t* lev_u, const int32_t* lev_l, int64_t L,
+                                int32_t n_lev) {
+    if (L == 0) return cudaSuccess;
+    k_check_levels<<<div_up(L, 256), 256, 0, ctx->stream>>>(lev_u, lev_l, L, n_lev, ctx->d_status);
     return cudaGetLastError();
 }

@@ -54,7 +54,8 @@ struct BroadArgs {
 enum { ST_CODE = 0, ST_CHECK = 1, ST_INDEX = 2 };
 enum {
     CHK_NONE = 0, CHK_CELL_T, CHK_CELL_N, CHK_LINE_SPECIES, CHK_LINE_LAM, CHK_LINE_G,
-    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT, CHK_LOS_INDEX, CHK_CR_TRANS, CHK_CR_SINGULAR
+    CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT, CHK_LOS_INDEX, CHK_CR_TRANS, CHK_CR_SINGULAR,
+    CHK_CR_POP, CHK_DEP_LEVEL
 };
 
 // ------------------------------------------------------------- records ----
@@ -148,6 +149,12 @@ struct rapral_ctx {
     int count_work = 1;                      // counters on (rapral_set_counters)
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing events
     BroadArgs broad = {};                    // optional Lorentz terms (flags 0: off)
+    // departure coefficients (rapral_set_departures; ln_b null: off)
+    const double* dep_lnb = nullptr;
+    const int32_t* dep_u = nullptr;
+    const int32_t* dep_l = nullptr;
+    int32_t dep_nlev = 0, dep_S = 0;
+    int64_t dep_C = 0, dep_L = 0;
     char err[512] = {0};
 };
 
@@ -249,6 +256,12 @@ struct LineSumArgs {
     const float2* lb32 = nullptr;
     const double2* cb = nullptr;
     const float2* cb32 = nullptr;
+    // optional departure coefficients (null: Boltzmann): ln b [C][S][dep_nlev],
+    // level index of every line's upper / lower level (-1: none)
+    const double* dep_lnb = nullptr;
+    const int32_t* dep_u = nullptr;
+    const int32_t* dep_l = nullptr;
+    int32_t dep_nlev = 0;
 };
 
 // Workspace of the optional resonance / van der Waals terms of one request:
@@ -311,6 +324,11 @@ cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n);
 // QSS collisional-radiative populations (k_qss.cu).
 cudaError_t launch_qss(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, double* n_out,
                        const Phys& ph);
+// ln b of the model's levels for one species, and the check of a departure table's level indices.
+cudaError_t launch_qss_departures(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, int32_t s,
+                                  int32_t S, const double* n_qss, double* ln_b, int32_t n_lev, const Phys& ph);
+cudaError_t launch_check_levels(rapral_ctx* ctx, const int32_t* lev_u, const int32_t* lev_l, int64_t L,
+                                int32_t n_lev);
 
 // Fibonacci lines of sight, node states and the angular flux (k_los.cu).
 cudaError_t launch_fib_count(rapral_ctx* ctx, const double* xf, int32_t nx, const double* rf, int32_t nr,

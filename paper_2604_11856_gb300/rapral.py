@@ -138,6 +138,8 @@ def load(build_if_missing=True):
             "rapral_fibonacci_flux": (i, [vp, i64, vp, vp, i32, vp, i32, i32, vp]),
             "rapral_set_broadening": (i, [vp, i32, i32, vp, i32, vp]),
             "rapral_qss_populations": (i, [vp, P(CrModel), P(Cells), vp]),
+            "rapral_qss_departures": (i, [vp, P(CrModel), P(Cells), i32, i32, vp, vp, i32]),
+            "rapral_set_departures": (i, [vp, i32, vp, i64, i32, vp, vp, i64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -179,6 +181,20 @@ class Context:
         self.check(self.lib.rapral_set_broadening(self.h, int(flags), E.shape[0],
                                                   E.ctypes.data_as(ct.c_void_p) if E.size else None, M.shape[0],
                                                   M.ctypes.data_as(ct.c_void_p) if M.size else None))
+
+    def set_departures(self, ln_b=None, lev_u=None, lev_l=None):
+        """Departure coefficients for later coefficient calls: device tensors
+        ln_b [C, S, n_lev] (float64), lev_u / lev_l [L] (int32, -1: none);
+        kept referenced while set.  No argument: off."""
+        if ln_b is None:
+            self.check(self.lib.rapral_set_departures(self.h, 0, None, 0, 0, None, None, 0))
+            self._dep = None
+            return
+        C, S, n = ln_b.shape
+        self._dep = (ln_b.contiguous(), lev_u.contiguous(), lev_l.contiguous())
+        b, u, lo = self._dep
+        self.check(self.lib.rapral_set_departures(self.h, int(n), _ptr(b), int(C), int(S), _ptr(u), _ptr(lo),
+                                                  int(u.shape[0])))
 
     def set_stream(self, stream):
         self.stream = stream
@@ -450,6 +466,15 @@ def qss_populations(ctx, dmodel, dcells, out):
     """QSS level populations [C, l] (rapral_qss_populations) into `out`."""
     ctx.check(ctx.lib.rapral_qss_populations(ctx.h, ct.byref(dmodel.struct), ct.byref(dcells.struct), _ptr(out)))
     return out
+
+
+def qss_departures(ctx, dmodel, dcells, species, n_qss, ln_b):
+    """ln b of the model's levels for radiator `species` (rapral_qss_departures)
+    into the device table ln_b [C, S, n_lev]."""
+    C, S, n = ln_b.shape
+    ctx.check(ctx.lib.rapral_qss_departures(ctx.h, ct.byref(dmodel.struct), ct.byref(dcells.struct), int(species),
+                                            int(S), _ptr(n_qss), _ptr(ln_b), int(n)))
+    return ln_b
 
 
 def fibonacci_rays(ctx, geo, n_los, device, points=None):
