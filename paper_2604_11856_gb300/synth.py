@@ -698,3 +698,60 @@ def cr_lines(model, species, base=None, seed=1006):
     order = np.argsort(new.lam0, kind="stable")
     new = Lines(**{k: np.ascontiguousarray(getattr(new, k)[order]) for k in Lines.__dataclass_fields__})
     return new, lev_u[order], lev_l[order]
+
+
+# Free-free fit coefficients c1..c8 of the hydrogenic cross section for N and
+# O (Sec. 2.2.1, Table 3).
+FF_FIT = {
+    "N": np.array([0.006805, -0.00934, 0.000116, 0.508, 1.046, 5.77e-5, 1.85, 0.000343]),
+    "O": np.array([0.001905, -0.005105, 8.176e-5, 0.4554, 1.0238, 5.329e-5, 1.7587, 0.003121]),
+}
+# Low terms of the ions (cm^-1, weight) for their partition functions.
+ION_TERMS = {"N": ([0.0, 15316.2, 32688.8], [9.0, 5.0, 1.0]),
+             "O": ([0.0, 26810.6, 40468.0], [4.0, 10.0, 6.0])}
+
+
+def continuum_model(seed=1007, species="N", n_levels=100, n_nodes=120, n_resonances=3, D="synthetic"):
+    """Synthetic atomic continuum model (Sec. 2.2.1 bound-free and free-free;
+    the TOPbase cross sections and Peach's D table are not available):
+    a ground level with the ground-term weight and n_levels - 1 levels
+    uniform in 15-99.5 % of the ionisation energy, weights 2-18; per level a
+    photoionisation table of n_nodes wavelengths, geometric from 10 nm to the
+    edge 1e7 / (E_ion - E_i) nm, with sigma = s0 (lam / edge)^3 (Kramers
+    shape), s0 log-uniform 1e-19-2e-17 cm^2, times up to n_resonances
+    Lorentzian bumps; the ion's low terms for Q_+; Table 3's free-free fit;
+    a D(sigma, T) table on 12 sigma x 8 T nodes, smooth with |D| <= 0.2
+    ("synthetic") or zero ("zero")."""
+    rng = np.random.default_rng(seed)
+    s = RAD_SPECIES.index(species)
+    E_ion = float(RAD_E_IONIZE[s])
+    E = np.concatenate([[0.0], np.sort(rng.uniform(0.15, 0.995, n_levels - 1)) * E_ion])
+    g = np.concatenate([[ATOM_GROUND_G[species]], 2.0 * rng.integers(1, 10, n_levels - 1)])
+    off = np.zeros(n_levels + 1, np.int64)
+    lam_parts, sig_parts = [], []
+    for i in range(n_levels):
+        edge = 1e7 / (E_ion - E[i])
+        lam = np.geomspace(10.0, edge, n_nodes)
+        lam[-1] = edge
+        s0 = 10.0 ** rng.uniform(np.log10(1e-19), np.log10(2e-17))
+        bump = np.ones(n_nodes)
+        for _ in range(rng.integers(0, n_resonances + 1)):
+            lr, w, a = rng.uniform(0.2, 0.98) * edge, rng.uniform(0.002, 0.02) * edge, rng.uniform(0.5, 5.0)
+            bump += a / (1.0 + ((lam - lr) / w) ** 2)
+        lam_parts.append(lam)
+        sig_parts.append(s0 * (lam / edge) ** 3 * bump)
+        off[i + 1] = off[i] + n_nodes
+    D_sigma = np.geomspace(0.02, 2.5, 12)
+    D_T = np.linspace(2000.0, 30000.0, 8)
+    if D == "zero":
+        Dv = np.zeros((8, 12))
+    else:
+        ph = rng.uniform(0, 2 * np.pi)
+        Dv = 0.2 * np.sin(ph + 2.0 * np.log(D_sigma)[None, :] + (D_T[:, None] / 12000.0)) * \
+            np.exp(-D_T[:, None] / 40000.0)
+    ion = {"N": "N+", "O": "O+"}[species]
+    iE, ig = ION_TERMS[species]
+    return dict(species=s, atom_col=int(RAD_DENSITY_COL[s]), ion_col=FLOW_SPECIES.index(ion), E_ion=E_ion,
+                E=E, g=g, node_off=off, node_lam=np.concatenate(lam_parts), node_sigma=np.concatenate(sig_parts),
+                ion_E=np.array(iE), ion_g=np.array(ig), ff_c=FF_FIT[species].copy(),
+                D_sigma=D_sigma, D_T=D_T, D=Dv)
