@@ -500,6 +500,57 @@ RAPRAL_API int rapral_set_departures(rapral_ctx* ctx, int32_t n_lev, const doubl
                                      int32_t n_species, const int32_t* lev_u, const int32_t* lev_l,
                                      int64_t n_lines);
 
+/* ------------------------------------------------------ atomic continuum -- */
+
+#define RAPRAL_MAX_CONT_MODELS 8
+#define RAPRAL_MAX_CONT_LEVELS 1024
+
+/* One atomic radiator's continuum data for rapral_continuum_coeffs (all
+ * arrays device, caller-owned).  Bound-free: levels i (E_i < E_ionize, g_i)
+ * each with a photoionisation table of >= 2 nodes (node_lam increasing,
+ * node_sigma >= 0), linear between nodes and zero outside them.  Free-free:
+ * the hydrogenic fit of Table 3 (ff_c = c1..c8) and an optional D(sigma, T)
+ * table, bilinear and clamped to its range (D NULL: D = 0).  Q_+ sums the
+ * ion terms (ion_E, ion_g). */
+typedef struct {
+    int32_t species;            /* radiator index: column of cells->lnpref      */
+    int32_t atom_col, ion_col;  /* density columns of the atom and of its ion   */
+    double E_ionize;            /* cm^-1                                        */
+    int32_t n_levels;           /* >= 1                                         */
+    const double* E;            /* [n_levels] cm^-1                             */
+    const double* g;            /* [n_levels]                                   */
+    int64_t n_nodes;            /* node_off[n_levels]                           */
+    const int64_t* node_off;    /* [n_levels + 1], node_off[0] = 0              */
+    const double* node_lam;     /* [n_nodes] nm                                 */
+    const double* node_sigma;   /* [n_nodes] cm^2                               */
+    int32_t n_ion_terms;        /* >= 1                                         */
+    const double* ion_E;        /* [n_ion_terms] cm^-1                          */
+    const double* ion_g;        /* [n_ion_terms]                                */
+    double ff_c[8];             /* free-free fit coefficients                   */
+    int32_t n_D_sigma, n_D_T;   /* >= 2 each when D is given, <= 64             */
+    const double* D_sigma;      /* [n_D_sigma] increasing                       */
+    const double* D_T;          /* [n_D_T] increasing, K                        */
+    const double* D;            /* [n_D_T][n_D_sigma] or NULL                   */
+} rapral_continuum;
+
+/* Atomic continuum of Sec. 2.2.1, ADDED to kappa and emis [C][ld] (FP64 or
+ * FP32 by precision, e.g. the output of rapral_spectral_coeffs) over grid
+ * points [k0, k0+nk).  Per cell (T = T_ve) and model:
+ *   kappa_bf = sum_i N_i sigma_i,  N_i = exp(lnpref[species]) g_i e^{-c2 E_i/T};
+ *   j_bf     = sum_i N_+ N_e S_i(T) B_lam(T) sigma_i (Kirchhoff with the
+ *              Saha-Boltzmann N_i,eq = N_+ N_e S_i, S_i = (h^2/(2 pi m_e k T))^1.5
+ *              g_i e^{c2 (E_ionize - E_i)/T} / (2 Q_+));
+ *   kappa_ff = exp(lnpref[species]) 2 Q_+ (2 pi m_e k T/h^2)^1.5 e^{-c2 E_ionize/T}
+ *              sigma^H (1 + D),  sigma^3 sigma^H 1e40 = A1/sigma + A2,
+ *              sigma = 91.1267 / lam;  j_ff = B_lam kappa_ff.
+ * cells->lnpref must hold rapral_populations' output; n_species is its row
+ * length.  Errors: EINVAL (sizes, columns; device: tables not increasing,
+ * node offsets, E_i >= E_ionize, g <= 0, at the call's sync). */
+RAPRAL_API int rapral_continuum_coeffs(rapral_ctx* ctx, const rapral_continuum* models, int32_t n_models,
+                                       int32_t n_species, const rapral_cells* cells, const rapral_grid* grid,
+                                       int64_t k0, int64_t nk, int precision, void* kappa, void* emis,
+                                       int64_t ld);
+
 /* ----------------------------------------------- Fibonacci lines of sight -- */
 
 /* Lines of sight of the paper's own angular path (Sec. 2.2.3, Fibonacci

@@ -54,12 +54,13 @@ static const char* check_name(int c) {
         case CHK_CR_SINGULAR: return "singular QSS rate matrix";
         case CHK_CR_POP: return "QSS population not positive: no departure coefficient";
         case CHK_DEP_LEVEL: return "line level index outside the departure table";
+        case CHK_CONT_TABLE: return "continuum model: node offsets, tables, levels or D grid invalid";
         default: return "device check";
     }
 }
 
 // Reads the sticky status (synchronises the stream).
-static int read_status(rapral_ctx* ctx) {
+int read_status(rapral_ctx* ctx) {
     cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost,
                                     ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

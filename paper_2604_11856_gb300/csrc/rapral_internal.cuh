@@ -55,7 +55,7 @@ enum { ST_CODE = 0, ST_CHECK = 1, ST_INDEX = 2 };
 enum {
     CHK_NONE = 0, CHK_CELL_T, CHK_CELL_N, CHK_LINE_SPECIES, CHK_LINE_LAM, CHK_LINE_G,
     CHK_LINE_A, CHK_SEG_CELL, CHK_SEG_DS, CHK_DIR, CHK_TIMEOUT, CHK_LOS_INDEX, CHK_CR_TRANS, CHK_CR_SINGULAR,
-    CHK_CR_POP, CHK_DEP_LEVEL
+    CHK_CR_POP, CHK_DEP_LEVEL, CHK_CONT_TABLE
 };
 
 // ------------------------------------------------------------- records ----
@@ -162,6 +162,7 @@ struct rapral_ctx {
 int set_error(rapral_ctx* ctx, int code, const char* fmt, ...);
 // Wraps a CUDA call result.
 int cuda_status(rapral_ctx* ctx, cudaError_t e, const char* what);
+int read_status(rapral_ctx* ctx);   // sync, then the device status as an error code
 // Ensures the arena holds `bytes`; may synchronise the stream.
 int ws_reserve(rapral_ctx* ctx, size_t bytes);
 

@@ -82,6 +82,15 @@ class CrModel(ct.Structure):
                 ("g_ion", ct.c_double), ("col", ct.c_int32), ("ion_col", ct.c_int32)]
 
 
+class Continuum(ct.Structure):
+    _fields_ = [("species", ct.c_int32), ("atom_col", ct.c_int32), ("ion_col", ct.c_int32),
+                ("E_ionize", ct.c_double), ("n_levels", ct.c_int32), ("E", ct.c_void_p), ("g", ct.c_void_p),
+                ("n_nodes", ct.c_int64), ("node_off", ct.c_void_p), ("node_lam", ct.c_void_p),
+                ("node_sigma", ct.c_void_p), ("n_ion_terms", ct.c_int32), ("ion_E", ct.c_void_p),
+                ("ion_g", ct.c_void_p), ("ff_c", ct.c_double * 8), ("n_D_sigma", ct.c_int32),
+                ("n_D_T", ct.c_int32), ("D_sigma", ct.c_void_p), ("D_T", ct.c_void_p), ("D", ct.c_void_p)]
+
+
 class BatchItem(ct.Structure):
     _fields_ = [("species", ct.c_void_p), ("lines", ct.c_void_p), ("cells", ct.c_void_p), ("grid", ct.c_void_p),
                 ("rays", ct.c_void_p), ("k0", ct.c_int64), ("nk", ct.c_int64), ("kappa", ct.c_void_p),
@@ -138,6 +147,7 @@ def load(build_if_missing=True):
             "rapral_fibonacci_flux": (i, [vp, i64, vp, vp, i32, vp, i32, i32, vp]),
             "rapral_set_broadening": (i, [vp, i32, i32, vp, i32, vp]),
             "rapral_qss_populations": (i, [vp, P(CrModel), P(Cells), vp]),
+            "rapral_continuum_coeffs": (i, [vp, vp, i32, i32, P(Cells), P(Grid), i64, i64, i, vp, vp, i64]),
             "rapral_qss_departures": (i, [vp, P(CrModel), P(Cells), i32, i32, vp, vp, i32]),
             "rapral_set_departures": (i, [vp, i32, vp, i64, i32, vp, vp, i64]),
         }
@@ -460,6 +470,44 @@ class DeviceCrModel:
         s.col, s.ion_col = int(m["col"]), int(m["ion_col"])
         self.struct = s
         self.l = s.n_levels
+
+
+class DeviceContinuum:
+    """Atomic continuum models (dicts of host arrays as made by
+    synth.continuum_model) on the device, with their rapral_continuum array."""
+
+    def __init__(self, models, device):
+        self.t = []
+        self.structs = (Continuum * len(models))()
+        for k, m in enumerate(models):
+            t = {n: _t(m[n], np.float64, device) for n in ("E", "g", "node_lam", "node_sigma", "ion_E", "ion_g",
+                                                             "D_sigma", "D_T", "D")}
+            t["node_off"] = _t(m["node_off"], np.int64, device)
+            self.t.append(t)
+            s = self.structs[k]
+            s.species, s.atom_col, s.ion_col = int(m["species"]), int(m["atom_col"]), int(m["ion_col"])
+            s.E_ionize = float(m["E_ion"])
+            s.n_levels = int(len(m["E"]))
+            s.n_nodes = int(m["node_off"][-1])
+            s.n_ion_terms = int(len(m["ion_E"]))
+            for n in ("E", "g", "node_off", "node_lam", "node_sigma", "ion_E", "ion_g"):
+                setattr(s, n, t[n].data_ptr())
+            for j in range(8):
+                s.ff_c[j] = float(m["ff_c"][j])
+            if m.get("D") is not None:
+                s.n_D_sigma, s.n_D_T = int(len(m["D_sigma"])), int(len(m["D_T"]))
+                s.D_sigma, s.D_T, s.D = t["D_sigma"].data_ptr(), t["D_T"].data_ptr(), t["D"].data_ptr()
+        self.n = len(models)
+
+
+def continuum_coeffs(ctx, dcont, n_species, dcells, grid, k0, nk, precision, kappa, emis):
+    """Adds the atomic continuum (rapral_continuum_coeffs) to kappa, emis
+    ([C, >= nk] of the precision's dtype, rows stride(0) apart)."""
+    ld = _row_stride(kappa, emis, nk)
+    g = grid_struct(grid)
+    ctx.check(ctx.lib.rapral_continuum_coeffs(ctx.h, ct.byref(dcont.structs), dcont.n, int(n_species),
+                                              ct.byref(dcells.struct), ct.byref(g), int(k0), int(nk),
+                                              int(precision), _ptr(kappa), _ptr(emis), int(ld)))
 
 
 def qss_populations(ctx, dmodel, dcells, out):
