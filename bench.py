@@ -48,8 +48,11 @@ def parse():
     ap.add_argument("--serve-fp64-requests", type=int, default=4)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
-    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci", "qss"], default="stagnation",
-                    help="stagnation line (the bench line); afterbody / batch / fibonacci / qss: one-off measurements")
+    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci", "qss", "continuum"],
+                    default="stagnation",
+                    help="stagnation line (the bench line); afterbody / batch / fibonacci / qss / continuum: "
+                         "one-off measurements")
+    ap.add_argument("--cont-levels", type=int, default=100, help="continuum workload: levels per atom (N, O)")
     ap.add_argument("--fib-points", type=int, default=8, help="fibonacci workload: surface points")
     ap.add_argument("--fib-los", type=int, default=128, help="fibonacci workload: Fibonacci directions per point")
     ap.add_argument("--ab-small", action="store_true",
@@ -362,6 +365,76 @@ def run_qss(args):
     return 0
 
 
+def continuum_terms(models, grid, C, W=128):
+    """(cell, level, point) terms of the continuum level sums: per tile of W
+    points the levels whose table reaches the tile's first wavelength."""
+    last = np.concatenate([m["node_lam"][m["node_off"][1:] - 1] for m in models])
+    h = (grid.lam_max - grid.lam_min) / (grid.n - 1)
+    T = (grid.n + W - 1) // W
+    lam0 = grid.lam_min + (np.arange(T) * W).astype(np.float64) * h
+    n = (last[None, :] >= lam0[:, None]).sum(1)
+    return int(C * n.sum() * W), int(n.sum() * W)
+
+
+def run_continuum(args):
+    """Atomic continuum (bound-free + free-free of N and O, 100 levels each)
+    added to the coefficients of the 200-cell, 1e6-point stagnation line."""
+    import torch
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver, synth
+    p = synth.stagnation_line(n_atomic=200, n_molecular=300)
+    ctx = R.Context(0)
+    models = [synth.continuum_model(species=s, n_levels=args.cont_levels, seed=1007 + i)
+              for i, s in enumerate(("N", "O"))]
+    dp = solver.DeviceProblem(p, ctx)
+    R.populations(ctx, dp.species, dp.cells)
+    dc = R.DeviceContinuum(models, ctx.device)
+    C, K = dp.C, p.grid.n
+    out = {}
+    terms, table_entries = continuum_terms(models, p.grid, C)
+    for prec, dt, name in ((R.FP32, torch.float32, "fp32"), (R.FP64, torch.float64, "fp64")):
+        kap = torch.zeros((C, K), dtype=dt, device=ctx.device)
+        em = torch.zeros_like(kap)
+        run = lambda: R.continuum_coeffs(ctx, dc, dp.species.S, dp.cells, p.grid, 0, K, prec, kap, em)
+        for _ in range(max(3, args.warmup)):
+            run()
+        ctx.sync()
+        steps = max(1, args.steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in kev:
+            a.record(ctx.stream); b.record(ctx.stream)
+        ctx.sync()
+        with ClockSampler(0) as clk:
+            for i in range(steps):
+                ev[i][0].record(ctx.stream)
+                ctx.set_profile_events(*kev[i])
+                run()
+                ctx.set_profile_events(None, None)
+                ev[i][1].record(ctx.stream)
+            ctx.sync()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+        esz = 4 if prec == R.FP32 else 8
+        # algorithmic bytes of the level-sum kernel: kappa and j read and written once, the resampled tables read once
+        nbytes = C * K * 4 * esz + table_entries * esz
+        peaks = measured_peaks()
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        out[name] = {"ms_per_call": ms, "value": C * K / (ms * 1e-3), "kernel_ms": kms,
+                     "roofline": {"bound": "hbm", "achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": nbytes / (kms * 1e-3) / 1e9 / hbm,
+                                  "traffic": None, "kernel": f"k_continuum<{'float, 4, 4' if esz == 4 else 'double, 4, 2'}>",
+                                  "algorithmic_bytes": nbytes,
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+                     "clocks": clk.summary()}
+        del kap, em
+    print(json.dumps({"workload": f"atomic continuum (bound-free + free-free, N and O, {args.cont_levels} levels "
+                                  f"each) on the stagnation line, {C} cells x {K} points",
+                      "metric": "cell·λ points/s", "terms_per_call": terms, "warmup": args.warmup,
+                      "steps": max(1, args.steps), **out}))
+    return 0
+
+
 def run_fibonacci(args):
     """The paper's own angular path on the afterbody at 100 x 50 cells (2e5
     points in 65,536-point chunks): Fibonacci lines of sight from
@@ -430,6 +503,8 @@ def main():
         return run_fibonacci(args)
     if args.workload == "qss":
         return run_qss(args)
+    if args.workload == "continuum":
+        return run_continuum(args)
     import torch
     import torch.distributed as dist
 

@@ -217,8 +217,9 @@ RAPRAL_API int rapral_get_stats(rapral_ctx* ctx, rapral_stats* out);
 RAPRAL_API int rapral_reset_stats(rapral_ctx* ctx);
 
 /* Records the CUDA events `before` / `after` (cudaEvent_t, caller-owned) on
- * the context's stream immediately around every line-sum kernel launch, so a
- * caller can time that kernel alone.  NULL, NULL turns it off. */
+ * the context's stream immediately around every line-sum kernel launch and
+ * every continuum level-sum kernel launch, so a caller can time that kernel
+ * alone.  NULL, NULL turns it off. */
 RAPRAL_API int rapral_set_profile_events(rapral_ctx* ctx, void* before, void* after);
 
 /* Device bytes the context's workspace needs for a solve of this size
