@@ -53,6 +53,8 @@ def parse():
                     help="stagnation line (the bench line); afterbody / batch / fibonacci / qss / continuum: "
                          "one-off measurements")
     ap.add_argument("--cont-levels", type=int, default=100, help="continuum workload: levels per atom (N, O)")
+    ap.add_argument("--cont-points", type=int, default=1_000_000,
+                    help="continuum workload: grid points (fewer only for profiler captures)")
     ap.add_argument("--fib-points", type=int, default=8, help="fibonacci workload: surface points")
     ap.add_argument("--fib-los", type=int, default=128, help="fibonacci workload: Fibonacci directions per point")
     ap.add_argument("--ab-small", action="store_true",
@@ -382,7 +384,7 @@ def run_continuum(args):
     import torch
     from paper_2604_11856_gb300 import rapral as R
     from paper_2604_11856_gb300 import solver, synth
-    p = synth.stagnation_line(n_atomic=200, n_molecular=300)
+    p = synth.stagnation_line(n_cells=args.cells, n_atomic=200, n_molecular=300, n_grid=args.cont_points)
     ctx = R.Context(0)
     models = [synth.continuum_model(species=s, n_levels=args.cont_levels, seed=1007 + i)
               for i, s in enumerate(("N", "O"))]
