@@ -474,6 +474,19 @@ typedef struct {
 RAPRAL_API int rapral_qss_populations(rapral_ctx* ctx, const rapral_cr_model* model, const rapral_cells* cells,
                        double* n_out);
 
+/* Saha-Boltzmann populations of one atomic radiator (Sec. 2.1): overwrites
+ * lnpref[c][species] (device, row length n_species: the output of
+ * rapral_populations, normally the array cells->lnpref points to) with ln(N_+ N_e) + 1.5 ln(h^2 / (2 pi m_e k T_ve))
+ * + hc E_ionize / (k T_ve) - ln(2 Q_+), Q_+ = sum_k ion_g[k] e^{-hc ion_E[k] / kT_ve},
+ * so that every level of the species takes N_i = N_+ N_e (h^2/(2 pi m_e k T))^1.5
+ * g_i e^{hc (E_ionize - E_i)/kT} / (2 Q_+) in later coefficient calls.  N_+ is
+ * density column ion_col, N_e column ne_col; a cell without ions or electrons
+ * gets -inf (no population).  ion_E, ion_g: device arrays [n_ion_terms].
+ * Errors: EINVAL (sizes, columns, E_ionize <= 0). */
+RAPRAL_API int rapral_saha_populations(rapral_ctx* ctx, const rapral_cells* cells, int32_t species,
+                                       int32_t n_species, double E_ionize, int32_t ion_col, int32_t n_ion_terms,
+                                       const double* ion_E, const double* ion_g, double* lnpref);
+
 /* Departure coefficients b = N / N^B of the model's levels (Sec. 2.1: the
  * QSS populations replace the Boltzmann populations of the main path for the
  * levels they solve).  For radiator `species` of n_species, writes

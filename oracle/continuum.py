@@ -117,3 +117,21 @@ def continuum(models, cells, lnpref, grid, k0=0, nk=None, ne_col=10):
             kap[c] += k
             em[c] += j
     return kap, em
+
+
+def saha_lnpref(cells, s_col_ion, E_ion, ion_E, ion_g, ne_col=10):
+    """Saha-Boltzmann populations of an atomic radiator (Sec. 2.1),
+    N_i = N_+ N_e (h^2 / (2 pi m_e k T))^1.5 g_i e^{c2 (E_ion - E_i) / T} / (2 Q_+),
+    written as the prefactor of the Boltzmann form N_i = e^{lnpref} g_i
+    e^{-c2 E_i / T}: lnpref = ln(N_+ N_e) + 1.5 ln(h^2 / (2 pi m_e k T)) + c2
+    E_ion / T - ln(2 Q_+), per cell (T = T_ve); -inf without ions or electrons."""
+    out = np.empty(len(cells.Tve))
+    m = dict(ion_E=np.asarray(ion_E, float), ion_g=np.asarray(ion_g, float))
+    for c, T in enumerate(cells.Tve):
+        pe = cells.n[c, s_col_ion] * cells.n[c, ne_col]
+        if pe <= 0:
+            out[c] = -np.inf
+            continue
+        out[c] = (np.log(cells.n[c, s_col_ion]) + np.log(cells.n[c, ne_col])
+                  + 1.5 * np.log(H * H / (2.0 * np.pi * ME * KB * T)) + C2 * E_ion / T - np.log(2.0 * ion_Q(m, T)))
+    return out

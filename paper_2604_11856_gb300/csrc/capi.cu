@@ -492,6 +492,28 @@ int rapral_qss_populations(rapral_ctx* ctx, const rapral_cr_model* m, const rapr
     return cuda_status(ctx, e, "QSS populations");
 }
 
+int rapral_saha_populations(rapral_ctx* ctx, const rapral_cells* cells, int32_t species, int32_t n_species,
+                            double E_ionize, int32_t ion_col, int32_t n_ion_terms, const double* ion_E,
+                            const double* ion_g, double* lnpref) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (!cells || !ion_E || !ion_g || !lnpref) return set_error(ctx, RAPRAL_EINVAL, "null argument");
+    if (n_species < 1 || n_species > RAPRAL_MAX_SPECIES || species < 0 || species >= n_species)
+        return set_error(ctx, RAPRAL_EINVAL, "species %d of %d", species, n_species);
+    if (cells->n_cells < 0 || cells->n_cols < 1 || cells->ne_col < 0 || cells->ne_col >= cells->n_cols ||
+        ion_col < 0 || ion_col >= cells->n_cols)
+        return set_error(ctx, RAPRAL_EINVAL, "density columns");
+    if (!(E_ionize > 0.0) || !std::isfinite(E_ionize) || n_ion_terms < 1)
+        return set_error(ctx, RAPRAL_EINVAL, "ionisation energy or ion terms");
+    if (cells->n_cells == 0) return RAPRAL_OK;
+    if (!cells->Tve || !cells->n) return set_error(ctx, RAPRAL_EINVAL, "cells need Tve and n");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_validate_cells(ctx, cells);
+    if (e == cudaSuccess)
+        e = launch_saha_prefactor(ctx, cells, species, n_species, E_ionize, ion_col, n_ion_terms, ion_E, ion_g,
+                                  make_phys(ctx->codata), lnpref);
+    return cuda_status(ctx, e, "Saha-Boltzmann populations");
+}
+
 int rapral_qss_departures(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, int32_t species,
                           int32_t n_species, const double* n_qss, double* ln_b, int32_t n_lev) {
     if (!ctx) return RAPRAL_EINVAL;

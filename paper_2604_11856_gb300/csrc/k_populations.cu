@@ -175,3 +175,36 @@ cudaError_t launch_cell_prep(rapral_ctx* ctx, const rapral_cells* cells, const P
         ctx->d_status);
     return cudaGetLastError();
 }
+
+// Saha-Boltzmann populations of an atomic radiator (Sec. 2.1): N_i =
+// N_+ N_e (h^2 / (2 pi m_e k T))^1.5 g_i e^{hc (E_ion - E_i) / kT} / (2 Q_+),
+// that is the prefactor ln(N / Z) of the Boltzmann form replaced by
+// ln(N_+ N_e) + 1.5 ln(h^2 / (2 pi m_e k T)) + c2 E_ion / T - ln(2 Q_+), T = T_ve.
+// No ions or electrons: -inf (no population).
+__global__ void k_saha_prefactor(const double* __restrict__ Tve, const double* __restrict__ n, int ncol, int ne_col,
+                                 int64_t C, int s, int S, double E_ion, int ion_col, int n_terms,
+                                 const double* __restrict__ ion_E, const double* __restrict__ ion_g, Phys ph,
+                                 double* __restrict__ lnpref, const int* status) {
+    if (*status) return;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const double T = Tve[c];
+    double Qp = 0.0;
+    for (int k = 0; k < n_terms; ++k) Qp += ion_g[k] * exp(-ph.c2 * ion_E[k] / T);
+    const double pe = n[c * ncol + ion_col] * n[c * ncol + ne_col];
+    lnpref[c * S + s] = pe > 0.0 && Qp > 0.0
+                            ? log(n[c * ncol + ion_col]) + log(n[c * ncol + ne_col]) +
+                                  1.5 * log(ph.h * ph.h / (2.0 * M_PI * ph.me * ph.kB * T)) + ph.c2 * E_ion / T -
+                                  log(2.0 * Qp)
+                            : -INFINITY;
+}
+
+cudaError_t launch_saha_prefactor(rapral_ctx* ctx, const rapral_cells* cells, int s, int S, double E_ion,
+                                  int ion_col, int n_terms, const double* ion_E, const double* ion_g,
+                                  const Phys& ph, double* lnpref) {
+    if (cells->n_cells == 0) return cudaSuccess;
+    k_saha_prefactor<<<div_up(cells->n_cells, 256), 256, 0, ctx->stream>>>(
+        cells->Tve, cells->n, cells->n_cols, cells->ne_col, cells->n_cells, s, S, E_ion, ion_col, n_terms, ion_E,
+        ion_g, ph, lnpref, ctx->d_status);
+    return cudaGetLastError();
+}

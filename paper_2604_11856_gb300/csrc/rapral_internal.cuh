@@ -322,6 +322,10 @@ cudaError_t launch_axisym_fill(rapral_ctx* ctx, const double* xf, int32_t nx, co
 // last entry receives the total); single block.
 cudaError_t launch_scan_i64(rapral_ctx* ctx, int64_t* data, int64_t n);
 
+// Saha-Boltzmann prefactor of one atomic radiator into cells->lnpref (k_populations.cu).
+cudaError_t launch_saha_prefactor(rapral_ctx* ctx, const rapral_cells* cells, int s, int S, double E_ion,
+                                  int ion_col, int n_terms, const double* ion_E, const double* ion_g,
+                                  const Phys& ph, double* lnpref);
 // QSS collisional-radiative populations (k_qss.cu).
 cudaError_t launch_qss(rapral_ctx* ctx, const rapral_cr_model* m, const rapral_cells* cells, double* n_out,
                        const Phys& ph);

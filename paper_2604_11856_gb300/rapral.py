@@ -148,6 +148,7 @@ def load(build_if_missing=True):
             "rapral_set_broadening": (i, [vp, i32, i32, vp, i32, vp]),
             "rapral_qss_populations": (i, [vp, P(CrModel), P(Cells), vp]),
             "rapral_continuum_coeffs": (i, [vp, vp, i32, i32, P(Cells), P(Grid), i64, i64, i, vp, vp, i64]),
+            "rapral_saha_populations": (i, [vp, P(Cells), i32, i32, d, i32, i32, vp, vp, vp]),
             "rapral_qss_departures": (i, [vp, P(CrModel), P(Cells), i32, i32, vp, vp, i32]),
             "rapral_set_departures": (i, [vp, i32, vp, i64, i32, vp, vp, i64]),
         }
@@ -514,6 +515,14 @@ def qss_populations(ctx, dmodel, dcells, out):
     """QSS level populations [C, l] (rapral_qss_populations) into `out`."""
     ctx.check(ctx.lib.rapral_qss_populations(ctx.h, ct.byref(dmodel.struct), ct.byref(dcells.struct), _ptr(out)))
     return out
+
+
+def saha_populations(ctx, dcells, species, n_species, E_ionize, ion_col, ion_E, ion_g):
+    """Saha-Boltzmann prefactor of radiator `species` into dcells.lnpref
+    (rapral_saha_populations); ion_E, ion_g: device float64 tensors."""
+    ctx.check(ctx.lib.rapral_saha_populations(ctx.h, ct.byref(dcells.struct), int(species), int(n_species),
+                                              float(E_ionize), int(ion_col), int(ion_E.numel()), _ptr(ion_E),
+                                              _ptr(ion_g), _ptr(dcells.lnpref)))
 
 
 def qss_departures(ctx, dmodel, dcells, species, n_qss, ln_b):

@@ -115,3 +115,40 @@ def test_continuum_checks(ctx):
     with pytest.raises(R.RapralError):
         _gpu(ctx, p, [bad], R.FP64)
     ctx.sync()
+
+
+@pytest.mark.parametrize("precision", [R.FP64, R.FP32])
+def test_saha_boltzmann_populations(ctx, precision):
+    """rapral_saha_populations replaces the N and O prefactors; the line sum
+    and the continuum then follow the oracle fed the same prefactors."""
+    p = _problem(n_cells=12, n_grid=30001)
+    p.cells.n[0, synth.FLOW_SPECIES.index("N+")] = 0.0          # no ions: no N population in cell 0
+    ms = _models(40)
+    dp = solver.DeviceProblem(p, ctx)
+    R.populations(ctx, dp.species, dp.cells)
+    lnp = oracle.lnpref(p)
+    for m in ms:
+        ie = torch.tensor(m["ion_E"], dtype=torch.float64, device=ctx.device)
+        ig = torch.tensor(m["ion_g"], dtype=torch.float64, device=ctx.device)
+        R.saha_populations(ctx, dp.cells, m["species"], dp.species.S, m["E_ion"], m["ion_col"], ie, ig)
+        lnp[:, m["species"]] = ct.saha_lnpref(p.cells, m["ion_col"], m["E_ion"], m["ion_E"], m["ion_g"])
+    got = dp.cells.lnpref.cpu().numpy()
+    fin = np.isfinite(lnp)
+    assert np.array_equal(np.isfinite(got), fin)
+    assert np.max(np.abs(got[fin] - lnp[fin])) <= 1e-12 * np.max(np.abs(lnp[fin]))
+    dt = torch.float64 if precision == R.FP64 else torch.float32
+    kap = torch.zeros((dp.C, p.grid.n), dtype=dt, device=ctx.device)
+    em = torch.zeros_like(kap)
+    R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, 0, p.grid.n, precision, kap, em)
+    R.continuum_coeffs(ctx, R.DeviceContinuum(ms, ctx.device), dp.species.S, dp.cells, p.grid, 0, p.grid.n,
+                       precision, kap, em)
+    ctx.sync()
+    lk, lj = oracle.spectral_coeffs(p, lnp=lnp)
+    ck, cj = ct.continuum(ms, p.cells, lnp, p.grid)
+    rk, rj = lk + ck, lj + cj
+    k, j = kap.double().cpu().numpy(), em.double().cpu().numpy()
+    if precision == R.FP64:
+        assert _rel(k, rk) <= 1e-10 and _rel(j, rj) <= 1e-10
+    else:
+        big = rj >= 1e-6 * rj.max(axis=1, keepdims=True)
+        assert np.max((np.abs(j - rj) / np.maximum(rj, 1e-300))[big]) <= 1e-3

@@ -144,3 +144,19 @@ def test_planck_equals_the_wall_planck_and_integrates_to_sigma_T4():
         tot = np.trapezoid(B, lam * 1e-3)
         sig = 2 * np.pi ** 5 * (1.380e-23) ** 4 / (15 * (6.626e-34) ** 3 * (2.998e8) ** 2) * 1e-4   # W/cm^2/K^4
         assert abs(tot / (sig * T ** 4 / np.pi) - 1) < 2e-3
+
+
+@pytest.mark.parametrize("T,species", [(7000.0, "N"), (12000.0, "O")])
+def test_saha_boltzmann_equals_boltzmann_at_saha_equilibrium(T, species):
+    """With the ions at the textbook Saha equilibrium of the atom, the
+    Saha-Boltzmann prefactor is the Boltzmann one, ln(N_a / Q_a)."""
+    p, m, s = _lte_problem(T, species)
+    lnp = oracle.lnpref(p)
+    sb = ct.saha_lnpref(p.cells, m["ion_col"], m["E_ion"], m["ion_E"], m["ion_g"])
+    assert np.max(np.abs(sb - lnp[:, s])) < 1e-11
+    # twice the ions: twice the populations
+    p.cells.n[:, m["ion_col"]] *= 2.0
+    sb2 = ct.saha_lnpref(p.cells, m["ion_col"], m["E_ion"], m["ion_E"], m["ion_g"])
+    assert np.allclose(sb2 - sb, np.log(2.0), atol=1e-13)
+    p.cells.n[0, m["ion_col"]] = 0.0
+    assert ct.saha_lnpref(p.cells, m["ion_col"], m["E_ion"], m["ion_E"], m["ion_g"])[0] == -np.inf
