@@ -73,6 +73,26 @@ LINE_SUM_TRAFFIC = {"sha1": "6ee8d3a0fab7f72540a80786e40edaa61ac4f18c", "cells":
                     "bytes": 55_519_488 + 1_548_487_424}
 
 
+# DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
+# 1e6 points, N and O with 100 levels each), from a one-pass ncu capture of the
+# kernel source with this SHA-1; a different source gives null.
+CONT_TRAFFIC = {"sha1": "56be3b7521f4cb1544556840cb4c7daba6b4cf02", "cells": 200, "grid_points": 1_000_000, "levels": 100,
+                "bytes": 1_782_893_056 + 1_539_134_464}
+
+
+def continuum_traffic(cells, grid_points, levels):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_11856_gb300", "csrc", "k_continuum.cu")
+    try:
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    t = CONT_TRAFFIC
+    if digest != t["sha1"] or (cells, grid_points, levels) != (t["cells"], t["grid_points"], t["levels"]):
+        return None
+    return t["bytes"]
+
+
 def line_sum_traffic(cells, grid_points):
     import hashlib
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_11856_gb300", "csrc", "k_lines.cu")
@@ -425,7 +445,8 @@ def run_continuum(args):
         out[name] = {"ms_per_call": ms, "value": C * K / (ms * 1e-3), "kernel_ms": kms,
                      "roofline": {"bound": "hbm", "achieved": nbytes / (kms * 1e-3) / 1e9, "peak": hbm,
                                   "unit": "GB/s", "frac": nbytes / (kms * 1e-3) / 1e9 / hbm,
-                                  "traffic": None, "kernel": f"k_continuum<{'float, 4, 4' if esz == 4 else 'double, 4, 2'}>",
+                                  "traffic": continuum_traffic(C, K, args.cont_levels) if esz == 4 else None,
+                                  "kernel": f"k_continuum<{'float, 4, 4' if esz == 4 else 'double, 4, 2'}>",
                                   "algorithmic_bytes": nbytes,
                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
                      "clocks": clk.summary()}
