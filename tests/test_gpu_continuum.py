@@ -152,3 +152,30 @@ def test_saha_boltzmann_populations(ctx, precision):
     else:
         big = rj >= 1e-6 * rj.max(axis=1, keepdims=True)
         assert np.max((np.abs(j - rj) / np.maximum(rj, 1e-300))[big]) <= 1e-3
+
+
+def test_continuum_edge_cases(ctx):
+    """One grid point; a range below every edge; a table wholly outside the
+    range; no cells."""
+    p = _problem(n_cells=5, n_grid=20001)
+    ms = _models(30)
+    lnp = oracle.lnpref(p)
+    for k0, nk in ((0, 1), (20000, 1), (7777, 129), (19900, 101)):
+        kap, em = _gpu(ctx, p, ms, R.FP64, k0, nk)
+        rk, re = ct.continuum(ms, p.cells, lnp, p.grid, k0, nk)
+        assert _rel(kap, rk) <= 1e-10 and _rel(em, re) <= 1e-10, (k0, nk)
+    far = dict(ms[0], node_lam=ms[0]["node_lam"] * 1e-3)        # tables at 0.01 .. 10 nm: no bound-free
+    kap, em = _gpu(ctx, p, [far], R.FP32)
+    rk, re = ct.continuum([far], p.cells, lnp, p.grid)
+    big = re >= 1e-6 * re.max(axis=1, keepdims=True)
+    assert np.max((np.abs(em - re) / np.maximum(re, 1e-300))[big]) <= 1e-3
+    dp = solver.DeviceProblem(p, ctx)
+    empty = R.Cells()
+    empty.n_cells, empty.n_cols, empty.ne_col = 0, dp.cells.struct.n_cols, dp.cells.struct.ne_col
+    kap = torch.zeros((1, 8), dtype=torch.float64, device=ctx.device)
+    dc = R.DeviceContinuum(ms, ctx.device)
+    g = R.grid_struct(p.grid)
+    ctx.check(ctx.lib.rapral_continuum_coeffs(ctx.h, R.ct.byref(dc.structs), dc.n, dp.species.S, R.ct.byref(empty),
+                                              R.ct.byref(g), 0, 8, R.FP64, R._ptr(kap), R._ptr(kap), 8))
+    ctx.sync()
+    assert float(kap.abs().sum()) == 0.0
