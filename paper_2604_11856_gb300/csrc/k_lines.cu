@@ -683,9 +683,10 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
         // the low part; relative to u itself, so the Gaussian core keeps FP32
         // accuracy however far the tile start lies from the line centre
         const float br = whiting_bracket<FAR>(fabsf(fmaf(k, s, ub) + ub_lo), r, omr, c16);
-        const bool in = k >= lo && k <= hi;
-        bj[i] = fmaf(in ? aj : 0.0f, br, bj[i]);
-        bk[i] = fmaf(in ? ak : 0.0f, br, bk[i]);
+        if (k >= lo && k <= hi) {   // predicated update: lanes outside the window part add nothing
+            bj[i] = fmaf(aj, br, bj[i]);
+            bk[i] = fmaf(ak, br, bk[i]);
+        }
     }
 }
 
