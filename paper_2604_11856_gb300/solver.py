@@ -53,13 +53,15 @@ def shard_range(n, rank, world, align=512):
 
 
 def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensity=False, ctx2=None,
-          buffers=None, k_start=0, k_stop=None):
+          buffers=None, k_start=0, k_stop=None, continuum=None):
     """Runs the whole path on device-resident inputs over the grid points
     [k_start, k_stop) (default: all).  Returns a dict with q [P] (FP64,
     device; the range's part of the flux with the whole grid's trapezoid
     weights) and, on request, kappa / emis [C, nk] and q_lambda [P, nk] /
     I [n_dirs, nk] (single chunk only).  With ctx2 (a second context on
-    another stream) chunk k+1's line sum overlaps chunk k's march."""
+    another stream) chunk k+1's line sum overlaps chunk k's march.  With
+    continuum (an R.DeviceContinuum) the atomic bound-free and free-free
+    continuum is added to every chunk's coefficients before the march."""
     k_stop = dp.grid.n if k_stop is None else k_stop
     n_range = k_stop - k_start
     chunk = n_range if not chunk else min(chunk, n_range)
@@ -83,6 +85,8 @@ def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensi
             nk = min(chunk, k_stop - k0)
             kap, em = buffers[0]
             R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
+            if continuum is not None:
+                R.continuum_coeffs(ctx, continuum, dp.species.S, dp.cells, dp.grid, k0, nk, precision, kap, em)
             R.trace_rays(ctx, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)
             R.wall_flux(ctx, qlam, precision, dp.grid, k0, nk, P, q)
     else:
@@ -100,6 +104,8 @@ def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensi
             if used[i % nbuf]:
                 sa.wait_event(free[i % nbuf])
             R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
+            if continuum is not None:
+                R.continuum_coeffs(ctx, continuum, dp.species.S, dp.cells, dp.grid, k0, nk, precision, kap, em)
             ready[i].record(sa)
             sb.wait_event(ready[i])
             R.trace_rays(ctx2, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)

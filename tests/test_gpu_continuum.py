@@ -179,3 +179,22 @@ def test_continuum_edge_cases(ctx):
                                               R.ct.byref(g), 0, 8, R.FP64, R._ptr(kap), R._ptr(kap), 8))
     ctx.sync()
     assert float(kap.abs().sum()) == 0.0
+
+
+@pytest.mark.parametrize("precision,chunk", [(R.FP64, None), (R.FP64, 7001), (R.FP32, None)])
+def test_solve_with_continuum(ctx, precision, chunk):
+    """The whole slab solve with the continuum added to every chunk's
+    coefficients: q against the oracle's march of lines + continuum."""
+    p = _problem(n_cells=10, n_grid=20001)
+    ms = _models(40)
+    dp = solver.DeviceProblem(p, ctx)
+    out = solver.solve(dp, ctx, precision, chunk=chunk, continuum=R.DeviceContinuum(ms, ctx.device))
+    ctx.sync()
+    q = float(out["q"].cpu().numpy()[0])
+    lk, lj = oracle.spectral_coeffs(p)
+    ck, cj = ct.continuum(ms, p.cells, oracle.lnpref(p), p.grid)
+    ref = oracle.solve_slab(p, coeffs=(lk + ck, lj + cj))["q"]
+    ref_lines = oracle.solve_slab(p, coeffs=(lk, lj))["q"]
+    print(f"  q {q:.6e} oracle {ref:.6e} (lines only {ref_lines:.6e})")
+    assert abs(q / ref - 1) <= (1e-10 if precision == R.FP64 else 1e-4)
+    assert abs(ref / ref_lines - 1) > 1e-6      # the continuum does change q
