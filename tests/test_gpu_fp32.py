@@ -116,3 +116,38 @@ def test_afterbody_small_fp32(ctx, rays):
     rel = np.abs(out["q"].cpu().numpy() / q - 1)
     print(f"  q rel err per point {rel}")
     assert rel.max() <= TOL_Q
+
+
+def test_stagnation_full_size_sampled_fp32():
+    """The benchmark's configuration (200 cells, 320k lines, 1e6 points,
+    autotuned tiling): FP32 kappa and j at 300 sampled (cell, point) pairs
+    against the oracle computed point by point, where the value is >= 1e-6
+    of its row's maximum; q against the FP64 plain solve."""
+    from paper_2604_11856_gb300 import autotune
+    c = R.Context(0)
+    p = synth.stagnation_line()
+    autotune.tune(c, p)
+    dp = solver.DeviceProblem(p, c)
+    out = solver.solve(dp, c, R.FP32, keep_coeffs=True)
+    c.sync()
+    kap, em = out["kappa"], out["emis"]
+    jmax = em.abs().amax(dim=1).double().cpu().numpy()
+    kmax = kap.abs().amax(dim=1).double().cpu().numpy()
+    rng = np.random.default_rng(12)
+    cells = rng.integers(0, 200, 300); ks = rng.integers(0, p.grid.n, 300)
+    lnp = oracle.lnpref(p)
+    rk, re, ra = oracle.coeffs_at(p, cells, ks, lnp)
+    ci = torch.as_tensor(cells, device=c.device); ki = torch.as_tensor(ks, device=c.device)
+    gk = kap[ci, ki].double().cpu().numpy(); gj = em[ci, ki].double().cpu().numpy()
+    mj = re >= MASK * jmax[cells]
+    mk = np.maximum(np.abs(rk), ra) >= MASK * kmax[cells]
+    ej = np.max(np.abs(gj - re)[mj] / re[mj])
+    ek = np.max(np.abs(gk - rk)[mk] / np.maximum(np.abs(rk), ra)[mk])
+    print(f"  j: {ej:.3e} over {mj.sum()} points, kappa: {ek:.3e} over {mk.sum()} points")
+    assert mj.sum() > 50 and ej <= TOL_POINT and ek <= TOL_POINT
+    q32 = float(out["q"].item())
+    q64 = float(solver.solve(dp, c, R.FP64)["q"].item())
+    c.sync()
+    print(f"  q fp32 {q32:.8e} fp64 {q64:.8e}")
+    assert abs(q32 / q64 - 1) <= 1e-4
+    c.close()
