@@ -430,6 +430,21 @@ RAPRAL_API int rapral_axisym_rays(rapral_ctx* ctx, const double* xf, int32_t nx,
 RAPRAL_API int rapral_set_broadening(rapral_ctx* ctx, int32_t flags, int32_t n_species, const double* E_ionize,
                        int32_t n_cols, const double* column_mass);
 
+/* ---------------------------------------------------------- line shape -- */
+
+#define RAPRAL_PROFILE_WHITING 0   /* Whiting's pseudo-Voigt (Sec. 2.2.1), the default */
+#define RAPRAL_PROFILE_VOIGT 1     /* the exact Voigt shape                            */
+
+/* Line shape of later rapral_spectral_coeffs calls of this context
+ * (Sec. 2.2.1).  RAPRAL_PROFILE_VOIGT: phi = 1e3 Re w(z) / (sigma sqrt(2 pi))
+ * um^-1, z = (lam - lam0 + i lamL) / (sigma sqrt 2), sigma = lamG /
+ * sqrt(2 ln 2), w the Faddeeva function (to ~5e-13 relative in FP64, ~1e-5
+ * in FP32); the line windows (100 Olivero HWHMs) do not change.  The exact
+ * shape uses 512-point tiles in FP64 and 128-point tiles in FP32 whatever
+ * rapral_set_tiling chose.  The batch and allocation-free paths use
+ * Whiting's shape.  Errors: EINVAL (unknown profile). */
+RAPRAL_API int rapral_set_profile(rapral_ctx* ctx, int32_t profile);
+
 /* ------------------------------------- QSS collisional-radiative populations -- */
 
 /* Level model of one atomic radiator for the quasi-steady-state populations

@@ -266,7 +266,9 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
         if (e == cudaSuccess) e = cudaMemset2DAsync(emis, ld * esz, 0, nk * esz, C, ctx->stream);
         return cuda_status(ctx, e, "zero coefficients");
     }
-    const int W = ctx->tile_w ? ctx->tile_w : (precision == RAPRAL_FP64 ? 512 : 128);
+    // the exact Voigt shape runs in one tiling per precision
+    const int W = (ctx->tile_w && ctx->profile == RAPRAL_PROFILE_WHITING) ? ctx->tile_w
+                                                                          : (precision == RAPRAL_FP64 ? 512 : 128);
     if (W != 128 && W != 256 && W != 512)
         return set_error(ctx, RAPRAL_EINVAL, "line sum supports tile widths 128, 256, 512 (got %d)", W);
     const int64_t T = (nk + W - 1) / W;
@@ -349,6 +351,10 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     a.lb = lb; a.lb32 = lb32; a.cb = cb; a.cb32 = cb32;
     if (ctx->dep_lnb) {
         a.dep_lnb = ctx->dep_lnb; a.dep_u = ctx->dep_u; a.dep_l = ctx->dep_l; a.dep_nlev = ctx->dep_nlev;
+    }
+    if (ctx->profile == RAPRAL_PROFILE_VOIGT) {
+        a.voigt = 1;
+        a.vc = voigt_coefficients();
     }
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");
@@ -544,6 +550,14 @@ int rapral_set_departures(rapral_ctx* ctx, int32_t n_lev, const double* ln_b, in
         return set_error(ctx, RAPRAL_EINVAL, "departure table sizes");
     ctx->dep_lnb = ln_b; ctx->dep_u = lev_u; ctx->dep_l = lev_l;
     ctx->dep_nlev = n_lev; ctx->dep_S = n_species; ctx->dep_C = n_cells; ctx->dep_L = n_lines;
+    return RAPRAL_OK;
+}
+
+int rapral_set_profile(rapral_ctx* ctx, int32_t profile) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (profile != RAPRAL_PROFILE_WHITING && profile != RAPRAL_PROFILE_VOIGT)
+        return set_error(ctx, RAPRAL_EINVAL, "line shape %d", profile);
+    ctx->profile = profile;
     return RAPRAL_OK;
 }
 

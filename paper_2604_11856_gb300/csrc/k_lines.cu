@@ -297,7 +297,7 @@ __device__ __forceinline__ double lorentz64(const LineSumArgs& a, const LinePrep
     return lamL;
 }
 
-template <int PPT>
+template <int PPT, bool VG = false>
 __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
     if (*a.status) return;
     const int W = 128 * PPT;
@@ -335,11 +335,16 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 const double lamG = L.cD * cp.sqrtT;
                 const double lamL = lorentz64(a, L, cp, l, c);
                 const double lamV = voigt_hwhm(lamL, lamG);
-                const double r = lamL / lamV;
-                const double pre = 1e3 / (2.0 * lamV * (1.065 + 0.447 * r + 0.058 * r * r));
+                double r = lamL / lamV;
+                double pre = 1e3 / (2.0 * lamV * (1.065 + 0.447 * r + 0.058 * r * r));
                 P.lam0 = L.lam0;
                 P.w100 = RAPRAL_WINDOW * lamV;
                 P.inv2V = 0.5 / lamV;
+                if (VG) {   // exact Voigt: x = dlam / (sigma sqrt 2) = dlam sqrt(ln 2) / lamG, y = lamL sqrt(ln 2) / lamG
+                    P.inv2V = 0.83255461115769775635 / lamG;
+                    r = lamL * P.inv2V;
+                    pre = 1e3 * 0.46971863934982566689 / lamG;   // 1e3 / (sigma sqrt(2 pi))
+                }
                 P.r = r;
                 P.omr = 1.0 - r;
                 P.c16 = 0.016 * r * (1.0 - r);
@@ -377,6 +382,12 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 const double lk = __dadd_rn(a.lam_min, __dmul_rn((double)k, a.h));
                 const double dl = fabs(lk - P.lam0);
                 if (!(dl <= P.w100)) continue;
+                if (VG) {
+                    const double br = voigt_re<double>(a.vc, dl * P.inv2V, P.r);
+                    accj[i] += P.aj * br;
+                    acck[i] += P.ak * br;
+                    continue;
+                }
                 const double u = dl * P.inv2V;
                 const double u2 = u * u;
                 const double ga = 2.772 * u2;
@@ -531,7 +542,7 @@ template <int FL>
 __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF32& L, const CellPrep& cp, float2 lp,
                                                float2 cb, int line, int64_t c, float hf, float inv_hf, int kt0,
                                                float kt0f, float kt1f, bool count, PairF32* P, int64_t* cnt) {
-    constexpr bool BR = (FL & 1) != 0, DEP = (FL & 2) != 0;
+    constexpr bool BR = (FL & 1) != 0, DEP = (FL & 2) != 0, VG = (FL & 4) != 0;
     if (!(lp.x > -INFINITY)) return false;
     // widths first: most candidates of a tile list miss the tile in a given cell
     const float lamG = L.cD * cp.sqrtT_f;
@@ -600,9 +611,15 @@ __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF
     const float Sk = exp_ff(yk) * fk;
     if (!(Sj > 0.0f) && Sk == 0.0f) return false;
     const float iv = rcp_approx(lamV);
-    const float r = lamL * iv;
-    const float pre = 1e3f * 0.5f * iv * rcp_approx(1.065f + 0.447f * r + 0.058f * r * r);
-    const float s = 0.5f * hf * iv;
+    float r = lamL * iv;
+    float pre = 1e3f * 0.5f * iv * rcp_approx(1.065f + 0.447f * r + 0.058f * r * r);
+    float s = 0.5f * hf * iv;
+    if (VG) {   // exact Voigt: u is x = dlam sqrt(ln 2) / lamG, r is y, pre 1e3 / (sigma sqrt(2 pi))
+        const float ig = rcp_approx(lamG);
+        r = 0.83255461f * lamL * ig;
+        pre = 1e3f * 0.46971864f * ig;
+        s = 0.83255461f * hf * ig;
+    }
     const float u0 = L.delta * s;                    // u of the centre's offset from kc
     {   // signed u at kt0 without rounding loss: (kt0 - kc) is exact, its
         // product with s and the sum with -u0 are split into hi + lo
@@ -690,6 +707,24 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
     }
 }
 
+// The same sweep with the exact Voigt shape: r is y, u is x.
+template <int PPT>
+__device__ __forceinline__ void sweep_pair_voigt(const VoigtCoef& vc, float lo, float hi, float lanef, float s, float ub,
+                                                 float ub_lo, float y, float aj, float ak, float (&bj)[PPT],
+                                                 float (&bk)[PPT]) {
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const float p0 = 32.0f * i;
+        if (p0 + 31.0f < lo || p0 > hi) continue;
+        const float k = lanef + p0;
+        const float br = voigt_re<float>(vc, fmaf(k, s, ub) + ub_lo, y);
+        if (k >= lo && k <= hi) {
+            bj[i] = fmaf(aj, br, bj[i]);
+            bk[i] = fmaf(ak, br, bk[i]);
+        }
+    }
+}
+
 // Warp-level line sum: a warp owns one cell and the TW = 32 PPT points of
 // tile t, lane l the points l, l + 32, ..., l + 32 (PPT - 1); it stages 32
 // (line, cell) pairs at a time in its own shared-memory slice (one per lane),
@@ -753,7 +788,8 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
             const float s = fabsf(A.w), r = B.x, aj = B.z, ak = B.w;
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
             const float ub = A.z, ub_lo = B.y;
-            if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            if (FL & 4) sweep_pair_voigt<PPT>(a.vc, lo, hi, lanef, s, ub, ub_lo, r, aj, ak, bj, bk);
+            else if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
             else sweep_pair<PPT, false>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
         }
 #pragma unroll
@@ -914,6 +950,11 @@ cudaError_t launch_line_sum(rapral_ctx* ctx, const LineSumArgs& a, int precision
 
 static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, int precision, dim3 grid) {
     if (precision == RAPRAL_FP64) {
+        if (a.voigt) {   // one tiling with the exact line shape
+            if (a.tile_w != 512) return cudaErrorInvalidValue;
+            k_line_sum_f64<4, true><<<grid, 128, 0, ctx->stream>>>(a);
+            return cudaGetLastError();
+        }
         switch (a.tile_w) {
             case 128: k_line_sum_f64<1><<<grid, 128, 0, ctx->stream>>>(a); break;
             case 256: k_line_sum_f64<2><<<grid, 128, 0, ctx->stream>>>(a); break;
@@ -924,7 +965,18 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
     }
     // FP32: warp-level kernel, WPB cells per block; with the optional
     // resonance / van der Waals terms four cells a block
-    const int fl = (a.lb32 ? 1 : 0) | (a.dep_lnb ? 2 : 0);
+    const int fl = (a.lb32 ? 1 : 0) | (a.dep_lnb ? 2 : 0) | (a.voigt ? 4 : 0);
+    if (fl & 4) {   // exact Voigt shape: one tiling, 128 x 4
+        if (a.tile_w != 128) return cudaErrorInvalidValue;
+        dim3 gb(div_up(a.C, 4), grid.y);
+        switch (fl) {
+            case 4: k_line_sum_f32<4, 4, 4><<<gb, 128, 0, ctx->stream>>>(a); break;
+            case 5: k_line_sum_f32<4, 4, 5><<<gb, 128, 0, ctx->stream>>>(a); break;
+            case 6: k_line_sum_f32<4, 4, 6><<<gb, 128, 0, ctx->stream>>>(a); break;
+            default: k_line_sum_f32<4, 4, 7><<<gb, 128, 0, ctx->stream>>>(a); break;
+        }
+        return cudaGetLastError();
+    }
     if (fl) {
         dim3 gb(div_up(a.C, 4), grid.y);
 #define RAPRAL_LSF(FL)                                                                   \
@@ -987,4 +1039,35 @@ cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const Ba
     if (tile_w == 256 && wpb == 8) return batch_launch<8, 8>(ctx, items, n, total, counter, blocks_out, launch);
     if (tile_w == 512) return batch_launch<16, 4>(ctx, items, n, total, counter, blocks_out, launch);
     return cudaErrorInvalidValue;
+}
+
+// Fourier coefficients a_1 .. a_N of f(t) = L^2 sec^2(t/2) e^{-L^2 tan^2(t/2)},
+// L = (N / sqrt 2)^{1/2}, by the trapezoid rule on 4N points of [-pi, pi)
+// (f vanishes at -pi): the coefficients of Weideman's rational expansion.
+static void weideman(int N, double* a, double* L) {
+    const int M = 2 * N, M2 = 2 * M;
+    const double l = std::sqrt(N / std::sqrt(2.0));
+    *L = l;
+    for (int n = 1; n <= N; ++n) {
+        double acc = 0.0;
+        for (int j = -M + 1; j <= M - 1; ++j) {
+            const double th = j * M_PI / M;
+            const double t = l * std::tan(0.5 * th);
+            acc += std::exp(-t * t) * (l * l + t * t) * std::cos(n * th);
+        }
+        a[n - 1] = acc / M2;
+    }
+}
+
+const VoigtCoef& voigt_coefficients() {
+    static const VoigtCoef vc = [] {
+        VoigtCoef v{};
+        weideman(RAPRAL_VOIGT_NW64, v.a64, &v.L64);
+        double a32[RAPRAL_VOIGT_NW32], L32;
+        weideman(RAPRAL_VOIGT_NW32, a32, &L32);
+        for (int n = 0; n < RAPRAL_VOIGT_NW32; ++n) v.a32[n] = (float)a32[n];
+        v.L32 = (float)L32;
+        return v;
+    }();
+    return vc;
 }

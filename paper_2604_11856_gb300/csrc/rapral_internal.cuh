@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "rapral.h"
+#include "voigt.cuh"
 
 // ------------------------------------------------------------- constants ----
 
@@ -155,6 +156,7 @@ struct rapral_ctx {
     const int32_t* dep_l = nullptr;
     int32_t dep_nlev = 0, dep_S = 0;
     int64_t dep_C = 0, dep_L = 0;
+    int profile = 0;   // RAPRAL_PROFILE_WHITING or RAPRAL_PROFILE_VOIGT
     char err[512] = {0};
 };
 
@@ -263,6 +265,9 @@ struct LineSumArgs {
     const int32_t* dep_u = nullptr;
     const int32_t* dep_l = nullptr;
     int32_t dep_nlev = 0;
+    // exact Voigt line shape instead of Whiting's (rapral_set_profile)
+    int voigt = 0;
+    VoigtCoef vc{};
 };
 
 // Workspace of the optional resonance / van der Waals terms of one request:
@@ -351,3 +356,6 @@ cudaError_t launch_fib_flux(rapral_ctx* ctx, int64_t P, const int64_t* point_off
                             int32_t n_los, const double* S, int32_t n_phi, int32_t n_theta, double* q,
                             void* scratch);
 cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n);
+
+// Coefficients of the rational Faddeeva expansion (computed once on the host).
+const VoigtCoef& voigt_coefficients();

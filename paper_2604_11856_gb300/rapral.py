@@ -27,6 +27,7 @@ _lock = threading.Lock()
 
 
 BROAD_STARK_IONIZE, BROAD_RESONANCE, BROAD_VDW = 1, 2, 4   # rapral_set_broadening flags
+PROFILE_WHITING, PROFILE_VOIGT = 0, 1                     # rapral_set_profile
 
 
 class RapralError(RuntimeError):
@@ -146,6 +147,7 @@ def load(build_if_missing=True):
             "rapral_los_node_states": (i, [vp, vp, i32, vp, i32, P(Cells), i64, vp, vp, vp, vp, vp]),
             "rapral_fibonacci_flux": (i, [vp, i64, vp, vp, i32, vp, i32, i32, vp]),
             "rapral_set_broadening": (i, [vp, i32, i32, vp, i32, vp]),
+            "rapral_set_profile": (i, [vp, i32]),
             "rapral_qss_populations": (i, [vp, P(CrModel), P(Cells), vp]),
             "rapral_continuum_coeffs": (i, [vp, vp, i32, i32, P(Cells), P(Grid), i64, i64, i, vp, vp, i64]),
             "rapral_saha_populations": (i, [vp, P(Cells), i32, i32, d, i32, i32, vp, vp, vp]),
@@ -206,6 +208,10 @@ class Context:
         b, u, lo = self._dep
         self.check(self.lib.rapral_set_departures(self.h, int(n), _ptr(b), int(C), int(S), _ptr(u), _ptr(lo),
                                                   int(u.shape[0])))
+
+    def set_profile(self, profile):
+        """Line shape of later coefficient calls: PROFILE_WHITING (default) or PROFILE_VOIGT."""
+        self.check(self.lib.rapral_set_profile(self.h, int(profile)))
 
     def set_stream(self, stream):
         self.stream = stream
