@@ -48,10 +48,10 @@ def parse():
     ap.add_argument("--serve-fp64-requests", type=int, default=4)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
-    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci", "qss", "continuum"],
+    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci", "qss", "continuum", "voigt"],
                     default="stagnation",
-                    help="stagnation line (the bench line); afterbody / batch / fibonacci / qss / continuum: "
-                         "one-off measurements")
+                    help="stagnation line (the bench line); afterbody / batch / fibonacci / qss / continuum / "
+                         "voigt (the stagnation step with the exact Voigt shape): one-off measurements")
     ap.add_argument("--cont-levels", type=int, default=100, help="continuum workload: levels per atom (N, O)")
     ap.add_argument("--cont-points", type=int, default=1_000_000,
                     help="continuum workload: grid points (fewer only for profiler captures)")
@@ -458,6 +458,49 @@ def run_continuum(args):
     return 0
 
 
+def run_voigt(args):
+    """The stagnation-line step (200 cells, 320k lines, 1e6 points) with the
+    exact Voigt line shape instead of Whiting's: FP32 step and line-sum
+    times, and one FP64 step."""
+    import torch
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver, synth
+    p = synth.stagnation_line(n_cells=args.cells)
+    ctx = R.Context(0)
+    ctx.set_profile(R.PROFILE_VOIGT)
+    dp = solver.DeviceProblem(p, ctx)
+    C, K = dp.C, p.grid.n
+    out = {}
+    for prec, dt, name, steps in ((R.FP32, torch.float32, "fp32", max(1, args.steps)), (R.FP64, torch.float64, "fp64", 1)):
+        bufs = [(torch.empty((C, K), dtype=dt, device=ctx.device), torch.empty((C, K), dtype=dt, device=ctx.device))]
+        for _ in range(max(3, args.warmup) if prec == R.FP32 else 1):
+            solver.solve(dp, ctx, prec, buffers=bufs)
+        ctx.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in kev:
+            a.record(ctx.stream); b.record(ctx.stream)
+        ctx.sync()
+        with ClockSampler(0) as clk:
+            for i in range(steps):
+                ev[i][0].record(ctx.stream)
+                ctx.set_profile_events(*kev[i])
+                r = solver.solve(dp, ctx, prec, buffers=bufs)
+                ctx.set_profile_events(None, None)
+                ev[i][1].record(ctx.stream)
+            ctx.sync()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+        out[name] = {"ms_per_step": ms, "value": C * K / (ms * 1e-3), "line_sum_ms": kms, "q_W_cm2": float(r["q"].item()),
+                     "clocks": clk.summary()}
+        del bufs
+    out["fp32_q_rel_err"] = abs(out["fp32"]["q_W_cm2"] / out["fp64"]["q_W_cm2"] - 1)
+    print(json.dumps({"workload": f"stagnation line with the exact Voigt shape: {C} cells, {len(p.lines)} lines, "
+                                  f"{K} points", "metric": "cell·λ points/s", "warmup": args.warmup,
+                      "steps": max(1, args.steps), **out}))
+    return 0
+
+
 def run_fibonacci(args):
     """The paper's own angular path on the afterbody at 100 x 50 cells (2e5
     points in 65,536-point chunks): Fibonacci lines of sight from
@@ -528,6 +571,8 @@ def main():
         return run_qss(args)
     if args.workload == "continuum":
         return run_continuum(args)
+    if args.workload == "voigt":
+        return run_voigt(args)
     import torch
     import torch.distributed as dist
 
