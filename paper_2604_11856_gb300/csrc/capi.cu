@@ -354,7 +354,8 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     }
     if (ctx->profile == RAPRAL_PROFILE_VOIGT) {
         a.voigt = 1;
-        a.vc = voigt_coefficients();
+        e = voigt_upload(ctx->device);
+        if (e != cudaSuccess) return cuda_status(ctx, e, "Voigt coefficients");
     }
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");

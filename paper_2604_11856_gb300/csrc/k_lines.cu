@@ -19,6 +19,11 @@
 // kappa and j.  Results are written once, coalesced.
 #include "rapral_internal.cuh"
 
+#include <mutex>
+
+// the rational Faddeeva expansion's coefficients (exact Voigt line shape)
+__constant__ VoigtCoef c_voigt;
+
 namespace {
 
 __device__ __forceinline__ double voigt_hwhm(double lamL, double lamG) {
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 const double dl = fabs(lk - P.lam0);
                 if (!(dl <= P.w100)) continue;
                 if (VG) {
-                    const double br = voigt_re<double>(a.vc, dl * P.inv2V, P.r);
+                    const double br = voigt_re<double>(c_voigt, dl * P.inv2V, P.r);
                     accj[i] += P.aj * br;
                     acck[i] += P.ak * br;
                     continue;
@@ -788,7 +793,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
             const float s = fabsf(A.w), r = B.x, aj = B.z, ak = B.w;
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
             const float ub = A.z, ub_lo = B.y;
-            if (FL & 4) sweep_pair_voigt<PPT>(a.vc, lo, hi, lanef, s, ub, ub_lo, r, aj, ak, bj, bk);
+            if (FL & 4) sweep_pair_voigt<PPT>(c_voigt, lo, hi, lanef, s, ub, ub_lo, r, aj, ak, bj, bk);
             else if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
             else sweep_pair<PPT, false>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
         }
@@ -1070,4 +1075,15 @@ const VoigtCoef& voigt_coefficients() {
         return v;
     }();
     return vc;
+}
+
+cudaError_t voigt_upload(int device) {
+    static std::mutex mu;
+    static bool done[256] = {};
+    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[device]) return cudaSuccess;
+    const cudaError_t e = cudaMemcpyToSymbol(c_voigt, &voigt_coefficients(), sizeof(VoigtCoef));
+    if (e == cudaSuccess) done[device] = true;
+    return e;
 }

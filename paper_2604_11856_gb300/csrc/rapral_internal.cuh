@@ -265,9 +265,9 @@ struct LineSumArgs {
     const int32_t* dep_u = nullptr;
     const int32_t* dep_l = nullptr;
     int32_t dep_nlev = 0;
-    // exact Voigt line shape instead of Whiting's (rapral_set_profile)
+    // exact Voigt line shape instead of Whiting's (rapral_set_profile; the
+    // expansion's coefficients are in constant memory, see voigt_upload)
     int voigt = 0;
-    VoigtCoef vc{};
 };
 
 // Workspace of the optional resonance / van der Waals terms of one request:
@@ -357,5 +357,7 @@ cudaError_t launch_fib_flux(rapral_ctx* ctx, int64_t P, const int64_t* point_off
                             void* scratch);
 cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n);
 
-// Coefficients of the rational Faddeeva expansion (computed once on the host).
+// Coefficients of the rational Faddeeva expansion: computed once on the host,
+// copied once to the constant memory of each device that uses them.
 const VoigtCoef& voigt_coefficients();
+cudaError_t voigt_upload(int device);

@@ -90,7 +90,7 @@ __device__ __forceinline__ void voigt_weid(const VoigtCoef& v, T x, T y, T& wr, 
     const T iD = vrcp(Ly * Ly + x * x);
     const T Zr = (L * L - x * x - y * y) * iD, Zi = T(2) * L * x * iD;
     T pr = vcoef(v, NW - 1, T()), pi = T(0);
-#pragma unroll
+#pragma unroll 4
     for (int n = NW - 2; n >= 0; --n) {
         const T tr = pr * Zr - pi * Zi + vcoef(v, n, T());
         pi = pr * Zi + pi * Zr;
