@@ -67,26 +67,36 @@ def parse():
 # DRAM bytes (read + write) of one FP32 line-sum launch on the stagnation line
 # at full size (200 cells x 1e6 points, tiling 128 x 4), from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
-# with this SHA-1.  Other cell / point counts scale in proportion (the bytes are
-# the kappa / j rows written); a different source gives null.
-LINE_SUM_TRAFFIC = {"sha1": "e145388161fd303dad3a82141d8e863926914ce0", "cells": 200, "grid_points": 1_000_000,
+# with this digest (source_digest).  Other cell / point counts scale in proportion (the bytes are
+# the kappa / j rows written); a different source (comments aside) gives null.
+LINE_SUM_TRAFFIC = {"sha1": "2e2ea4a3618e146d5c99d862b8a40566e6a56bd0", "cells": 200, "grid_points": 1_000_000,
                     "bytes": 56_704_256 + 1_548_718_848}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
 # 1e6 points, N and O with 100 levels each), from a one-pass ncu capture of the
-# kernel source with this SHA-1; a different source gives null.
-CONT_TRAFFIC = {"sha1": "56be3b7521f4cb1544556840cb4c7daba6b4cf02", "cells": 200, "grid_points": 1_000_000, "levels": 100,
+# kernel source with this digest (source_digest); a different source gives null.
+CONT_TRAFFIC = {"sha1": "fdd094a6c5ddad4bd32e272bb576b7a73d4c4a93", "cells": 200, "grid_points": 1_000_000, "levels": 100,
                 "bytes": 1_782_893_056 + 1_539_134_464}
 
 
-def continuum_traffic(cells, grid_points, levels):
+def source_digest(name):
+    """SHA-1 of a kernel source with its comments and white space removed, so
+    that only a change of the code itself invalidates a stored measurement."""
     import hashlib
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_11856_gb300", "csrc", "k_continuum.cu")
+    import re
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_11856_gb300", "csrc", name)
     try:
-        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        text = open(src).read()
     except OSError:
         return None
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return hashlib.sha1(re.sub(r"\s+", "", text).encode()).hexdigest()
+
+
+def continuum_traffic(cells, grid_points, levels):
+    digest = source_digest("k_continuum.cu")
     t = CONT_TRAFFIC
     if digest != t["sha1"] or (cells, grid_points, levels) != (t["cells"], t["grid_points"], t["levels"]):
         return None
@@ -94,12 +104,7 @@ def continuum_traffic(cells, grid_points, levels):
 
 
 def line_sum_traffic(cells, grid_points):
-    import hashlib
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2604_11856_gb300", "csrc", "k_lines.cu")
-    try:
-        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
+    digest = source_digest("k_lines.cu")
     if digest != LINE_SUM_TRAFFIC["sha1"]:
         return None
     t = LINE_SUM_TRAFFIC

@@ -1,7 +1,11 @@
 /*
  * rapral.h -- C ABI of the GB300 (sm_103a) implementation of the RAPRAL hot
  * path (arXiv 2604.11856): two-temperature populations, line-by-line spectral
- * coefficients, the segment-wise RTE march and the wall radiative heat flux.
+ * coefficients, the segment-wise RTE march and the wall radiative heat flux;
+ * batched and allocation-free variants; and the optional parts of the method:
+ * the Fibonacci lines of sight, the full Lorentz width and the exact Voigt
+ * shape, quasi-steady-state collisional-radiative and Saha-Boltzmann
+ * populations with departure coefficients, and the atomic continuum.
  *
  * Conventions (every entry point):
  *  - Returns an int status: RAPRAL_OK or one of the codes below.  No call

@@ -10,13 +10,20 @@
 //   scan           exclusive prefix of the counts -> CSR offsets
 //   k_bin_fill     same scan, ordered compaction of the line indices
 //
-// Line sum: one block per (tile, cell).  Threads own consecutive grid points
-// of the tile.  Lines of the tile are processed in batches of blockDim: each
-// thread sets up one (line, cell) pair -- populations in log space, strengths,
-// Doppler / Stark / Voigt widths, profile normalisation and the window --
-// into shared memory; then every thread evaluates the Whiting profile of each
-// staged pair at its own points inside that pair's window and accumulates
-// kappa and j.  Results are written once, coalesced.
+// Line sum, FP64: one block per (tile, cell).  Threads own consecutive grid
+// points of the tile.  Lines of the tile are processed in batches of
+// blockDim: each thread sets up one (line, cell) pair -- populations in log
+// space, strengths, Doppler / Stark / Voigt widths, profile normalisation and
+// the window -- into shared memory; then every thread evaluates the profile
+// of each staged pair at its own points inside that pair's window and
+// accumulates kappa and j.  Results are written once, coalesced.  FP32: one
+// warp per (tile, cell), described with its kernel below.
+//
+// Optional per-context parts, each a template flag of the kernels so that the
+// default path is unchanged: the full Lorentz width (Stark from the
+// ionisation gap, resonance, van der Waals), departure coefficients of
+// collisional-radiative levels, and the exact Voigt shape (voigt.cuh) in
+// place of Whiting's fit.
 #include "rapral_internal.cuh"
 
 #include <mutex>
