@@ -151,3 +151,39 @@ def test_departure_checks(ctx):
     ctx.clear_status()
     ctx.set_departures()
     ctx.sync()
+
+
+@pytest.mark.parametrize("precision", [R.FP64, R.FP32])
+@pytest.mark.parametrize("voigt_shape", [False, True])
+def test_departures_with_broadening_and_line_shape(ctx, precision, voigt_shape):
+    """Departures together with the optional Lorentz terms, with Whiting's
+    shape and with the exact Voigt shape (every combination of the line
+    sums' optional flags)."""
+    from oracle import voigt
+    ALL = R.BROAD_STARK_IONIZE | R.BROAD_RESONANCE | R.BROAD_VDW
+    p, m, lu, ll = _problem(6)
+    ctx.set_broadening(ALL, synth.RAD_E_IONIZE, synth.FLOW_MASS)
+    ctx.set_profile(R.PROFILE_VOIGT if voigt_shape else R.PROFILE_WHITING)
+    try:
+        kap, em, ln_b = _gpu(ctx, p, precision, m, lu, ll, 20)
+    finally:
+        ctx.set_broadening(0)
+        ctx.set_profile(R.PROFILE_WHITING)
+    oracle.set_broadening(ALL, synth.RAD_E_IONIZE, synth.FLOW_MASS)
+    oracle.set_departures(_oracle_departures(p, m, 20, ln_b.shape[1]), lu, ll)
+    try:
+        rk, re, ra = (voigt.spectral_coeffs(p, with_abs=True) if voigt_shape
+                      else oracle.spectral_coeffs(p, with_abs=True))
+    finally:
+        oracle.set_departures()
+        oracle.set_broadening(0)
+    scale = np.maximum(np.abs(rk), ra)
+    if precision == R.FP64:
+        assert np.max(np.abs(em - re) / np.maximum(np.abs(re), 1e-300)) <= 1e-10
+        m_ = scale > 0
+        assert np.max(np.abs(kap - rk)[m_] / scale[m_]) <= 1e-10
+    else:
+        big = re >= 1e-6 * re.max(axis=1, keepdims=True)
+        assert np.max((np.abs(em - re) / np.maximum(re, 1e-300))[big]) <= 1e-3
+        bigk = scale >= 1e-6 * scale.max(axis=1, keepdims=True)
+        assert np.max((np.abs(kap - rk) / np.maximum(scale, 1e-300))[bigk]) <= 1e-3
