@@ -354,8 +354,11 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     }
     if (ctx->profile == RAPRAL_PROFILE_VOIGT) {
         a.voigt = 1;
-        e = voigt_upload(ctx->device);
-        if (e != cudaSuccess) return cuda_status(ctx, e, "Voigt coefficients");
+        if (!ctx->voigt_ready) {
+            e = voigt_upload();
+            if (e != cudaSuccess) return cuda_status(ctx, e, "Voigt coefficients");
+            ctx->voigt_ready = true;
+        }
     }
     e = launch_line_sum(ctx, a, precision, T);
     return cuda_status(ctx, e, "line sum");

@@ -26,8 +26,6 @@
 // place of Whiting's fit.
 #include "rapral_internal.cuh"
 
-#include <mutex>
-
 // the rational Faddeeva expansion's coefficients (exact Voigt line shape)
 __constant__ VoigtCoef c_voigt;
 
@@ -1084,13 +1082,6 @@ const VoigtCoef& voigt_coefficients() {
     return vc;
 }
 
-cudaError_t voigt_upload(int device) {
-    static std::mutex mu;
-    static bool done[256] = {};
-    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (done[device]) return cudaSuccess;
-    const cudaError_t e = cudaMemcpyToSymbol(c_voigt, &voigt_coefficients(), sizeof(VoigtCoef));
-    if (e == cudaSuccess) done[device] = true;
-    return e;
+cudaError_t voigt_upload() {
+    return cudaMemcpyToSymbol(c_voigt, &voigt_coefficients(), sizeof(VoigtCoef));
 }

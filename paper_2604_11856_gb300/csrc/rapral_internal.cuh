@@ -156,7 +156,8 @@ struct rapral_ctx {
     const int32_t* dep_l = nullptr;
     int32_t dep_nlev = 0, dep_S = 0;
     int64_t dep_C = 0, dep_L = 0;
-    int profile = 0;   // RAPRAL_PROFILE_WHITING or RAPRAL_PROFILE_VOIGT
+    int profile = 0;          // RAPRAL_PROFILE_WHITING or RAPRAL_PROFILE_VOIGT
+    bool voigt_ready = false; // the expansion's coefficients are on this context's device
     char err[512] = {0};
 };
 
@@ -358,6 +359,7 @@ cudaError_t launch_fib_flux(rapral_ctx* ctx, int64_t P, const int64_t* point_off
 cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n);
 
 // Coefficients of the rational Faddeeva expansion: computed once on the host,
-// copied once to the constant memory of each device that uses them.
+// copied to the current device's constant memory by the first exact-Voigt
+// call of each context.
 const VoigtCoef& voigt_coefficients();
-cudaError_t voigt_upload(int device);
+cudaError_t voigt_upload();
