@@ -679,7 +679,8 @@ def main():
                 "kernel": "k_line_sum_f32", "kernel_ms": k3_mean, "evaluations": evals_per_step,
                 "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"}
     else:
-        # FP64: ~40 FP64 operations per evaluation, 2 FP64 FMA lanes per SM per clock
+        # FP64: about 40 FP64 operations per evaluation (two exponentials, two square roots, the bracket),
+        # 2 FP64 FMA lanes per SM per clock
         fp64_ops = 40.0 * evals_per_step
         peak = n_sm * 2 * 2 * sm_max / 1e9
         achieved = fp64_ops / (k3_mean * 1e-3) / 1e9
