@@ -291,8 +291,28 @@ __device__ void block_count(unsigned long long* stats, int64_t ev, int64_t g, in
 
 struct __align__(16) PairF64 {
     double lam0, w100, inv2V, r, omr, c16, aj, ak;
+    double ug2, ue2;   // u^2 past which the Gaussian / correction exponential is left out
     int klo, khi, pad0, pad1;
 };
+
+// Exponentials of the Whiting bracket left out where they are below 1e-17 of
+// its Lorentz part (at least r / (2 (1 + 4u^2)); the part is positive for
+// every u), far below the FP64 rounding of the sum:
+//   Gaussian (1 - r) e^{-2.772 x}, x = u^2: from the x with
+//     2.772 x - ln(1 + 4x) = ln(2e17 (1 - r) / r), by fixed-point iteration
+//     from below plus a margin, capped at the FP64 underflow (2.772 x = 745.5);
+//   correction c16 e^{-0.4 x^1.125}: c16 / r <= 0.016 for every r, so one
+//     bound serves all pairs, x = 65.14 (0.4 x^1.125 - ln(1 + 4x) = ln(3.2e15)).
+constexpr double SKIP_CORR_U2 = 65.14;
+__device__ double skip_gauss_u2(double omr, double r) {
+    const double under = 745.5 / 2.772;
+    if (!(omr > 0.0)) return 0.0;
+    if (!(r > 0.0)) return under;
+    const double K = log(2e17 * omr / r);
+    double x = fmax(K, 0.0) / 2.772;
+    for (int i = 0; i < 4; ++i) x = fmax(K + log1p(4.0 * x), 0.0) / 2.772;
+    return fmin(1.05 * x + 0.5, under);
+}
 
 // Lorentz HWHM of line l in cell c in FP64: natural + Stark, plus the
 // optional resonance and van der Waals terms.
@@ -358,6 +378,10 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 P.r = r;
                 P.omr = 1.0 - r;
                 P.c16 = 0.016 * r * (1.0 - r);
+                if (!VG) {
+                    P.ug2 = skip_gauss_u2(P.omr, r);
+                    P.ue2 = P.c16 > 0.0 ? SKIP_CORR_U2 : 0.0;
+                }
                 P.aj = Sj * pre;
                 P.ak = Sk * pre;
                 const double lo = ceil((L.lam0 - P.w100 - a.lam_min) / a.h) - 1.0;
@@ -400,11 +424,9 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
                 }
                 const double u = dl * P.inv2V;
                 const double u2 = u * u;
-                const double ga = 2.772 * u2;
-                const double g = ga < 745.5 ? exp(-ga) : 0.0;
+                const double g = u2 < P.ug2 ? exp(-2.772 * u2) : 0.0;
                 const double v = u2 * sqrt(sqrt(u));
-                const double ea = 0.4 * v;
-                const double e2 = ea < 745.5 ? exp(-ea) : 0.0;
+                const double e2 = u2 < P.ue2 ? exp(-0.4 * v) : 0.0;
                 const double qd = 1.0 + 4.0 * u2;
                 const double pd = 1.0 + 0.1 * v;
                 const double br = P.omr * g + (P.r * pd - P.c16 * qd) / (qd * pd) + P.c16 * e2;
