@@ -76,8 +76,8 @@ LINE_SUM_TRAFFIC = {"sha1": "8dd4c7c80e6ada12c1dd1e31d4114b3adf1873e9", "cells":
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
 # 1e6 points, N and O with 100 levels each), from a one-pass ncu capture of the
 # kernel source with this digest (source_digest); a different source gives null.
-CONT_TRAFFIC = {"sha1": "fdd094a6c5ddad4bd32e272bb576b7a73d4c4a93", "cells": 200, "grid_points": 1_000_000, "levels": 100,
-                "bytes": 1_782_893_056 + 1_539_134_464}
+CONT_TRAFFIC = {"sha1": "5acd74ef87910912678c8d6546c788ab0f5e87b0", "cells": 200, "grid_points": 1_000_000, "levels": 100,
+                "bytes": 1_782_956_800 + 1_538_739_456}
 
 
 def source_digest(name):

@@ -404,6 +404,20 @@ struct Pair<double> {
 template <typename V>
 __device__ __forceinline__ auto& comp(V& v, int e) { return e ? v.y : v.x; }
 
+// asynchronous global -> shared copies (cp.async): 16-byte pieces, and
+// single 4- or 8-byte elements with zero fill when `in` is false
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+template <typename Tp>
+__device__ __forceinline__ void cp_async_elem(unsigned dst, const Tp* src, bool in) {
+    const unsigned n = in ? (unsigned)sizeof(Tp) : 0u;
+    if (sizeof(Tp) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
 template <typename Tp, int PP>
 __device__ __forceinline__ void load_pts(const Tp* p, Tp (&o)[PP]) {
     using V = typename VecOf<Tp, PP>::type;
@@ -448,10 +462,34 @@ __device__ __forceinline__ void cont_block(const ContMain& a, int64_t t, int64_t
     for (int r0 = 0; r0 < nl; r0 += CONT_LCH) {
         const int nr = min(CONT_LCH, nl - r0);
         __syncthreads();
-        {   // all loads of the chunk in flight before the first shared-memory store
+        if (sizeof(Tp) == 4) {   // the chunk's table rows and level factors, copied asynchronously
+            constexpr int NV = CONT_LCH * W * (int)sizeof(Tp) / 16 / 128;   // 16-byte pieces a thread
+            constexpr int NC = CONT_LCH * CB / 128;                        // factors a thread
+            const int nv = nr * W * (int)sizeof(Tp) / 16;
+            const char* src = reinterpret_cast<const char*>(tab + (int64_t)r0 * W);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&sg[0][0]);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int x = threadIdx.x + i * 128;
+                if (x < nv) cp_async16(dst + 16u * x, src + 16 * (int64_t)x);
+            }
+            const unsigned dN = (unsigned)__cvta_generic_to_shared(&sN[0][0]);
+            const unsigned dA = (unsigned)__cvta_generic_to_shared(&sA[0][0]);
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const int x = threadIdx.x + i * 128, rr = x / CB;
+                const int64_t c = cb0 + x % CB;
+                const bool in = rr < nr && c < a.C;
+                const int64_t o = in ? (int64_t)(r0 + rr) * a.C + c : 0;   // a valid address; nothing is read when out
+                cp_async_elem<Tp>(dN + sizeof(Tp) * x, cN + o, in);
+                cp_async_elem<Tp>(dA + sizeof(Tp) * x, cA + o, in);
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        } else {   // FP64: every load of the chunk in flight before the first shared-memory store
             using V = typename VecOf<Tp, 16 / sizeof(Tp)>::type;
-            constexpr int NV = CONT_LCH * W * (int)sizeof(Tp) / 16 / 128;   // 16-byte vectors a thread
-            constexpr int NC = CONT_LCH * CB / 128;                        // coefficients a thread
+            constexpr int NV = CONT_LCH * W * (int)sizeof(Tp) / 16 / 128;
+            constexpr int NC = CONT_LCH * CB / 128;
             const int nv = nr * W * (int)sizeof(Tp) / 16;
             const V* src = reinterpret_cast<const V*>(tab + (int64_t)r0 * W);
             V* dst = reinterpret_cast<V*>(&sg[0][0]);
