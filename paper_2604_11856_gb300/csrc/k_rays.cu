@@ -88,6 +88,52 @@ __device__ __forceinline__ void seg_step(float& I, float kf, float s, float jf, 
     I = fmaf(m, fmaf(pa, jf, pb * jn), I * e);
 }
 
+// Two steps at once in FP32 (two wavelength columns, or two directions of a
+// bundle): where both are optically thin the series and the update run as
+// packed pairs (one instruction for both, each with the scalar step's IEEE
+// result); otherwise each takes the scalar step.
+__device__ __forceinline__ void seg_step2(float& I0, float& I1, float k0, float k1, float s0, float s1, float jf0,
+                                          float jf1, float jn0, float jn1) {
+    const float2 dt = __fmul2_rn(make_float2(k0, k1), make_float2(s0, s1));
+    if (fabsf(dt.x) < (float)RAPRAL_THIN_F32 && fabsf(dt.y) < (float)RAPRAL_THIN_F32) {
+        const float e0 = ex2f_approx(-1.44269504f * dt.x), e1 = ex2f_approx(-1.44269504f * dt.y);
+        const auto c2 = [](float c) { return make_float2(c, c); };
+        float2 pa = __ffma2_rn(dt, c2(1.0f / 5760.0f), c2(-1.0f / 840.0f));
+        pa = __ffma2_rn(dt, pa, c2(1.0f / 144.0f));
+        pa = __ffma2_rn(dt, pa, c2(-1.0f / 30.0f));
+        pa = __ffma2_rn(dt, pa, c2(0.125f));
+        pa = __ffma2_rn(dt, pa, c2(-1.0f / 3.0f));
+        pa = __ffma2_rn(dt, pa, c2(0.5f));
+        float2 pb = __ffma2_rn(dt, c2(1.0f / 40320.0f), c2(-1.0f / 5040.0f));
+        pb = __ffma2_rn(dt, pb, c2(1.0f / 720.0f));
+        pb = __ffma2_rn(dt, pb, c2(-1.0f / 120.0f));
+        pb = __ffma2_rn(dt, pb, c2(1.0f / 24.0f));
+        pb = __ffma2_rn(dt, pb, c2(-1.0f / 6.0f));
+        pb = __ffma2_rn(dt, pb, c2(0.5f));
+        const float2 u = __ffma2_rn(pa, make_float2(jf0, jf1), __fmul2_rn(pb, make_float2(jn0, jn1)));
+        const float2 r = __ffma2_rn(make_float2(s0, s1), u, __fmul2_rn(make_float2(I0, I1), make_float2(e0, e1)));
+        I0 = r.x;
+        I1 = r.y;
+    } else {
+        seg_step(I0, k0, s0, jf0, jn0);
+        seg_step(I1, k1, s1, jf1, jn1);
+    }
+}
+
+// the MAXD directions of one column: packed in pairs in FP32
+template <class T, int MAXD>
+__device__ __forceinline__ void dir_steps(T (&I)[MAXD], T kf, T ds, const T* sc, T jf, T jn) {
+    if constexpr (sizeof(T) == 4 && MAXD > 1) {
+#pragma unroll
+        for (int d = 0; d + 1 < MAXD; d += 2)
+            seg_step2(I[d], I[d + 1], kf, kf, ds * sc[d], ds * sc[d + 1], jf, jf, jn, jn);
+        if (MAXD & 1) seg_step(I[MAXD - 1], kf, ds * sc[MAXD - 1], jf, jn);
+    } else {
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) seg_step(I[d], kf, MAXD == 1 ? ds : ds * sc[d], jf, jn);
+    }
+}
+
 __global__ void k_validate_rays(const int32_t* seg_cell, const double* seg_ds, int64_t nseg, int64_t C,
                                 const double* dir_scale, int64_t ndir, int* status) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -207,9 +253,14 @@ __device__ __forceinline__ void march_nodes(const MarchArgs& a, int64_t b, T sc,
                 ky[v] = *reinterpret_cast<const T*>(rn + offK + 32 * v * sizeof(T));
                 jy[v] = *reinterpret_cast<const T*>(rn + offJ + 32 * v * sizeof(T));
             }
+            if constexpr (V == 2 && sizeof(T) == 4) {
+                seg_step2(I[0][0], I[1][0], kf[0], kf[1], ds, ds, jf[0], jf[1], jx[0], jx[1]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) seg_step(I[v][0], kf[v], ds, jf[v], jx[v]);
+            }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                seg_step(I[v][0], kf[v], ds, jf[v], jx[v]);
                 kf[v] = kx[v]; jf[v] = jx[v];
                 kx[v] = ky[v]; jx[v] = jy[v];
             }
@@ -276,12 +327,21 @@ __device__ __forceinline__ void march_bundle(const MarchArgs& a, int64_t b, int6
                 ky[v] = *reinterpret_cast<const T*>(rn + offK + 32 * v * sizeof(T));
                 jy[v] = *reinterpret_cast<const T*>(rn + offJ + 32 * v * sizeof(T));
             }
+            T kn[V], jn[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const T kn = T(0.5) * (kc[v] + kx[v]), jn = T(0.5) * (jc[v] + jx[v]);
+                kn[v] = T(0.5) * (kc[v] + kx[v]);
+                jn[v] = T(0.5) * (jc[v] + jx[v]);
+            }
+            if constexpr (V == 2 && MAXD == 1 && sizeof(T) == 4) {
+                seg_step2(I[0][0], I[1][0], kf[0], kf[1], ds, ds, jf[0], jf[1], jn[0], jn[1]);
+            } else {
 #pragma unroll
-                for (int d = 0; d < MAXD; ++d) seg_step(I[v][d], kf[v], MAXD == 1 ? ds : ds * sc[d], jf[v], jn);
-                kf[v] = kn; jf[v] = jn;
+                for (int v = 0; v < V; ++v) dir_steps<T, MAXD>(I[v], kf[v], ds, sc, jf[v], jn[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                kf[v] = kn[v]; jf[v] = jn[v];
                 kc[v] = kx[v]; jc[v] = jx[v];
                 kx[v] = ky[v]; jx[v] = jy[v];
             }
@@ -289,10 +349,12 @@ __device__ __forceinline__ void march_bundle(const MarchArgs& a, int64_t b, int6
     }
     {   // last segment: its near node is the cell's own value
         const T ds = seg_len<T>(a, s1 - 1) * stage_scale;
+        if constexpr (V == 2 && MAXD == 1 && sizeof(T) == 4) {
+            seg_step2(I[0][0], I[1][0], kf[0], kf[1], ds, ds, jf[0], jf[1], jc[0], jc[1]);
+        } else {
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d) seg_step(I[v][d], kf[v], MAXD == 1 ? ds : ds * sc[d], jf[v], jc[v]);
+            for (int v = 0; v < V; ++v) dir_steps<T, MAXD>(I[v], kf[v], ds, sc, jf[v], jc[v]);
+        }
     }
 }
 
