@@ -344,11 +344,11 @@ RAPRAL_API int rapral_batch_units(const rapral_batch* batch, int64_t* units, int
 RAPRAL_API void rapral_batch_destroy(rapral_batch* batch);
 
 /* rapral_spectral_coeffs without any device allocation.  (No counterpart in
- * the paper: it exists for callers that cannot allocate.)  Code that runs
- * while a CUDA graph is being captured on its stream, real-time loops that
- * must stay off the allocator, and programs whose device memory belongs to
- * an outer framework's pool cannot call cudaMalloc; this entry point needs
- * neither a context nor a workspace.  Its scratch is one static device array
+ * the paper: it exists for callers that cannot allocate.)  Real-time loops
+ * that must stay off the allocator (an allocation can block on the driver),
+ * and plug-ins whose device memory belongs to the host program's own pool,
+ * cannot call cudaMalloc; this entry point needs neither a context nor a
+ * workspace.  Its scratch is one static device array
  * of 64 MiB inside the library, held by every GPU that loads the library
  * until the process exits.  The first call on a device looks the array's
  * address up (cudaGetSymbolAddress); make that first call before any stream

@@ -1,10 +1,10 @@
 // rapral_spectral_coeffs_noalloc: the line-by-line coefficients for callers
 // that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured on its stream, real-time loops that must not touch the
-// allocator, and host processes embedded in a framework that owns all device
-// memory (a pool that must not be fragmented or exceeded).  This entry point
+// Some callers cannot call cudaMalloc: real-time loops that must not touch
+// the allocator (an allocation can block on the driver for an unbounded
+// time), and plug-ins running inside a host program that owns all device
+// memory through its own pool, which must not be fragmented or exceeded.  This entry point
 // runs the same kernels as rapral_spectral_coeffs, but every scratch buffer
 // (per-line and per-cell records, the tile ranges, the tile lists, the
 // status and counter words) lives in one file-scope __device__ array of

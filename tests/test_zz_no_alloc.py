@@ -1,6 +1,6 @@
 """rapral_spectral_coeffs_noalloc: the coefficients for callers that cannot
-allocate device memory (graph capture, allocator-free loops, memory owned by
-an outer pool).  Its output must equal the regular entry point's on two
+allocate device memory (allocator-free real-time loops, plug-ins whose
+device memory belongs to the host program's pool).  Its output must equal the regular entry point's on two
 calls in a row with different problems (the shared static scratch keeps the
 previous call's contents), and a problem larger than the 64 MiB scratch must
 be refused with ENOMEM and a message.  Collected last (file name) so that a
