@@ -61,6 +61,8 @@ def parse():
                     help="afterbody workload at 100 x 50 cells, 20 points, 2e5 grid points (profiler captures)")
     ap.add_argument("--cells", type=int, default=200,
                     help="cells of the stagnation line (fewer only for profiler captures)")
+    ap.add_argument("--oracle-phases", action="store_true",
+                    help="with --impl reference: the oracle's time per phase, all threads and one thread")
     return ap.parse_args()
 
 
@@ -249,6 +251,78 @@ def run_reference(args):
             "cpu_baseline": {**last, "value": v},
             "e2e": {"value": v, "unit": "cell·λ points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+    return 0
+
+
+def oracle_phases(args):
+    """--impl reference --oracle-phases: wall-clock of the oracle as it stands,
+    per phase (populations, coefficients, march with the angular sum, spectral
+    integral), with all OpenMP threads and with one.  The uniform slab runs
+    whole.  On the stagnation line the populations run whole, the
+    coefficients on a sample of cells over the whole grid (one cell per
+    thread; two cells on one thread), projected by the cell ratio, and the
+    march and spectral integral over every cell and direction on a
+    5,000-point slice in the middle of the grid, projected by the column
+    ratio.  One JSON line per (workload, threads)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2604_11856_gb300 import synth
+    lib = oracle.lib()
+    n_all = lib.orc_num_threads()
+    cases = (("uniform slab: 20 cells, 1,500 atomic lines, 2e5-point grid, 16-mu tangent slab + normal ray",
+              synth.uniform_slab(), False),
+             ("stagnation line: 200 cells, 20k atomic + 300k molecular lines, 1e6-point grid, 16-mu tangent slab",
+              synth.stagnation_line(), True))
+    for name, p, sampled in cases:
+        K, C = p.grid.n, len(p.cells)
+        geo = p.geometry
+        order = np.asarray(geo.cell_order, np.int64)
+        w = 2.0 * np.pi * np.asarray(geo.wmu) * np.asarray(geo.mu)
+        lnp = oracle.lnpref(p)
+        k0, nk = ((K - 5000) // 2, 5000) if sampled else (0, K)
+        kap, em = oracle.spectral_coeffs(p, lnp, k0, nk)    # the march's input (timed below when whole)
+        for threads in (n_all, 1):
+            lib.orc_set_threads(threads)
+            t, full, sample = {}, {}, {}
+            t0 = time.perf_counter()
+            lnp = oracle.lnpref(p)
+            t["populations"] = full["populations"] = time.perf_counter() - t0
+            if sampled:
+                n_c = threads if threads > 1 else 2
+                idx = np.linspace(0, C - 1, n_c).round().astype(int)
+                sub = synth.Problem(p.name, p.species, p.lines,
+                                    synth.Cells(Ttr=p.cells.Ttr[idx], Tve=p.cells.Tve[idx], n=p.cells.n[idx]),
+                                    p.grid, geo)
+                t0 = time.perf_counter()
+                oracle.spectral_coeffs(sub, lnp[idx], 0, K)
+                t["coefficients"] = time.perf_counter() - t0
+                full["coefficients"] = t["coefficients"] * C / n_c
+                sample["coefficients"] = f"{n_c} of {C} cells, whole grid"
+            else:
+                t0 = time.perf_counter()
+                oracle.spectral_coeffs(p, lnp, 0, K)
+                t["coefficients"] = full["coefficients"] = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            qlam = np.zeros(nk)
+            for m, mu in enumerate(geo.mu):
+                qlam += w[m] * oracle.march(order, geo.dx, 1.0 / mu, kap, em, p.grid, k0, geo.wall_start, geo.T_wall)
+            if geo.normal_ray:
+                oracle.march(order, geo.dx, 1.0, kap, em, p.grid, k0, geo.wall_start, geo.T_wall)
+            t["march_angular"] = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle.spectral_integral(qlam, p.grid, k0)
+            t["spectral_integral"] = time.perf_counter() - t0
+            for k in ("march_angular", "spectral_integral"):
+                full[k] = t[k] * K / nk
+                if sampled:
+                    sample[k] = f"all cells and directions, {nk} of {K} grid points"
+            print(json.dumps({"impl": "reference", "kind": "oracle phases", "workload": name, "threads": threads,
+                              "seconds_run": t, "sample": sample, "seconds_projected_full": full,
+                              "total_projected_s": sum(full.values()),
+                              "cell_lambda_per_s": C * K / full["coefficients"]}))
+    lib.orc_set_threads(n_all)
     return 0
 
 
@@ -568,7 +642,7 @@ def run_fibonacci(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        return run_reference(args)
+        return oracle_phases(args) if args.oracle_phases else run_reference(args)
     if args.workload == "afterbody":
         return run_afterbody(args)
     if args.workload == "batch":
