@@ -67,12 +67,12 @@ def parse():
 
 
 # DRAM bytes (read + write) of one FP32 line-sum launch on the stagnation line
-# at full size (200 cells x 1e6 points, tiling 128 x 4), from a one-pass ncu
+# at full size (200 cells x 1e6 points, tiling 128 x 2), from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
 # with this digest (source_digest).  Other cell / point counts scale in proportion (the bytes are
 # the kappa / j rows written); a different source (comments aside) gives null.
-LINE_SUM_TRAFFIC = {"sha1": "8dd4c7c80e6ada12c1dd1e31d4114b3adf1873e9", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 57_231_360 + 1_548_549_888}
+LINE_SUM_TRAFFIC = {"sha1": "c7b234de6b625182054a75ef472fb6cdfda8519b", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 58_913_536 + 1_547_149_568}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x

@@ -739,6 +739,49 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
     }
 }
 
+// One pair whose window covers every point of the tile: no point needs the
+// window test, so the brackets of runs i and i + 1 are evaluated together in
+// packed FP32 (two results per instruction; the MUFU operations stay
+// scalar).  Operations and roundings are those of whiting_bracket and of the
+// predicated update, so the sums are bitwise the same as sweep_pair's.
+template <int PPT, bool FAR>
+__device__ __forceinline__ void sweep_pair_full(float lanef, float s, float ub, float ub_lo, float r, float omr,
+                                                float c16, float aj, float ak, float (&bj)[PPT], float (&bk)[PPT]) {
+    static_assert(PPT % 2 == 0, "runs are taken two at a time");
+    const float2 s2 = make_float2(s, s), ub2 = make_float2(ub, ub), ubl2 = make_float2(ub_lo, ub_lo);
+    const float2 one = make_float2(1.0f, 1.0f), four = make_float2(4.0f, 4.0f), tenth = make_float2(0.1f, 0.1f);
+    const float2 r2 = make_float2(r, r), nc16 = make_float2(-c16, -c16);
+    const float2 aj2 = make_float2(aj, aj), ak2 = make_float2(ak, ak);
+#pragma unroll
+    for (int i = 0; i < PPT; i += 2) {
+        const float2 k = make_float2(lanef + 32.0f * i, lanef + 32.0f * (i + 1));
+        const float2 u = __fadd2_rn(__ffma2_rn(k, s2, ub2), ubl2);     // signed u; only |u| and u^2 are used
+        const float2 u2 = __fmul2_rn(u, u);
+        const float2 q = make_float2(rsqrt_approx(rsqrt_approx(fabsf(u.x))), rsqrt_approx(rsqrt_approx(fabsf(u.y))));
+        const float2 v = __fmul2_rn(u2, q);                            // u^2.25
+        const float2 q4 = __ffma2_rn(four, u2, one);
+        const float2 p1 = __ffma2_rn(tenth, v, one);
+        const float2 qp = __fmul2_rn(q4, p1);
+        const float2 rd = make_float2(rcp_approx(qp.x), rcp_approx(qp.y));
+        const float2 num = __ffma2_rn(r2, p1, __fmul2_rn(nc16, q4));   // r(1+0.1v) - c16(1+4u^2)
+        float2 br;
+        if (FAR) {
+            br = __fmul2_rn(num, rd);
+        } else {
+            const float2 xg = __fmul2_rn(make_float2(-3.99915f, -3.99915f), u2);
+            const float2 xc = __fmul2_rn(make_float2(-0.5770780f, -0.5770780f), v);
+            const float2 g = make_float2(ex2_approx(xg.x), ex2_approx(xg.y));     // e^{-2.772 u^2}
+            const float2 e2 = make_float2(ex2_approx(xc.x), ex2_approx(xc.y));    // e^{-0.4 v}
+            br = __ffma2_rn(make_float2(omr, omr), g,
+                            __ffma2_rn(num, rd, __fmul2_rn(make_float2(c16, c16), e2)));
+        }
+        const float2 j2 = __ffma2_rn(aj2, br, make_float2(bj[i], bj[i + 1]));
+        const float2 k2 = __ffma2_rn(ak2, br, make_float2(bk[i], bk[i + 1]));
+        bj[i] = j2.x; bj[i + 1] = j2.y;
+        bk[i] = k2.x; bk[i + 1] = k2.y;
+    }
+}
+
 // The same sweep with the exact Voigt shape: r is y, u is x.
 template <int PPT>
 __device__ __forceinline__ void sweep_pair_voigt(const VoigtCoef& vc, float lo, float hi, float lanef, float s, float ub,
@@ -821,7 +864,10 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
             const float ub = A.z, ub_lo = B.y;
             if (FL & 4) sweep_pair_voigt<PPT>(c_voigt, lo, hi, lanef, s, ub, ub_lo, r, aj, ak, bj, bk);
-            else if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            else if (lo <= 0.0f && hi >= (float)(TW - 1)) {   // the whole tile in the window
+                if (A.w < 0.0f) sweep_pair_full<PPT, true>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+                else sweep_pair_full<PPT, false>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            } else if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
             else sweep_pair<PPT, false>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
         }
 #pragma unroll
