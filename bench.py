@@ -34,7 +34,8 @@ L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 20 for the stagnation-line step, 5 for the other workloads)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["rapral", "reference"], default="rapral")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
@@ -63,7 +64,10 @@ def parse():
                     help="cells of the stagnation line (fewer only for profiler captures)")
     ap.add_argument("--oracle-phases", action="store_true",
                     help="with --impl reference: the oracle's time per phase, all threads and one thread")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:   # the stagnation step takes ~31 ms: 20 steps give the clock sampler a few samples
+        args.steps = 20 if (args.impl == "rapral" and args.workload == "stagnation") else 5
+    return args
 
 
 # DRAM bytes (read + write) of one FP32 line-sum launch on the stagnation line
@@ -71,8 +75,8 @@ def parse():
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
 # with this digest (source_digest).  Other cell / point counts scale in proportion (the bytes are
 # the kappa / j rows written); a different source (comments aside) gives null.
-LINE_SUM_TRAFFIC = {"sha1": "c7b234de6b625182054a75ef472fb6cdfda8519b", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 58_913_536 + 1_547_149_568}
+LINE_SUM_TRAFFIC = {"sha1": "f87f52f2af490b38f1ab0030a15cf40f00f184d5", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 55_842_048 + 1_546_275_840}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
@@ -128,7 +132,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()

@@ -670,7 +670,10 @@ __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF
     P->lo = lo_rel;
     P->hi = hi_rel;
     P->s = umin > 11.0f ? -s : s;
-    P->r = r;
+    // between |u| = 5.62 and 11 only the Gaussian core is zero in FP32
+    // (2.772 u^2 log2(e) > 126): r (> 0, lamL holds the natural width) is
+    // stored negated
+    P->r = (!VG && umin > 5.62f && umin <= 11.0f) ? -r : r;
     P->aj = Sj * pre;
     P->ak = Sk * pre;
     if (count) {
@@ -687,11 +690,17 @@ __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF
     return true;
 }
 
+// Bracket modes: both exponentials; the Gaussian core zero in FP32 over the
+// span (|u| > 5.62, 2.772 u^2 log2(e) > 126); both zero (|u| > 11, also
+// 0.4 u^2.25 log2(e) > 126).  Dropping a term that ex2 flushes to zero leaves
+// every sum bitwise the same.
+enum { BR_NEAR = 0, BR_MID = 1, BR_FAR = 2 };
+
 // One Whiting evaluation, bracket only (the factor 1e3 / (2 lamV (1.065 +
 // 0.447 r + 0.058 r^2)) is folded into aj, ak).  Near the line centre both
-// exponentials are kept; `far` drops them where they are zero in FP32
-// (u^2 >= 31.5 and u^2.25 >= 218 over the whole span being evaluated).
-template <bool FAR>
+// exponentials are kept; BR_MID drops the Gaussian core and BR_FAR both
+// where they are zero in FP32 over the whole span being evaluated.
+template <int M>
 __device__ __forceinline__ float whiting_bracket(float u, float r, float omr, float c16) {
     const float u2 = u * u;
     const float v = u2 * rsqrt_approx(rsqrt_approx(u));                      // u^2.25
@@ -699,11 +708,12 @@ __device__ __forceinline__ float whiting_bracket(float u, float r, float omr, fl
     const float p1 = fmaf(0.1f, v, 1.0f);
     const float rd = rcp_approx(q4 * p1);
     const float num = fmaf(r, p1, -c16 * q4);                                // r(1+0.1v) - c16(1+4u^2)
-    if (FAR) return num * rd;
+    if (M == BR_FAR) return num * rd;
     // past u^2 = 31.5 and v = 218 the approximate ex2 returns 0 (flushed) or
     // below 1.5e-38, so neither exponential needs a guard
-    const float g = ex2_approx(-3.99915f * u2);      // e^{-2.772 u^2}
     const float e2 = ex2_approx(-0.5770780f * v);    // e^{-0.4 v}
+    if (M == BR_MID) return fmaf(num, rd, c16 * e2);
+    const float g = ex2_approx(-3.99915f * u2);      // e^{-2.772 u^2}
     return fmaf(omr, g, fmaf(num, rd, c16 * e2));
 }
 
@@ -719,7 +729,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 // points outside the window part [lo, hi] are skipped (the test is the same
 // for the whole warp); in the others each lane adds its point if it lies in
 // the window.
-template <int PPT, bool FAR>
+template <int PPT, int M>
 __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, float s, float ub, float ub_lo, float r,
                                            float omr, float c16, float aj, float ak, float (&bj)[PPT],
                                            float (&bk)[PPT]) {
@@ -731,7 +741,7 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
         // signed u at point k: one rounding of k s + ub (exact product), then
         // the low part; relative to u itself, so the Gaussian core keeps FP32
         // accuracy however far the tile start lies from the line centre
-        const float br = whiting_bracket<FAR>(fabsf(fmaf(k, s, ub) + ub_lo), r, omr, c16);
+        const float br = whiting_bracket<M>(fabsf(fmaf(k, s, ub) + ub_lo), r, omr, c16);
         if (k >= lo && k <= hi) {   // predicated update: lanes outside the window part add nothing
             bj[i] = fmaf(aj, br, bj[i]);
             bk[i] = fmaf(ak, br, bk[i]);
@@ -744,7 +754,7 @@ __device__ __forceinline__ void sweep_pair(float lo, float hi, float lanef, floa
 // packed FP32 (two results per instruction; the MUFU operations stay
 // scalar).  Operations and roundings are those of whiting_bracket and of the
 // predicated update, so the sums are bitwise the same as sweep_pair's.
-template <int PPT, bool FAR>
+template <int PPT, int M>
 __device__ __forceinline__ void sweep_pair_full(float lanef, float s, float ub, float ub_lo, float r, float omr,
                                                 float c16, float aj, float ak, float (&bj)[PPT], float (&bk)[PPT]) {
     static_assert(PPT % 2 == 0, "runs are taken two at a time");
@@ -765,15 +775,17 @@ __device__ __forceinline__ void sweep_pair_full(float lanef, float s, float ub, 
         const float2 rd = make_float2(rcp_approx(qp.x), rcp_approx(qp.y));
         const float2 num = __ffma2_rn(r2, p1, __fmul2_rn(nc16, q4));   // r(1+0.1v) - c16(1+4u^2)
         float2 br;
-        if (FAR) {
+        if (M == BR_FAR) {
             br = __fmul2_rn(num, rd);
         } else {
-            const float2 xg = __fmul2_rn(make_float2(-3.99915f, -3.99915f), u2);
             const float2 xc = __fmul2_rn(make_float2(-0.5770780f, -0.5770780f), v);
-            const float2 g = make_float2(ex2_approx(xg.x), ex2_approx(xg.y));     // e^{-2.772 u^2}
             const float2 e2 = make_float2(ex2_approx(xc.x), ex2_approx(xc.y));    // e^{-0.4 v}
-            br = __ffma2_rn(make_float2(omr, omr), g,
-                            __ffma2_rn(num, rd, __fmul2_rn(make_float2(c16, c16), e2)));
+            br = __ffma2_rn(num, rd, __fmul2_rn(make_float2(c16, c16), e2));
+            if (M == BR_NEAR) {
+                const float2 xg = __fmul2_rn(make_float2(-3.99915f, -3.99915f), u2);
+                const float2 g = make_float2(ex2_approx(xg.x), ex2_approx(xg.y));     // e^{-2.772 u^2}
+                br = __ffma2_rn(make_float2(omr, omr), g, br);
+            }
         }
         const float2 j2 = __ffma2_rn(aj2, br, make_float2(bj[i], bj[i + 1]));
         const float2 k2 = __ffma2_rn(ak2, br, make_float2(bk[i], bk[i + 1]));
@@ -860,15 +872,21 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
             const float4 A = sm0[q];
             const float4 B = sm1[q];
             const float lo = A.x, hi = A.y;             // window part in the tile
-            const float s = fabsf(A.w), r = B.x, aj = B.z, ak = B.w;
+            const float s = fabsf(A.w), r = fabsf(B.x), aj = B.z, ak = B.w;
             const float omr = 1.0f - r, c16 = 0.016f * r * omr;
             const float ub = A.z, ub_lo = B.y;
             if (FL & 4) sweep_pair_voigt<PPT>(c_voigt, lo, hi, lanef, s, ub, ub_lo, r, aj, ak, bj, bk);
             else if (lo <= 0.0f && hi >= (float)(TW - 1)) {   // the whole tile in the window
-                if (A.w < 0.0f) sweep_pair_full<PPT, true>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-                else sweep_pair_full<PPT, false>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-            } else if (A.w < 0.0f) sweep_pair<PPT, true>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-            else sweep_pair<PPT, false>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+                if (A.w < 0.0f) sweep_pair_full<PPT, BR_FAR>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+                else if (B.x < 0.0f) sweep_pair_full<PPT, BR_MID>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+                else sweep_pair_full<PPT, BR_NEAR>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            } else if (A.w < 0.0f) {
+                sweep_pair<PPT, BR_FAR>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            } else if (B.x < 0.0f) {
+                sweep_pair<PPT, BR_MID>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            } else {
+                sweep_pair<PPT, BR_NEAR>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+            }
         }
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
