@@ -70,13 +70,13 @@ def parse():
     return args
 
 
-# DRAM bytes (read + write) of one FP32 line-sum launch on the stagnation line
+# DRAM bytes (read + write) of one timed FP32 line-sum launch on the stagnation line
 # at full size (200 cells x 1e6 points, tiling 128 x 2), from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
 # with this digest (source_digest).  Other cell / point counts scale in proportion (the bytes are
 # the kappa / j rows written); a different source (comments aside) gives null.
 LINE_SUM_TRAFFIC = {"sha1": "f87f52f2af490b38f1ab0030a15cf40f00f184d5", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 55_842_048 + 1_546_275_840}
+                    "bytes": 58_360_320 + 1_547_189_504}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
