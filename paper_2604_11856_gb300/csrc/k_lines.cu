@@ -559,14 +559,21 @@ __device__ __forceinline__ float sinpi_series(float d) {
 // One (line, cell) pair set up for a warp's tile [kt0, kt0 + TW): window
 // offsets inside the tile (as floats), u at the tile's first point, profile
 // constants, and whether every point of the window part in the tile lies in
-// the far wings (|u| > 11, where both exponentials are zero in FP32: then s
-// is stored negated).  Everything a warp needs per pair is computed here, by
-// one lane per pair.
+// the far wings (|u| > 11, where both exponentials are zero in FP32) or past
+// the Gaussian core (|u| > 5.62).  Everything a warp needs per pair is
+// computed here, by one lane per pair.
+// Bracket modes: both exponentials; the Gaussian core zero in FP32 over the
+// span (|u| > 5.62, 2.772 u^2 log2(e) > 126); both zero (|u| > 11, also
+// 0.4 u^2.25 log2(e) > 126).  Dropping a term that ex2 flushes to zero does
+// not change a sum.
+enum { BR_NEAR = 0, BR_MID = 1, BR_FAR = 2 };
+
 struct PairF32 {
     float lo, hi;     // window part inside the tile, offsets from kt0
     float ub, ub_lo;  // signed u at kt0, (kt0 - kc) s - u0, as a float-float pair
-    float s;          // h / (2 lamV): step of u per grid point (negative: far wings only)
+    float s;          // h / (2 lamV): step of u per grid point
     float r, aj, ak;
+    int mode;         // BR_NEAR, BR_MID or BR_FAR over the window part in the tile
 };
 
 // FL: bit 0 the optional Lorentz terms, bit 1 the departure coefficients.
@@ -669,11 +676,9 @@ __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF
     const float umin = (ua > 0.0f) ? ua : (ue < 0.0f ? -ue : 0.0f);
     P->lo = lo_rel;
     P->hi = hi_rel;
-    P->s = umin > 11.0f ? -s : s;
-    // between |u| = 5.62 and 11 only the Gaussian core is zero in FP32
-    // (2.772 u^2 log2(e) > 126): r (> 0, lamL holds the natural width) is
-    // stored negated
-    P->r = (!VG && umin > 5.62f && umin <= 11.0f) ? -r : r;
+    P->s = s;
+    P->r = r;
+    P->mode = umin > 11.0f ? BR_FAR : ((!VG && umin > 5.62f) ? BR_MID : BR_NEAR);
     P->aj = Sj * pre;
     P->ak = Sk * pre;
     if (count) {
@@ -689,12 +694,6 @@ __device__ __forceinline__ bool setup_pair_f32(const LineSumArgs& a, const LineF
     }
     return true;
 }
-
-// Bracket modes: both exponentials; the Gaussian core zero in FP32 over the
-// span (|u| > 5.62, 2.772 u^2 log2(e) > 126); both zero (|u| > 11, also
-// 0.4 u^2.25 log2(e) > 126).  Dropping a term that ex2 flushes to zero leaves
-// every sum bitwise the same.
-enum { BR_NEAR = 0, BR_MID = 1, BR_FAR = 2 };
 
 // One Whiting evaluation, bracket only (the factor 1e3 / (2 lamV (1.065 +
 // 0.447 r + 0.058 r^2)) is folded into aj, ak).  Near the line centre both
@@ -794,6 +793,20 @@ __device__ __forceinline__ void sweep_pair_full(float lanef, float s, float ub, 
     }
 }
 
+// The staged pairs q0 .. q1 - 1 of one class: bracket mode M, and whether
+// their windows cover the whole tile.
+template <int PPT, int M, bool WHOLE>
+__device__ __forceinline__ void sweep_class(const float4* sm0, const float4* sm1, int q0, int q1, float lanef,
+                                            float (&bj)[PPT], float (&bk)[PPT]) {
+    for (int q = q0; q < q1; ++q) {
+        const float4 A = sm0[q];   // lo, hi, ub, s
+        const float4 B = sm1[q];   // r, ub_lo, aj, ak
+        const float r = B.x, omr = 1.0f - r, c16 = 0.016f * r * omr;
+        if (WHOLE) sweep_pair_full<PPT, M>(lanef, A.w, A.z, B.y, r, omr, c16, B.z, B.w, bj, bk);
+        else sweep_pair<PPT, M>(A.x, A.y, lanef, A.w, A.z, B.y, r, omr, c16, B.z, B.w, bj, bk);
+    }
+}
+
 // The same sweep with the exact Voigt shape: r is y, u is x.
 template <int PPT>
 __device__ __forceinline__ void sweep_pair_voigt(const VoigtCoef& vc, float lo, float hi, float lanef, float s, float ub,
@@ -818,7 +831,9 @@ __device__ __forceinline__ void sweep_pair_voigt(const VoigtCoef& vc, float lo, 
 // then sweeps them over its points.  With the points interleaved, whether a
 // pair's window reaches the i-th run of 32 points is the same for the whole
 // warp, so runs outside the window are skipped without a masked evaluation.
-// Warps never wait for each other.
+// The staged pairs are grouped by class (bracket mode, and whether the
+// window covers the whole tile, where two points go per packed FP32
+// instruction), one loop per class.  Warps never wait for each other.
 template <int PPT, int FL>
 __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
                                               float2* smlp, float2* smcb, float4* acc, int lane, int64_t* cnt) {
@@ -859,34 +874,41 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
                                        c, hf, inv_hf, kt0, kt0f, kt1f,
                                    count, &P, cnt);
         }
-        // compact the pairs that reach the tile to the front of the staging area
-        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        const int nv = __popc(vmask);
-        if (valid) {
-            const int pos = __popc(vmask & ((1u << lane) - 1u));
+        // stage the pairs that reach the tile grouped by class (bracket mode,
+        // plus 3 where the window covers the whole tile; one class with the
+        // exact Voigt shape), in lane order within a class, so the sweeps
+        // below run one loop per class with no test per pair
+        constexpr int NCLS = (FL & 4) ? 1 : 6;
+        int cls = -1;
+        if (valid) cls = (FL & 4) ? 0 : P.mode + ((P.lo <= 0.0f && P.hi >= (float)(TW - 1)) ? 3 : 0);
+        const unsigned lt = (1u << lane) - 1u;
+        int base[NCLS + 1];
+        int pos = 0;
+        base[0] = 0;
+#pragma unroll
+        for (int k = 0; k < NCLS; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, cls == k);
+            if (cls == k) pos = base[k] + __popc(m & lt);
+            base[k + 1] = base[k] + __popc(m);
+        }
+        if (cls >= 0) {
             sm0[pos] = make_float4(P.lo, P.hi, P.ub, P.s);
             sm1[pos] = make_float4(P.r, P.ub_lo, P.aj, P.ak);
         }
         __syncwarp();
-        for (int q = 0; q < nv; ++q) {
-            const float4 A = sm0[q];
-            const float4 B = sm1[q];
-            const float lo = A.x, hi = A.y;             // window part in the tile
-            const float s = fabsf(A.w), r = fabsf(B.x), aj = B.z, ak = B.w;
-            const float omr = 1.0f - r, c16 = 0.016f * r * omr;
-            const float ub = A.z, ub_lo = B.y;
-            if (FL & 4) sweep_pair_voigt<PPT>(c_voigt, lo, hi, lanef, s, ub, ub_lo, r, aj, ak, bj, bk);
-            else if (lo <= 0.0f && hi >= (float)(TW - 1)) {   // the whole tile in the window
-                if (A.w < 0.0f) sweep_pair_full<PPT, BR_FAR>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-                else if (B.x < 0.0f) sweep_pair_full<PPT, BR_MID>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-                else sweep_pair_full<PPT, BR_NEAR>(lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-            } else if (A.w < 0.0f) {
-                sweep_pair<PPT, BR_FAR>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-            } else if (B.x < 0.0f) {
-                sweep_pair<PPT, BR_MID>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
-            } else {
-                sweep_pair<PPT, BR_NEAR>(lo, hi, lanef, s, ub, ub_lo, r, omr, c16, aj, ak, bj, bk);
+        if (FL & 4) {
+            for (int q = 0; q < base[NCLS]; ++q) {
+                const float4 A = sm0[q];
+                const float4 B = sm1[q];
+                sweep_pair_voigt<PPT>(c_voigt, A.x, A.y, lanef, A.w, A.z, B.y, B.x, B.z, B.w, bj, bk);
             }
+        } else {
+            sweep_class<PPT, BR_NEAR, false>(sm0, sm1, base[0], base[1], lanef, bj, bk);
+            sweep_class<PPT, BR_MID, false>(sm0, sm1, base[1], base[2], lanef, bj, bk);
+            sweep_class<PPT, BR_FAR, false>(sm0, sm1, base[2], base[3], lanef, bj, bk);
+            sweep_class<PPT, BR_NEAR, true>(sm0, sm1, base[3], base[4], lanef, bj, bk);
+            sweep_class<PPT, BR_MID, true>(sm0, sm1, base[4], base[5], lanef, bj, bk);
+            sweep_class<PPT, BR_FAR, true>(sm0, sm1, base[5], base[6], lanef, bj, bk);
         }
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
