@@ -45,3 +45,35 @@ def test_workspace_query_is_host_only():
 def test_no_cpu_fallback():
     with pytest.raises(RuntimeError, match="CUDA"):
         R.Context(0)
+
+
+def test_noalloc_entry_point_rejects_bad_arguments_before_any_cuda_call():
+    """The allocation-free entry point checks its host arguments first: null
+    arrays and impossible sizes come back as RAPRAL_EINVAL with a message,
+    without touching a device (this runs on a machine with none)."""
+    lib = R.load()
+    f = lib.rapral_spectral_coeffs_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(R.Species), ctypes.POINTER(R.Lines), ctypes.POINTER(R.Cells),
+                  ctypes.POINTER(R.Grid), ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_char_p, ctypes.c_size_t]
+    err = ctypes.create_string_buffer(256)
+    sp, ln, ce = R.Species(), R.Lines(), R.Cells()
+    fake = ctypes.c_void_p(16)   # never dereferenced: every case below fails a host check first
+    assert f(None, None, None, None, None, 0, 1, R.FP32, None, None, 1, err, 256) == 1
+    assert b"null" in err.value
+    sp.n_species, ce.n_cells, ce.n_cols, ce.ne_col, ce.lnpref = 11, 4, 11, 10, 16
+
+    def call(grid, k0=0, nk=10, precision=R.FP32, ld=10):
+        err.value = b""
+        return f(None, ctypes.byref(sp), ctypes.byref(ln), ctypes.byref(ce), ctypes.byref(grid), k0, nk, precision,
+                 fake, fake, ld, err, 256)
+
+    bad = [dict(grid=R.Grid(50.0, 100.0, 1)),                     # fewer than two grid points
+           dict(grid=R.Grid(100.0, 50.0, 100)),                   # empty wavelength range
+           dict(grid=R.Grid(50.0, 100.0, 100), k0=95, nk=10),     # range past the grid's end
+           dict(grid=R.Grid(50.0, 100.0, 100), ld=5),             # row stride below the range
+           dict(grid=R.Grid(50.0, 100.0, 100), precision=7)]      # unknown precision
+    for case in bad:
+        assert call(**case) == 1, case
+        assert err.value, case
