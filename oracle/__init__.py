@@ -68,10 +68,13 @@ class _Grid(ct.Structure):
 
 
 def lib():
+    """The oracle library, built on first use.  RAPRAL_ORACLE_LIB names a
+    different build of the same source to load instead: the mutation tests use
+    it to run the pins against copies with planted mistakes."""
     global _lib
     with _lock:
         if _lib is None:
-            _lib = ct.CDLL(build())
+            _lib = ct.CDLL(os.environ.get("RAPRAL_ORACLE_LIB") or build())
             d, i64, i32, vp = ct.c_double, ct.c_int64, ct.c_int32, ct.c_void_p
             P = ct.POINTER
             sig = {

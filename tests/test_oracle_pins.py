@@ -333,6 +333,29 @@ def test_windowed_sum_equals_brute_force():
                 assert kap[c, k - k0] == pytest.approx(math.fsum(tk), rel=1e-15, abs=1e-300)
 
 
+def test_window_is_fifty_full_widths_each_side():
+    """The line wings are cut at |lam - lam0| = 100 lamV, fifty Voigt FWHM on
+    each side (reading A3).  One line whose window lies inside a fine grid:
+    its emission summed over the grid, divided by its strength, is the area of
+    Whiting's shape over exactly that interval (Simpson, independent of the
+    oracle's window test).  A cut at 50 lamV would lose about 0.6 % of it."""
+    p = synth.uniform_slab(n_lines=1, n_cells=1, n_grid=8001, lam=(53.0, 57.0), seed=11)
+    p.lines.lam0[:] = 55.0
+    p.lines.lamS0[:] = 0.008           # Stark-dominated: lamV ~ 0.0085 nm at n_e = 1e16
+    p.cells.n[:, synth.NE_COL] = 1e16
+    lnp = oracle.lnpref(p)
+    st = oracle.line_states(p, lnp, 0)
+    lamL, lamV, Sj = st["lamL"][0], st["lamV"][0], st["Sj"][0]
+    h = (p.grid.lam_max - p.grid.lam_min) / (p.grid.n - 1)
+    assert 100 * lamV < 2.0 - 2 * h and lamV / h > 10     # window inside the grid, well resolved
+    _, em = oracle.spectral_coeffs(p, lnp)
+    area_grid = em[0].sum() * h * 1e-3 / Sj            # um^-1 x um
+    area_100 = _simpson_area(lambda x: L.orc_whiting_phi(x, lamL, lamV), 100 * lamV, n=400_001) * 1e-3
+    area_50 = _simpson_area(lambda x: L.orc_whiting_phi(x, lamL, lamV), 50 * lamV, n=400_001) * 1e-3
+    assert area_grid == pytest.approx(area_100, rel=1e-5)     # measured 7e-8
+    assert abs(area_100 / area_50 - 1) > 1e-3                 # 6.4e-3
+
+
 def test_coeffs_at_points_matches_full_table():
     p = synth.uniform_slab(n_lines=200, n_cells=2, n_grid=5000, seed=9)
     lnp = oracle.lnpref(p)
