@@ -45,6 +45,24 @@ def test_fibonacci_neighbours_are_evenly_spaced():
     assert nn.min() > 0.3 * spacing
 
 
+def test_fibonacci_azimuths_turn_by_the_golden_angle():
+    """A Fibonacci sphere lattice turns each point by the golden angle
+    2 pi / phi^2 (phi = (1 + sqrt 5) / 2) about the pole axis and steps the
+    polar coordinate w uniformly from 1 to -1; the azimuth of direction i is
+    atan2(dt, dx) here (Sec. 2.2.3)."""
+    n = 257
+    d = los.fibonacci_directions(n)
+    phi = (1.0 + 5.0 ** 0.5) / 2.0
+    golden = 2.0 * np.pi / phi ** 2
+    az = np.arctan2(d[:, 2], d[:, 0])
+    inner = slice(1, n - 1)                     # the poles have no azimuth
+    turn = np.diff(az[inner])
+    off = np.minimum(np.abs((turn - golden + np.pi) % (2 * np.pi) - np.pi),
+                     np.abs((turn + golden + np.pi) % (2 * np.pi) - np.pi))
+    assert np.max(off) < 1e-9
+    np.testing.assert_allclose(d[:, 1], np.linspace(1.0, -1.0, n), rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("n", [64, 400, 401])
 def test_valid_los_leave_the_body(n):
     keep = los.valid_los(n)

@@ -1,12 +1,18 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case plants one mistake in a copy of oracle/rapral_oracle.cpp (a flipped
-sign, a swapped coefficient, a wrong temperature, a dropped term, a changed
-constant), builds the copy with the oracle's own flags, and runs
-tests/test_oracle_pins.py against it (RAPRAL_ORACLE_LIB).  At least one pin
-must fail for every mistake.  CPU only: nothing here touches a GPU."""
+Each case plants one mistake in a copy of the oracle (a flipped sign, a
+swapped coefficient, a wrong temperature, a dropped term, a changed
+constant) and runs the pins against the copy; at least one pin must fail for
+every mistake.  Mistakes in oracle/rapral_oracle.cpp are built with the
+oracle's own flags and loaded through RAPRAL_ORACLE_LIB by
+tests/test_oracle_pins.py.  Mistakes in the numpy modules (QSS populations,
+continuum, exact Voigt shape, the Fibonacci angular path) go into a copy of
+the oracle package in a scratch tree, where that module's pin file runs.
+CPU only: nothing here touches a GPU."""
 import concurrent.futures as cf
+import glob
 import os
+import shutil
 import subprocess
 import sys
 
@@ -90,3 +96,76 @@ def test_unmutated_copy_passes_the_pins(tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-q", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+# (module, name, text in the module, planted mistake, pin file).  Not here: the
+# A1 / sigma term of the Table 3 free-free fit.  It is at most ~7 % of the fit
+# over 100-2000 nm, inside the Kramers-Gaunt band that is the only check
+# independent of the printed formula, so no pin can tell it from A1 sigma.
+PY_MUTATIONS = [
+    ("qss.py", "detailed balance inverted (Sec. 2.1)",
+     "kh_dn = kh_up * Qh[i] / Qh[j]", "kh_dn = kh_up * Qh[j] / Qh[i]", "test_oracle_qss_pins.py"),
+    ("qss.py", "three-body recombination by the wrong partition ratio (Sec. 2.1)",
+     "kr = kf * Qe_lv[i] / (Qp * Qel)", "kr = kf * Qe_lv[i] * Qp / Qel", "test_oracle_qss_pins.py"),
+    ("qss.py", "closure without the lumped levels' Boltzmann ratio (Sec. 2.1)",
+     "1.0 + np.sum(Qe_lv[l:]) / Qe_lv[l - 1]", "1.0 + np.sum(Qe_lv[l:])", "test_oracle_qss_pins.py"),
+    ("continuum.py", "free-free emission without the Planck factor (Kirchhoff, Sec. 2.2.1)",
+     "em + planck(lam, T) * kff", "em + kff", "test_oracle_continuum_pins.py"),
+    ("continuum.py", "bound-free emission, sign of the ionisation gap (Sec. 2.2.1)",
+     "+ C2 * (model[\"E_ion\"] - model[\"E\"][i]) / T", "- C2 * (model[\"E_ion\"] - model[\"E\"][i]) / T",
+     "test_oracle_continuum_pins.py"),
+    ("continuum.py", "free-free correction D with the wrong sign (Sec. 2.2.1)",
+     "* (1.0 + D)", "* (1.0 - D)", "test_oracle_continuum_pins.py"),
+    ("continuum.py", "cross sections extrapolated past the table edge (Sec. 2.2.1)",
+     "left=0.0, right=0.0", "left=None, right=None", "test_oracle_continuum_pins.py"),
+    ("continuum.py", "Saha factor without the electron spin weight 2 (Sec. 2.1)",
+     "- np.log(2.0 * ion_Q(m, T))", "- np.log(ion_Q(m, T))", "test_oracle_continuum_pins.py"),
+    ("voigt.py", "Gaussian sigma from the half width (Sec. 2.2.1)",
+     "sig = lamG / np.sqrt(2.0 * np.log(2.0))", "sig = lamG / np.sqrt(np.log(2.0))", "test_oracle_voigt_pins.py"),
+    ("voigt.py", "Voigt normalisation (Sec. 2.2.1)",
+     "(sig * np.sqrt(2.0 * np.pi))", "(sig * np.sqrt(np.pi))", "test_oracle_voigt_pins.py"),
+    ("voigt.py", "Lorentz half width doubled in the Faddeeva argument (Sec. 2.2.1)",
+     "1j * lamL", "1j * 2.0 * lamL", "test_oracle_voigt_pins.py"),
+    ("los.py", "Fibonacci azimuth step (Sec. 2.2.3)",
+     "(np.sqrt(5.0) - 1.0) * np.pi", "(np.sqrt(5.0) - 1.0) * 0.5 * np.pi", "test_oracle_los_pins.py"),
+    ("los.py", "four-point sum with the printed weight (Sec. 2.2.3, reading F5)",
+     "0.5 * (np.cos(phi[p]) ** 2 - np.cos(phi[p + 1]) ** 2)", "(np.cos(phi[p + 1]) - np.cos(phi[p]))",
+     "test_oracle_los_pins.py"),
+    ("los.py", "azimuth grid spacing (Sec. 2.2.3)",
+     "2.0 * np.pi * np.arange(n_theta) / (n_theta - 1)", "2.0 * np.pi * np.arange(n_theta) / n_theta",
+     "test_oracle_los_pins.py"),
+]
+
+
+def _run_py(idx, case, tmp, lib):
+    module, name, old, new, pins = case
+    root = os.path.join(tmp, f"tree{idx}")
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(root, "oracle"),
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    pkg = os.path.join(root, "paper_2604_11856_gb300")
+    os.makedirs(pkg)
+    for f in glob.glob(os.path.join(ROOT, "paper_2604_11856_gb300", "*.py")):
+        shutil.copy(f, pkg)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(root, "tests", "golden"))
+    for f in ("conftest.py", pins):
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(root, "tests", f))
+    path = os.path.join(root, "oracle", module)
+    src = open(path).read()
+    assert src.count(old) == 1, f"mutation site not unique or missing: {name}"
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    env = dict(os.environ, RAPRAL_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", pins), "-x", "-q", "-p",
+                        "no:cacheprovider"], cwd=root, env=env, capture_output=True, text=True)
+    return name, r.returncode, r.stdout[-400:]
+
+
+def test_every_planted_mistake_in_the_numpy_modules_fails_a_pin(tmp_path):
+    import oracle
+    lib = oracle.build()
+    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+        results = list(ex.map(lambda ic: _run_py(ic[0], ic[1], str(tmp_path), lib), enumerate(PY_MUTATIONS)))
+    survived = [(name, out) for name, rc, out in results if rc == 0]
+    assert not survived, "mistakes no pin caught:\n" + "\n".join(f"{n}\n{o}" for n, o in survived)
+    broken = [(name, rc, out) for name, rc, out in results if rc not in (0, 1)]
+    assert not broken, broken
