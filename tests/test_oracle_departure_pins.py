@@ -83,3 +83,24 @@ def test_upper_level_departure_linear_in_j_affine_in_kappa():
     np.testing.assert_allclose(j3 - j1, 2 * dj, rtol=1e-9, atol=1e-30 * j1.max())
     # kappa: affine in b (lines with level 5 as upper or lower level)
     np.testing.assert_allclose(k3 - k2, k2 - k1, rtol=1e-8, atol=1e-12 * np.abs(k1).max())
+
+
+def test_lower_level_departure_moves_kappa_only():
+    """A line absorbs from its lower level and emits from its upper one
+    (Sec. 2.2.1): a departure on the lower level alone leaves j unchanged and
+    scales the absorbing part of kappa, so kappa grows with b, affinely."""
+    p, m, lu, ll = _problem()
+    s = synth.RAD_SPECIES.index("N")
+    sel = (ll == 5) & (lu != 5)
+    assert sel.sum() >= 1
+    only = synth.Lines(**{k: getattr(p.lines, k)[sel] for k in synth.Lines.__dataclass_fields__})
+    p2 = synth.Problem("cr", p.species, only, p.cells, p.grid, p.geometry, chunk=0)
+    out = []
+    for b in (1.0, 2.0, 3.0):
+        ln_b = np.zeros((len(p.cells), 8, m["l"]))
+        ln_b[:, s, 5] = np.log(b)
+        out.append(_coeffs(p2, ln_b, lu[sel], ll[sel]))
+    (k1, j1), (k2, j2), (k3, j3) = out
+    assert np.array_equal(j1, j2) and np.array_equal(j1, j3)
+    assert np.all(k2 >= k1) and (k2 > k1).any()
+    np.testing.assert_allclose(k3 - k2, k2 - k1, rtol=1e-8, atol=1e-12 * np.abs(k1).max())

@@ -22,7 +22,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "rapral_oracle.cpp")
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
-# (name, text in the oracle, planted mistake)
+# (name, text in the oracle, planted mistake[, pin file; test_oracle_pins.py by default])
 MUTATIONS = [
     ("whiting correction sign (Sec. 2.2.1)",
      "+ 0.016 * r * (1.0 - r)", "- 0.016 * r * (1.0 - r)"),
@@ -57,11 +57,27 @@ MUTATIONS = [
      "(1e4 * std::pow(lcm, 5) * std::expm1(x))", "(1e4 * std::pow(lcm, 4) * std::expm1(x))"),
     ("emission strength prefactor hc/4pi (Sec. 2.2.1)",
      "(hP * cL / (4.0 * M_PI))", "(hP * cL / (2.0 * M_PI))"),
+    ("Stark coefficient, exponent of the ionisation gap (Sec. 2.2.1)",
+     "std::pow(dE, 2.623)", "std::pow(dE, 2.5)", "test_oracle_broadening_pins.py"),
+    ("Stark coefficient, floor of the ionisation gap (Sec. 2.2.1)",
+     "E_IONIZE_H / 25.0", "E_IONIZE_H / 16.0", "test_oracle_broadening_pins.py"),
+    ("oscillator strength with the weights inverted (Sec. 2.2.1)",
+     "* gu / gl * A;", "* gl / gu * A;", "test_oracle_broadening_pins.py"),
+    ("resonance width, weight ratio inverted (Sec. 2.2.1)",
+     "std::sqrt(gl / gu)", "std::sqrt(gu / gl)", "test_oracle_broadening_pins.py"),
+    ("van der Waals width without the factor 2 in the speed (Sec. 2.2.1)",
+     "6.65e-29 * N * std::sqrt(2.0 * Ttr / M)", "6.65e-29 * N * std::sqrt(Ttr / M)",
+     "test_oracle_broadening_pins.py"),
+    ("departure of the lower level taken from the upper level's index (Sec. 2.1)",
+     "departure(sp, c, s, DEP_LEV_L, l)", "departure(sp, c, s, DEP_LEV_U, l)", "test_oracle_departure_pins.py"),
+    ("departure of the upper level with the wrong sign (Sec. 2.1)",
+     "departure(sp, c, s, DEP_LEV_U, l);", "-departure(sp, c, s, DEP_LEV_U, l);", "test_oracle_departure_pins.py"),
 ]
 
 
 def _run(case, tmp):
-    name, old, new = case
+    name, old, new = case[:3]
+    pins = os.path.join(ROOT, "tests", case[3]) if len(case) > 3 else PINS
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site not unique or missing: {name}"
     tag = str(MUTATIONS.index(case))
@@ -72,7 +88,7 @@ def _run(case, tmp):
     subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", cpp, "-o", so],
                    check=True)
     env = dict(os.environ, RAPRAL_ORACLE_LIB=so, OMP_NUM_THREADS="2")
-    r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider"],
+    r = subprocess.run([sys.executable, "-m", "pytest", pins, "-x", "-q", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True)
     return name, r.returncode, r.stdout[-400:]
 
@@ -107,6 +123,10 @@ PY_MUTATIONS = [
      "kh_dn = kh_up * Qh[i] / Qh[j]", "kh_dn = kh_up * Qh[j] / Qh[i]", "test_oracle_qss_pins.py"),
     ("qss.py", "three-body recombination by the wrong partition ratio (Sec. 2.1)",
      "kr = kf * Qe_lv[i] / (Qp * Qel)", "kr = kf * Qe_lv[i] * Qp / Qel", "test_oracle_qss_pins.py"),
+    ("qss.py", "electron-impact rates at the translational temperature (Sec. 2.1, reading Q2)",
+     'theta, Tve)\n        ke_dn', 'theta, Ttr)\n        ke_dn', "test_oracle_qss_pins.py"),
+    ("qss.py", "VUV lines not trapped (escape factor, Sec. 2.1 reading Q4)",
+     "(1.0 if model[\"lam\"][t] >= 200.0 else 0.0)", "1.0", "test_oracle_qss_pins.py"),
     ("qss.py", "closure without the lumped levels' Boltzmann ratio (Sec. 2.1)",
      "1.0 + np.sum(Qe_lv[l:]) / Qe_lv[l - 1]", "1.0 + np.sum(Qe_lv[l:])", "test_oracle_qss_pins.py"),
     ("continuum.py", "free-free emission without the Planck factor (Kirchhoff, Sec. 2.2.1)",

@@ -33,6 +33,22 @@ def test_detailed_balance_without_radiation_gives_boltzmann(lumped):
         np.testing.assert_allclose(n, _boltzmann(m, T, 1e16), rtol=1e-10)
 
 
+@pytest.mark.parametrize("kind", ["electrons", "heavy"])
+def test_each_collision_partner_thermalises_at_its_own_temperature(kind):
+    """Two temperatures, no radiation and no ionisation: with electron
+    collisions alone the levels take the Boltzmann distribution at T_ve, with
+    heavy-particle collisions alone at T_tr (Sec. 2.1: electron rates at the
+    electron temperature, heavy-particle rates at the translational one)."""
+    m = synth.cr_model(n_levels=10)
+    m["A"][:] = 0.0
+    m["ii_C"][:] = 0.0
+    m["hp_C" if kind == "electrons" else "e_C"][:] = 0.0
+    st = dict(Ttr=6000.0, Tve=12000.0, n_M=1e17, n_e=1e15, n_ion=0.0, n_total=1e16)
+    n = _solve(m, st)
+    T = st["Tve"] if kind == "electrons" else st["Ttr"]
+    np.testing.assert_allclose(n, _boltzmann(m, T, 1e16), rtol=1e-10)
+
+
 def test_saha_consistent_ions_keep_boltzmann():
     m = synth.cr_model(n_levels=10)
     m["A"][:] = 0.0
@@ -67,6 +83,27 @@ def test_closure_and_two_level_closed_form():
     m["lam"][:] = 150.0
     n = _solve(m, st)
     assert abs(n[1] / n[0] / (Q[1] / Q[0]) - 1) < 1e-12
+
+
+def test_two_level_closed_form_at_two_temperatures():
+    """Two temperatures and both partners: the two-level balance
+    n1 / n0 = (heavy up + electron up) / (heavy down + electron down + A), with
+    heavy-particle rates at T_tr and electron rates at T_ve (Sec. 2.1), and each
+    downward rate from its upward one by detailed balance at the partner's
+    temperature."""
+    m = synth.cr_model(n_levels=2)
+    m["ii_C"][:] = 0.0
+    m["A"][:] = 3e7
+    m["lam"][:] = 500.0
+    Ttr, Tve, n_M, n_e = 6000.0, 14000.0, 1e16, 1e14
+    n = _solve(m, dict(Ttr=Ttr, Tve=Tve, n_M=n_M, n_e=n_e, n_ion=0.0, n_total=1e16))
+    th = qss.C2 * (m["E"][1] - m["E"][0])
+    kh = m["hp_C"][0] * Ttr ** m["hp_n"][0] * np.exp(-th / Ttr)
+    ke = m["e_C"][0] * Tve ** m["e_n"][0] * np.exp(-th / Tve)
+    Qh, Qe = qss.level_Q(m, Ttr), qss.level_Q(m, Tve)
+    up = (kh * n_M + ke * n_e) / qss.N_A
+    dn = (kh * Qh[0] / Qh[1] * n_M + ke * Qe[0] / Qe[1] * n_e) / qss.N_A + 3e7
+    assert abs(n[1] / n[0] / (up / dn) - 1) < 1e-12
 
 
 def test_collisions_win_at_high_density():
