@@ -70,6 +70,12 @@ MUTATIONS = [
      "test_oracle_broadening_pins.py"),
     ("departure of the lower level taken from the upper level's index (Sec. 2.1)",
      "departure(sp, c, s, DEP_LEV_L, l)", "departure(sp, c, s, DEP_LEV_U, l)", "test_oracle_departure_pins.py"),
+    ("ln(N_s / Z_s) with the partition function multiplied in (Sec. 2.1)",
+     "std::log(N) - std::log(Z);", "std::log(N) + std::log(Z);"),
+    ("rotational sum multiplied by the symmetry number instead of divided (Sec. 2.1)",
+     "* rot / sp->st_sigma[i];", "* rot * sp->st_sigma[i];"),
+    ("ray's radial distance with the body radius dropped (ray-cell segments)",
+     "const double y = r_body + t * dn, z = t * dt;", "const double y = t * dn, z = t * dt;"),
     ("departure of the upper level with the wrong sign (Sec. 2.1)",
      "departure(sp, c, s, DEP_LEV_U, l);", "-departure(sp, c, s, DEP_LEV_U, l);", "test_oracle_departure_pins.py"),
 ]
@@ -140,6 +146,9 @@ PY_MUTATIONS = [
      "left=0.0, right=0.0", "left=None, right=None", "test_oracle_continuum_pins.py"),
     ("continuum.py", "Saha factor without the electron spin weight 2 (Sec. 2.1)",
      "- np.log(2.0 * ion_Q(m, T))", "- np.log(ion_Q(m, T))", "test_oracle_continuum_pins.py"),
+    ("continuum.py", "Saha-Boltzmann populations, thermal de Broglie exponent (Sec. 2.1)",
+     "+ 1.5 * np.log(H * H / (2.0 * np.pi * ME * KB * T)) + C2 * E_ion / T",
+     "+ 1.0 * np.log(H * H / (2.0 * np.pi * ME * KB * T)) + C2 * E_ion / T", "test_oracle_continuum_pins.py"),
     ("voigt.py", "Gaussian sigma from the half width (Sec. 2.2.1)",
      "sig = lamG / np.sqrt(2.0 * np.log(2.0))", "sig = lamG / np.sqrt(np.log(2.0))", "test_oracle_voigt_pins.py"),
     ("voigt.py", "Voigt normalisation (Sec. 2.2.1)",
