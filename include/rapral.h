@@ -258,8 +258,10 @@ RAPRAL_API int rapral_populations(rapral_ctx* ctx, const rapral_species* sp,
  * Out: kappa, emis [C][ld] (columns 0 .. nk-1 written), FP64 or FP32 per
  * `precision`.  ld >= nk.  Lines are binned into spectral tiles on the
  * device first (workspace).  Errors: EINVAL (k0 + nk > n, nk < 1, ld < nk,
- * n < 2, lam_max <= lam_min; device: species index out of range, lam0 <= 0,
- * g <= 0), ENOMEM (workspace), ECUDA. */
+ * n < 2, lam_max <= lam_min or not finite; line windows that give more than
+ * 2^31 - 1 (line, tile) entries, the limit of the tile lists' int32 offsets,
+ * before anything is filled: split the range; device: species index out of
+ * range, lam0 <= 0, g <= 0), ENOMEM (workspace), ECUDA. */
 RAPRAL_API int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp,
                            const rapral_lines* lines, const rapral_cells* cells,
                            const rapral_grid* grid, int64_t k0, int64_t nk,
@@ -350,9 +352,13 @@ RAPRAL_API void rapral_batch_destroy(rapral_batch* batch);
  * cannot call cudaMalloc; this entry point needs neither a context nor a
  * workspace.  Its scratch is one static device array
  * of 64 MiB inside the library, held by every GPU that loads the library
- * until the process exits.  The first call on a device looks the array's
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the array and clears what must start at zero;
+ * until the process exits.  The call runs on the device that owns
+ * `cuda_stream` (for the legacy default stream, the current device): it makes
+ * that device current while it runs and restores the caller's current device
+ * before it returns.  The first call on a device, and the first after that
+ * device's context was reset, looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and clears what must start at zero;
  * calls that overlap on the GPU (other streams, unordered host threads) race
  * on it, so serialise them.  The call synchronises `cuda_stream` once (to
  * read the input checks and the tile-list length) and then enqueues the line
@@ -360,8 +366,8 @@ RAPRAL_API void rapral_batch_destroy(rapral_batch* batch);
  * widths (512 FP64, 128 FP32), paper constants.  Arguments as rapral_spectral_coeffs, plus an optional
  * caller buffer `err` (err_len bytes) for a message.  Errors: EINVAL (sizes,
  * ranges, failed device-side input checks), ENOMEM (the problem needs more
- * than the 64 MiB scratch: about 230 bytes per line plus 64 per cell and the
- * tile lists), ECUDA. */
+ * than the 64 MiB scratch: about 230 bytes per line plus 64 per cell and 4
+ * per (line, tile) entry of the tile lists), ECUDA. */
 RAPRAL_API int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_species* sp,
                                               const rapral_lines* lines, const rapral_cells* cells,
                                               const rapral_grid* grid, int64_t k0, int64_t nk,

@@ -108,6 +108,7 @@ def lib():
                 "orc_vdw_hwhm": (d, [d, d, d, d, d, d]),
                 "orc_spectral_integral": (d, [vp, P(_Grid), i64, i64]),
                 "orc_segment_coeffs": (None, [d, d, d, P(d), P(d)]),
+                "orc_last_evaluations": (i64, []),
                 "orc_num_threads": (ct.c_int, []),
                 "orc_set_threads": (None, [ct.c_int]),
             }
@@ -254,6 +255,28 @@ def line_states(problem, lnp, cell):
     lnp = np.ascontiguousarray(lnp, np.float64)
     lib().orc_line_states(ct.byref(sp), ct.byref(ln), ct.byref(ce), _p(lnp), int(cell), *[_p(o) for o in out])
     return dict(Sj=out[0], Sk=out[1], lamG=out[2], lamL=out[3], lamV=out[4])
+
+
+def last_evaluations():
+    """In-window (line, cell, grid point) triples the last spectral_coeffs
+    call evaluated the profile at."""
+    return int(lib().orc_last_evaluations())
+
+
+def line_widths_all_cells(problem, lnp):
+    """HWHMs (G, L, V) of every line in every cell, [C, L] each (for short
+    line lists: one orc_line_states call per cell)."""
+    keep = _Keep()
+    sp = species_struct(problem.species, keep)
+    ln = lines_struct(problem.lines, keep)
+    ce = cells_struct(problem.cells, keep)
+    C, L = len(problem.cells), len(problem.lines)
+    lnp = np.ascontiguousarray(lnp, np.float64)
+    out = [np.zeros((C, L)) for _ in range(5)]
+    f = lib().orc_line_states
+    for c in range(C):
+        f(ct.byref(sp), ct.byref(ln), ct.byref(ce), _p(lnp), c, *[_p(o[c]) for o in out])
+    return dict(lamG=out[2], lamL=out[3], lamV=out[4])
 
 
 def spectral_coeffs(problem, lnp=None, k0=0, nk=None, with_abs=False):
@@ -403,16 +426,21 @@ def solve_slab(problem, k0=0, nk=None, coeffs=None, thin=THIN_FP64):
     return out
 
 
-def solve_axisym_points(problem, points, kappa, emis, k0=0, thin=THIN_FP64):
+def solve_axisym_points(problem, points, kappa, emis, k0=0, thin=THIN_FP64, rows=None):
     """Afterbody rays of the given surface points over the columns of the
     (kappa, emis) tables (which cover grid points [k0, k0 + ncol)):
-    q_lambda[p] = sum_rays w_m mu_m dphi I, and the chunk's flux part."""
+    q_lambda[p] = sum_rays w_m mu_m dphi I, and the chunk's flux part.
+    Row c of the tables belongs to cell c, or, with `rows` (an array over the
+    grid's cells), to the cells c with rows[c] = that row (tables of only the
+    cells the rays cross)."""
     geo = problem.geometry
     dirs, wts = hemisphere_directions(geo)
     qlam = np.zeros((len(points), kappa.shape[1]))
     for ip, p in enumerate(points):
         for d, w in zip(dirs, wts):
             cells, ds = axisym_segments(geo, geo.surf_x[p], d)
+            if rows is not None:
+                cells = rows[cells]
             qlam[ip] += w * march(cells, ds, 1.0, kappa, emis, problem.grid, k0, False, 0.0, thin)
     q = np.array([spectral_integral(qlam[i], problem.grid, k0) for i in range(len(points))])
     return qlam, q

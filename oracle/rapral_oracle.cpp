@@ -358,6 +358,12 @@ static inline void neumaier(double& s, double& comp, double x) {
     s = t;
 }
 
+// Number of in-window (line, cell, grid point) triples the last
+// orc_spectral_coeffs call evaluated the profile at (a count of work, not a
+// step of the method).
+static int64_t LAST_EVALUATIONS = 0;
+int64_t orc_last_evaluations(void) { return LAST_EVALUATIONS; }
+
 // Line-by-line sums over the grid points [k0, k0 + nk) for every cell:
 //   j_k = sum_lines j0 phi(|lam_k - lam0|), kappa_k = sum_lines kappa0 phi(...),
 // in-window lines only, lines visited in list order.  Outputs [C][nk].
@@ -366,7 +372,8 @@ void orc_spectral_coeffs(const orc_species* sp, const orc_lines* ln, const orc_c
                          const double* lnpref, const orc_grid* g, int64_t k0, int64_t nk,
                          double* kappa, double* emis, double* kabs) {
     const double h = grid_h(g);
-#pragma omp parallel
+    int64_t evaluations = 0;
+#pragma omp parallel reduction(+ : evaluations)
     {
         std::vector<double> sk(nk), ck(nk), sj(nk), cj(nk), sa(nk);
 #pragma omp for schedule(dynamic, 1)
@@ -386,6 +393,7 @@ void orc_spectral_coeffs(const orc_species* sp, const orc_lines* ln, const orc_c
                 for (int64_t k = a; k <= b; ++k) {
                     const double lk = grid_lam(g, k);
                     if (!orc_in_window(lk, lam0, st.lamV)) continue;
+                    ++evaluations;
                     const double phi = orc_whiting_phi(std::fabs(lk - lam0), st.lamL, st.lamV);
                     neumaier(sj[k - k0], cj[k - k0], st.Sj * phi);
                     neumaier(sk[k - k0], ck[k - k0], st.Sk * phi);
@@ -399,6 +407,7 @@ void orc_spectral_coeffs(const orc_species* sp, const orc_lines* ln, const orc_c
             }
         }
     }
+    LAST_EVALUATIONS = evaluations;
 }
 
 // The same sums at individual (cell, k) points, each over the whole line list.

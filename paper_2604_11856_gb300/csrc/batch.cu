@@ -45,8 +45,7 @@ static int check_item(rapral_ctx* ctx, const rapral_batch_item& it, int i) {
     if (!it.species || !it.lines || !it.cells || !it.grid || !it.rays || !it.kappa || !it.emis || !it.q_lambda || !it.q)
         return set_error(ctx, RAPRAL_EINVAL, "request %d: null argument", i);
     const rapral_grid* g = it.grid;
-    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || it.k0 < 0 || it.nk < 1 ||
-        it.k0 + it.nk > g->n || it.ld < it.nk)
+    if (grid_problem(g) || !range_in_grid(g, it.k0, it.nk) || it.ld < it.nk)
         return set_error(ctx, RAPRAL_EINVAL, "request %d: grid, range or ld", i);
     if (it.lines->n_lines < 1 || it.lines->n_lines > 2147483647LL || it.cells->n_cells < 1 || !it.cells->lnpref ||
         it.cells->n_cols < 1 || it.cells->ne_col < 0 || it.cells->ne_col >= it.cells->n_cols ||
@@ -117,8 +116,8 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     std::vector<BroadTabs> btabs(n_items);
     const Phys ph = make_phys(ctx->codata);
     static const int one = 1;
-    int* h_tot = nullptr;
-    e = cudaMallocHost(&h_tot, sizeof(int) * n_items);
+    long long* h_tot = nullptr;   // [n_items] tile-list lengths, then the status word
+    e = cudaMallocHost(&h_tot, sizeof(long long) * (n_items + 1));
     for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
         BatchReq& r = B->req[i];
         const int64_t L = r.ln.n_lines, C = r.cells.n_cells, T = (r.nk + W - 1) / W;
@@ -132,6 +131,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         pl.tile_off = ar.take<int>(T + 1);
         unsigned long long* dmax = ar.take<unsigned long long>(RAPRAL_DMAX_SLOTS + 2);
         pl.wmax = dmax + RAPRAL_DMAX_SLOTS;
+        pl.total = reinterpret_cast<long long*>(dmax + RAPRAL_DMAX_SLOTS + 1);
         pl.sorted_flag = ar.take<int>(4);
         const bool bt = broad_terms(&ctx->broad);
         BroadTabs& bb = btabs[i];
@@ -152,12 +152,27 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         if (e == cudaSuccess) e = launch_bin_bounds(ctx, &r.ln, lps[i], cps[i], dmax, r.h, &pl, bb.lb);
         if (e == cudaSuccess) e = launch_bin_count(ctx, &r.ln, &r.grid, r.h, &pl);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h_tot + i, pl.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+            e = cudaMemcpyAsync(h_tot + i, pl.total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream);
     }
+    // the device checks ran before the counts: on a failed one the counts were never written
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_tot + n_items, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && reinterpret_cast<const int*>(h_tot + n_items)[ST_CODE] != RAPRAL_OK) {
+        cudaFreeHost(h_tot);
+        rapral_batch_destroy(B);
+        return read_status(ctx);
+    }
     size_t csr_need = 0;
     std::vector<size_t> csr_base(n_items);
     for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+        if (h_tot[i] > RAPRAL_MAX_TILE_ENTRIES) {
+            cudaFreeHost(h_tot);
+            rapral_batch_destroy(B);
+            return set_error(ctx, RAPRAL_EINVAL,
+                             "request %d: the line windows give %lld (line, tile) entries, more than the 2^31 - 1 "
+                             "the tile lists index", i, h_tot[i]);
+        }
         csr_base[i] = csr_need;
         csr_need += (size_t)h_tot[i] + 1;
     }

@@ -225,12 +225,11 @@ int rapral_populations(rapral_ctx* ctx, const rapral_species* sp, const rapral_c
 }
 
 static int check_grid(rapral_ctx* ctx, const rapral_grid* g, int64_t k0, int64_t nk) {
-    if (!g) return set_error(ctx, RAPRAL_EINVAL, "null grid");
-    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || !std::isfinite(g->lam_max))
-        return set_error(ctx, RAPRAL_EINVAL, "grid needs n >= 2 and 0 < lam_min < lam_max");
-    if (k0 < 0 || nk < 1 || k0 + nk > g->n)
+    const char* why = grid_problem(g);
+    if (why) return set_error(ctx, RAPRAL_EINVAL, "%s", why);
+    if (!range_in_grid(g, k0, nk))
         return set_error(ctx, RAPRAL_EINVAL, "range [%lld, %lld) outside the grid of %lld points", (long long)k0,
-                         (long long)(k0 + nk), (long long)g->n);
+                         (long long)k0 + (long long)nk, (long long)g->n);
     return RAPRAL_OK;
 }
 
@@ -301,6 +300,7 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     plan.tile_off = ar.take<int>(T + 1);
     unsigned long long* dmax = ar.take<unsigned long long>(RAPRAL_DMAX_SLOTS + 2);
     plan.wmax = dmax + RAPRAL_DMAX_SLOTS;
+    plan.total = reinterpret_cast<long long*>(dmax + RAPRAL_DMAX_SLOTS + 1);
     plan.sorted_flag = ar.take<int>(4);
     double2* lb = nullptr; float2* lb32 = nullptr; double2* cb = nullptr; float2* cb32 = nullptr;
     double* g0 = nullptr;
@@ -322,14 +322,19 @@ int rapral_spectral_coeffs(rapral_ctx* ctx, const rapral_species* sp, const rapr
     if (e == cudaSuccess) e = launch_bin_bounds(ctx, ln, lp, cp, dmax, h, &plan, lb);
     if (e == cudaSuccess) e = launch_bin_count(ctx, ln, g, h, &plan);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->h_pinned, plan.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        e = cudaMemcpyAsync(ctx->h_pinned, plan.total, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream);
     // the device checks ran before: on a failed one the counts were never written
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_pinned + 4, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_status(ctx, e, "line binning");
     if (ctx->h_pinned[4 + ST_CODE]) return read_status(ctx);
-    const int64_t total = ctx->h_pinned[0];
+    const int64_t total = reinterpret_cast<const long long*>(ctx->h_pinned)[0];
+    if (total > RAPRAL_MAX_TILE_ENTRIES)
+        return set_error(ctx, RAPRAL_EINVAL,
+                         "the line windows give %lld (line, tile) entries, more than the 2^31 - 1 the tile lists "
+                         "index; split the spectral range into smaller calls",
+                         (long long)total);
     // phase 2: tile lists
     need = arena_need(phase1, (size_t)(total + 1) * sizeof(int));
     if (need > ctx->ws_bytes) {

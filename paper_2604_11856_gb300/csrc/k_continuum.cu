@@ -835,8 +835,8 @@ int rapral_continuum_coeffs(rapral_ctx* ctx, const rapral_continuum* models, int
         return set_error(ctx, RAPRAL_EINVAL, "1 .. %d continuum models", RAPRAL_MAX_CONT_MODELS);
     if (precision != RAPRAL_FP64 && precision != RAPRAL_FP32)
         return set_error(ctx, RAPRAL_EINVAL, "precision %d", precision);
-    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || k0 < 0 || nk < 1 || k0 + nk > g->n)
-        return set_error(ctx, RAPRAL_EINVAL, "grid or range");
+    if (const char* why = grid_problem(g)) return set_error(ctx, RAPRAL_EINVAL, "%s", why);
+    if (!range_in_grid(g, k0, nk)) return set_error(ctx, RAPRAL_EINVAL, "range outside the grid");
     if (ld < nk) return set_error(ctx, RAPRAL_EINVAL, "ld < nk");
     if (n_species < 1 || n_species > RAPRAL_MAX_SPECIES) return set_error(ctx, RAPRAL_EINVAL, "species count");
     if (cells->n_cells < 0 || cells->n_cols < 1 || cells->ne_col < 0 || cells->ne_col >= cells->n_cols)

@@ -231,6 +231,50 @@ __global__ void __launch_bounds__(256) k_bin_fill(const double* __restrict__ lam
     }
 }
 
+// Exclusive scan of the per-tile line counts into the int32 offsets of the
+// tile lists, carried in int64 so that a total beyond 2^31 - 1 is seen:
+// total[0] receives the exact sum (offsets past 2^31 - 1 wrap, and the
+// callers refuse such a plan before the lists are filled).  Single block.
+__global__ void __launch_bounds__(1024) k_scan_counts(int* data, int64_t n, long long* total) {
+    __shared__ long long part[32];
+    __shared__ long long carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int64_t i = c0 + threadIdx.x;
+        const long long v = (i < n) ? (long long)data[i] : 0LL;
+        long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) part[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            long long p = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0LL;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, p, o);
+                if (lane >= o) p += y;
+            }
+            part[lane] = p;
+        }
+        __syncthreads();
+        const long long carry = carry_s;
+        const long long incl = x + (warp > 0 ? part[warp - 1] : 0LL);
+        if (i < n) data[i] = (int)(unsigned)(unsigned long long)(carry + incl - v);
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry_s = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        data[n] = (int)(unsigned)(unsigned long long)carry_s;
+        *total = carry_s;
+    }
+}
+
 // Single-block exclusive scan over n entries; data[n] receives the total.
 template <class T>
 __global__ void __launch_bounds__(1024) k_scan(T* data, int64_t n) {
@@ -1031,7 +1075,8 @@ cudaError_t launch_bin_count(rapral_ctx* ctx, const rapral_lines* ln, const rapr
                                                                   ctx->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_scan_i32(ctx, plan->tile_off, plan->n_tiles);
+    k_scan_counts<<<1, 1024, 0, ctx->stream>>>(plan->tile_off, plan->n_tiles, plan->total);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
@@ -1040,11 +1085,6 @@ cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapra
                                                                  plan->sorted_flag, plan->wmax, g->lam_min, h,
                                                                  plan->k0, plan->nk, plan->tile_w, plan->tile_off,
                                                                  plan->tile_lines, ctx->d_status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n) {
-    k_scan<int><<<1, 1024, 0, ctx->stream>>>(data, n);
     return cudaGetLastError();
 }
 

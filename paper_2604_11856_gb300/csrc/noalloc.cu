@@ -16,6 +16,12 @@
 // last call's contents, so each call clears the words that must start at
 // zero.  Calls that overlap on the GPU (different streams, or host threads
 // without ordering) race on the array: serialise them.
+//
+// The call runs on the device that owns `cuda_stream` (the current device
+// for the legacy default stream): it makes that device current for its
+// duration and restores the caller's current device before it returns.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "rapral_internal.cuh"
@@ -27,8 +33,17 @@ constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
+// Per device: the scratch array's device address and the identity of the
+// CUDA context it was looked up in.  A device reset destroys that context and
+// the next one loads the array afresh, possibly elsewhere, so the address is
+// looked up again whenever the current context's identity differs.
+struct ScratchAddr {
+    void* ptr = nullptr;
+    unsigned long long ctx_id = 0;
+    bool have_id = false;
+};
 std::mutex g_mu;
-void* g_ptr[MAX_DEVICES] = {nullptr};
+ScratchAddr g_addr[MAX_DEVICES];
 
 void put_err(char* err, size_t len, const char* msg) {
     if (err && len) {
@@ -37,30 +52,82 @@ void put_err(char* err, size_t len, const char* msg) {
     }
 }
 
-// Device address of the scratch array on the current device.  The address
-// is looked up once per device (this is the set-up the first call on a
-// device performs).
-int scratch_ptr(void** out, char* err, size_t len) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+// Unique identity of the calling thread's current CUDA context (driver API,
+// reached through the runtime's entry-point table, so no link to libcuda).
+// False when no context is current or the driver cannot tell.
+bool current_ctx_id(unsigned long long* id) {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
         cudaGetLastError();
-        put_err(err, len, "no usable current CUDA device");
-        return RAPRAL_ECUDA;
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array on device `dev`, which must be current.
+// This is the set-up of the first call on a device (and the first call after
+// a reset of it): cudaGetSymbolAddress, with its return code checked.
+int scratch_ptr(int dev, void** out, char* err, size_t len) {
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        put_err(err, len, "device index beyond the scratch table");
+        return RAPRAL_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
+    ScratchAddr& a = g_addr[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_ctx_id(&id);
+    if (!a.ptr || !have_id || !a.have_id || a.ctx_id != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            a = ScratchAddr{};
             put_err(err, len, "cudaGetSymbolAddress of the scratch array failed");
             return RAPRAL_ECUDA;
         }
-        g_ptr[dev] = p;
+        a.ptr = p;
+        a.have_id = current_ctx_id(&a.ctx_id);   // the lookup made the context current if none was
     }
-    *out = g_ptr[dev];
+    *out = a.ptr;
     return RAPRAL_OK;
 }
+
+// Makes `dev` current for the lifetime of the guard and restores the
+// caller's current device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    cudaError_t enter(int dev) {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) return e;
+        if (prev == dev) return cudaSuccess;
+        e = cudaSetDevice(dev);
+        switched = e == cudaSuccess;
+        return e;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
+int noalloc_impl(int dev, cudaStream_t stream, const rapral_species* sp, const rapral_lines* ln,
+                 const rapral_cells* cells, const rapral_grid* g, int64_t k0, int64_t nk, int precision,
+                 void* kappa, void* emis, int64_t ld, char* err, size_t err_len);
 
 }  // namespace
 
@@ -72,14 +139,38 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
         put_err(err, err_len, "null argument");
         return RAPRAL_EINVAL;
     }
-    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || k0 < 0 || nk < 1 || k0 + nk > g->n ||
-        ld < nk || (precision != RAPRAL_FP64 && precision != RAPRAL_FP32) || ln->n_lines < 0 ||
-        ln->n_lines > 2147483647LL || cells->n_cells < 0 || cells->n_cols < 1 || cells->ne_col < 0 ||
-        cells->ne_col >= cells->n_cols || sp->n_species < 1 || sp->n_species > RAPRAL_MAX_SPECIES ||
-        (cells->n_cells > 0 && !cells->lnpref)) {
+    if (const char* why = grid_problem(g)) {
+        put_err(err, err_len, why);
+        return RAPRAL_EINVAL;
+    }
+    if (!range_in_grid(g, k0, nk) || ld < nk || (precision != RAPRAL_FP64 && precision != RAPRAL_FP32) ||
+        ln->n_lines < 0 || ln->n_lines > 2147483647LL || cells->n_cells < 0 || cells->n_cols < 1 ||
+        cells->ne_col < 0 || cells->ne_col >= cells->n_cols || sp->n_species < 1 ||
+        sp->n_species > RAPRAL_MAX_SPECIES || (cells->n_cells > 0 && !cells->lnpref)) {
         put_err(err, err_len, "invalid size, range, precision or null array");
         return RAPRAL_EINVAL;
     }
+    const cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    if (cudaStreamGetDevice(stream, &dev) != cudaSuccess) {
+        cudaGetLastError();
+        put_err(err, err_len, "cannot tell the device of the stream");
+        return RAPRAL_ECUDA;
+    }
+    DeviceGuard guard;
+    if (guard.enter(dev) != cudaSuccess) {
+        cudaGetLastError();
+        put_err(err, err_len, "cannot make the stream's device current");
+        return RAPRAL_ECUDA;
+    }
+    return noalloc_impl(dev, stream, sp, ln, cells, g, k0, nk, precision, kappa, emis, ld, err, err_len);
+}
+
+namespace {
+
+int noalloc_impl(int dev, cudaStream_t stream, const rapral_species* sp, const rapral_lines* ln,
+                 const rapral_cells* cells, const rapral_grid* g, int64_t k0, int64_t nk, int precision,
+                 void* kappa, void* emis, int64_t ld, char* err, size_t err_len) {
     const int64_t C = cells->n_cells, L = ln->n_lines;
     if (C == 0) return RAPRAL_OK;
     const int W = precision == RAPRAL_FP64 ? 512 : 128;   // the regular entry point's defaults
@@ -108,14 +199,14 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
         return RAPRAL_ENOMEM;
     }
     void* base = nullptr;
-    int st = scratch_ptr(&base, err, err_len);
+    int st = scratch_ptr(dev, &base, err, err_len);
     if (st) return st;
 
     // a context on the caller's stack: the stream, the status word and the
     // counters in the scratch array; no workspace of its own
     rapral_ctx ctx;
-    cudaGetDevice(&ctx.device);
-    ctx.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    ctx.device = dev;
+    ctx.stream = stream;
     Arena ar{reinterpret_cast<char*>(base), SCRATCH_BYTES};
     ctx.d_status = ar.take<int>(8);
     ctx.d_stats = ar.take<unsigned long long>(4);
@@ -130,6 +221,7 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     plan.tile_off = ar.take<int>(T + 1);
     plan.sorted_flag = sorted_flag;
     plan.wmax = dmax + 2;
+    plan.total = reinterpret_cast<long long*>(dmax + 3);
     const size_t csr_at = ar.used;
 
     const double h = (g->lam_max - g->lam_min) / (double)(g->n - 1);
@@ -156,11 +248,11 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     if (e == cudaSuccess) e = launch_bin_count(&ctx, ln, g, h, &plan);
     // read the status word and the tile-list length (host stack, no pinned buffer)
     int status_words[3] = {0, 0, 0};
-    int total = 0;
+    long long total = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(status_words, ctx.d_status, sizeof(status_words), cudaMemcpyDeviceToHost, ctx.stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&total, plan.tile_off + T, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream);
+        e = cudaMemcpyAsync(&total, plan.total, sizeof(long long), cudaMemcpyDeviceToHost, ctx.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -172,9 +264,10 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
                               "weights or Einstein coefficients)");
         return status_words[ST_CODE];
     }
-    if (arena_need(csr_at, (size_t)(total + 1) * sizeof(int)) > SCRATCH_BYTES) {
+    if (total > (long long)(SCRATCH_BYTES / sizeof(int)) ||
+        arena_need(csr_at, (size_t)(total + 1) * sizeof(int)) > SCRATCH_BYTES) {
         char msg[200];
-        snprintf(msg, sizeof(msg), "tile lists of %d entries exceed the %zu-byte scratch", total, SCRATCH_BYTES);
+        snprintf(msg, sizeof(msg), "tile lists of %lld entries exceed the %zu-byte scratch", total, SCRATCH_BYTES);
         put_err(err, err_len, msg);
         return RAPRAL_ENOMEM;
     }
@@ -195,3 +288,5 @@ extern "C" int rapral_spectral_coeffs_noalloc(void* cuda_stream, const rapral_sp
     }
     return RAPRAL_OK;
 }
+
+}  // namespace

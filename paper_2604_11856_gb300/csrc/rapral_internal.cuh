@@ -182,6 +182,19 @@ struct Arena {
 };
 inline size_t arena_need(size_t cur, size_t bytes) { return ((cur + 255) & ~size_t(255)) + bytes; }
 
+// Host-side check of a spectral grid and a range [k0, k0 + nk) of it: null
+// when they are valid, else a message (static storage).  Every entry point
+// that takes a grid uses this one check.
+inline const char* grid_problem(const rapral_grid* g) {
+    if (!g) return "null grid";
+    if (g->n < 2 || !(g->lam_max > g->lam_min) || !(g->lam_min > 0.0) || !std::isfinite(g->lam_max))
+        return "grid needs n >= 2 and 0 < lam_min < lam_max (finite)";
+    return nullptr;
+}
+inline bool range_in_grid(const rapral_grid* g, int64_t k0, int64_t nk) {
+    return k0 >= 0 && nk >= 1 && k0 <= g->n - nk;
+}
+
 // Grid launch helper.
 inline unsigned div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -226,14 +239,21 @@ struct BinPlan {
     int2* line_tiles;            // [L] first / last tile a line may touch (first > last: none)
     int* tile_off;               // [T+1]
     int* tile_lines;             // [tile_off[T]]
+    long long* total;            // [1] exact number of (line, tile) entries (int64: may exceed the
+                                 // int32 offsets; a plan with more than 2^31 - 1 is refused)
     int* sorted_flag;            // [1] 1 while lam0 is non-decreasing
     unsigned long long* wmax;    // [1] largest window half-width, grid points (double bits)
 };
 cudaError_t launch_bin_bounds(rapral_ctx* ctx, const rapral_lines* ln, const LinePrep* lp, const CellPrep* cp,
                               const unsigned long long* d_max, double h, BinPlan* plan,
                               const double2* lb = nullptr);
+// Counts each tile's lines and scans the counts into plan->tile_off; the
+// exact total goes to plan->total (device).
 cudaError_t launch_bin_count(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
                              BinPlan* plan);
+// Largest number of (line, tile) entries a plan may hold: the tile lists are
+// indexed by int32 offsets.
+constexpr long long RAPRAL_MAX_TILE_ENTRIES = 2147483647LL;
 cudaError_t launch_bin_fill(rapral_ctx* ctx, const rapral_lines* ln, const rapral_grid* g, double h,
                             BinPlan* plan);
 
@@ -356,7 +376,6 @@ size_t fib_flux_scratch_bytes(int64_t P, int32_t n_los, int32_t n_phi, int32_t n
 cudaError_t launch_fib_flux(rapral_ctx* ctx, int64_t P, const int64_t* point_off, const int32_t* los_index,
                             int32_t n_los, const double* S, int32_t n_phi, int32_t n_theta, double* q,
                             void* scratch);
-cudaError_t launch_scan_i32(rapral_ctx* ctx, int* data, int64_t n);
 
 // Coefficients of the rational Faddeeva expansion: computed once on the host,
 // copied to the current device's constant memory by the first exact-Voigt

@@ -71,6 +71,7 @@ def test_noalloc_entry_point_rejects_bad_arguments_before_any_cuda_call():
 
     bad = [dict(grid=R.Grid(50.0, 100.0, 1)),                     # fewer than two grid points
            dict(grid=R.Grid(100.0, 50.0, 100)),                   # empty wavelength range
+           dict(grid=R.Grid(50.0, float("inf"), 100)),            # infinite upper wavelength
            dict(grid=R.Grid(50.0, 100.0, 100), k0=95, nk=10),     # range past the grid's end
            dict(grid=R.Grid(50.0, 100.0, 100), ld=5),             # row stride below the range
            dict(grid=R.Grid(50.0, 100.0, 100), precision=7)]      # unknown precision

@@ -65,16 +65,23 @@ def test_coeffs_fp32_stagnation(ctx):
     assert point_error(kap, rk, ra, what="kappa") <= TOL_POINT
 
 
-def test_fp32_window_decisions_match_fp64(ctx):
+@pytest.mark.parametrize("tile", [None, 256])
+def test_fp32_window_decisions_match_fp64(ctx, tile):
     """The FP32 path includes exactly the (line, point) pairs the FP64 path
-    does: its evaluation count equals the FP64 kernel's."""
+    does, and both exactly those of the oracle's literal window test: the
+    library's evaluation counter (the numerator of the line sum's roofline)
+    equals the oracle's count of in-window (line, cell, point) triples on a
+    two-temperature case."""
     p = synth.stagnation_line(n_cells=8, n_atomic=4000, n_molecular=20000, n_grid=80001)
     counts = {}
     for prec in (R.FP64, R.FP32):
         ctx.reset_stats()
-        _coeffs(ctx, p, prec)
+        _coeffs(ctx, p, prec, tile)
         counts[prec] = ctx.get_stats()["evaluations"]
-    assert counts[R.FP64] == counts[R.FP32] > 0
+    oracle.spectral_coeffs(p)
+    ref = oracle.last_evaluations()
+    print(f"  evaluations: oracle {ref}, FP64 {counts[R.FP64]}, FP32 {counts[R.FP32]}")
+    assert counts[R.FP64] == counts[R.FP32] == ref > 0
 
 
 def test_slab_solve_fp32(ctx):

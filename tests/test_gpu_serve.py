@@ -1,9 +1,11 @@
 """Serving loop on the GPU: continuous admission under a memory budget,
-concurrent requests on several streams, and each served result equal to
-the same request solved alone."""
+concurrent requests on several streams, each served result equal to the
+same request solved alone, and served results of both kinds (slab and line
+of sight) equal to the oracle's within the tolerance of their arithmetic."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_11856_gb300 import rapral as R
 from paper_2604_11856_gb300 import serve, synth
 
@@ -45,3 +47,25 @@ def test_bounded_queue_sheds(pool):
     stats = serve.run_open_loop(srv, reqs)
     assert stats["shed"] > 0
     assert stats["done"] + stats["shed"] == len(reqs)
+
+
+@pytest.mark.parametrize("precision,tol", [(R.FP32, 1e-4), (R.FP64, 1e-10)])
+def test_served_results_match_oracle(pool, precision, tol):
+    """Requests served in a concurrent mix: at least two tangent-slab and two
+    single line-of-sight requests are checked against the oracle's whole
+    solve of the same problem (heat flux within 1e-4 for FP32, 1e-10 for
+    FP64)."""
+    lines, species, _ = pool
+    reqs = _requests(pool, 16, 400.0, precision, seed=2024)
+    srv = serve.Server(lines, species, slots=4)
+    stats = serve.run_open_loop(srv, reqs)
+    assert stats["done"] == len(reqs), stats
+    slab = [r for r in reqs if len(r.problem.geometry.mu) > 1][:2]
+    los = [r for r in reqs if len(r.problem.geometry.mu) == 1][:2]
+    assert len(slab) == 2 and len(los) == 2
+    for r in slab + los:
+        ref = oracle.solve_slab(r.problem)["q"]
+        err = abs(r.q[0] / ref - 1)
+        print(f"  request {r.rid} ({len(r.problem.cells)} cells, {r.problem.grid.n} points, "
+              f"{len(r.problem.geometry.mu)} directions): q {r.q[0]!r} oracle {ref!r} rel {err:.2e}")
+        assert err <= tol

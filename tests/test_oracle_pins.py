@@ -333,6 +333,28 @@ def test_windowed_sum_equals_brute_force():
                 assert kap[c, k - k0] == pytest.approx(math.fsum(tk), rel=1e-15, abs=1e-300)
 
 
+def test_evaluation_count_is_the_in_window_triples():
+    """The oracle's count of profile evaluations (the work unit of the line
+    sum's roofline) is the number of (line, cell, grid point) triples with
+    |lam_k - lam0| <= 100 lamV, counted here by brute force over every grid
+    point of the range, windows cut by the grid ends included."""
+    p = synth.uniform_slab(n_lines=12, n_cells=3, n_grid=2000, lam=(50.0, 60.0), seed=5)
+    p.lines.lam0[:] = np.sort(np.random.default_rng(3).uniform(49.0, 61.0, 12))
+    p.cells.n[:, synth.NE_COL] = 3e16
+    p.cells.Ttr[:] = [4000.0, 9000.0, 25000.0]
+    lnp = oracle.lnpref(p)
+    h = (p.grid.lam_max - p.grid.lam_min) / (p.grid.n - 1)
+    for k0, nk in [(0, 2000), (700, 600)]:
+        oracle.spectral_coeffs(p, lnp, k0, nk)
+        got = oracle.last_evaluations()
+        lam = p.grid.lam_min + np.arange(k0, k0 + nk) * h
+        want = 0
+        for c in range(3):
+            lamV = oracle.line_states(p, lnp, c)["lamV"]
+            want += int((np.abs(lam[None, :] - p.lines.lam0[:, None]) <= 100.0 * lamV[:, None]).sum())
+        assert got == want > 0
+
+
 def test_window_is_fifty_full_widths_each_side():
     """The line wings are cut at |lam - lam0| = 100 lamV, fifty Voigt FWHM on
     each side (reading A3).  One line whose window lies inside a fine grid:
