@@ -1,15 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the RAPRAL hot path on GB300.
 
-A step is one whole solve of the stagnation-line workload (200 two-temperature
-cells, 20,000 atomic + 300,000 molecular lines, 1,000,000-point grid over
-50-2000 nm, 16-direction tangent slab plus the normal ray): populations ->
-line binning -> line-by-line kappa / j -> ray march -> wall flux, with inputs
-resident in HBM.  The FP32-chosen arithmetic is the headline; the FP64-plain
-path on the same workload is measured beside it.
+Headline (default): the axisymmetric afterbody stand-in of the paper's
+Fire II case (Sec. 3.2): 400 x 200 two-temperature cells, 20,000 atomic +
+300,000 molecular lines, a 1,000,000-point grid over 50-2000 nm in 65,536-point
+chunks, 200 surface points x 512 rays (16 mu x 32 azimuths), FP32-chosen
+arithmetic.  A step is one spectral chunk of that solve, through every step of
+the path: line binning -> line-by-line kappa / j of all 80,000 cells -> ray
+march of all 102,400 rays with the angular sum -> wall flux; populations at
+the first chunk of each solve.  Steps run back to back through the two-stream
+chunk pipeline (the line sum of chunk i + 1 overlaps the march of chunk i),
+cycling through the 16 chunks, so 16 steps are one whole solve.  The ray
+segments depend on the geometry only and are built once, before timing.
+Inputs are resident in HBM when timing starts; each step's kappa / j table
+(42 GB) is far larger than L2.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
-instead, on a bounded sample of the same workload.
+Secondary blocks: the stagnation-line step (FP32 and FP64 plain), the served
+request loop.  `--impl reference` times the CPU oracle instead, on a bounded
+sample of the same workload.  Prints one JSON line (rank 0).
 """
 from __future__ import annotations
 
@@ -27,31 +35,38 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 METRIC = "cell·λ coeff points/s and ray·λ segments/s; served q_rad p50/p99 vs FP64 plain"
-WORKLOAD = "stagnation line: 200 cells, 20k atomic + 300k molecular lines, 1e6-point grid 50-2000 nm, 16-mu tangent slab"
+WORKLOAD = ("afterbody: 400x200 cells, 20k atomic + 300k molecular lines, 1e6-point grid 50-2000 nm "
+            "in 65,536-point chunks, 200 points x 512 rays (16 mu x 32 azimuths)")
+STAG_WORKLOAD = "stagnation line: 200 cells, 20k atomic + 300k molecular lines, 1e6-point grid 50-2000 nm, 16-mu tangent slab"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+SERVE_RATES = (50.0, 100.0, 200.0, 500.0, 1000.0, 2000.0)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 20 for the stagnation-line step, 5 for the other workloads)")
-    ap.add_argument("--warmup", type=int, default=3)
+                    help="timed steps (default: 20 for the afterbody chunks and the stagnation step, 5 otherwise)")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["rapral", "reference"], default="rapral")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain side measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--no-serve", action="store_true", help="skip the served-requests measurement")
-    ap.add_argument("--serve-requests", type=int, default=40)
-    ap.add_argument("--serve-fp64-requests", type=int, default=4)
-    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--no-secondary", action="store_true", help="headline only: skip the stagnation and served blocks")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-requests block")
+    ap.add_argument("--serve-requests", type=int, default=100, help="FP32 requests per offered rate")
+    ap.add_argument("--serve-fp64-requests", type=int, default=4, help="FP64 requests per offered rate (the first ones)")
+    ap.add_argument("--serve-rates", type=str, default="4,50,2000",
+                    help=f"offered rates, req/s (the whole study: {','.join(str(int(r)) for r in SERVE_RATES)})")
+    ap.add_argument("--serve-fp64-rates", type=str, default="2000")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
-    ap.add_argument("--workload", choices=["stagnation", "afterbody", "batch", "fibonacci", "qss", "continuum", "voigt"],
-                    default="stagnation",
-                    help="stagnation line (the bench line); afterbody / batch / fibonacci / qss / continuum / "
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="stagnation workload only")
+    ap.add_argument("--no-fp64", action="store_true", help="stagnation: skip the FP64-plain side measurement")
+    ap.add_argument("--workload", choices=["afterbody", "stagnation", "serve", "batch", "fibonacci", "qss", "continuum",
+                                           "voigt"],
+                    default="afterbody",
+                    help="afterbody (the bench line); stagnation / serve / batch / fibonacci / qss / continuum / "
                          "voigt (the stagnation step with the exact Voigt shape): one-off measurements")
     ap.add_argument("--cont-levels", type=int, default=100, help="continuum workload: levels per atom (N, O)")
     ap.add_argument("--cont-points", type=int, default=1_000_000,
@@ -59,14 +74,16 @@ def parse():
     ap.add_argument("--fib-points", type=int, default=8, help="fibonacci workload: surface points")
     ap.add_argument("--fib-los", type=int, default=128, help="fibonacci workload: Fibonacci directions per point")
     ap.add_argument("--ab-small", action="store_true",
-                    help="afterbody workload at 100 x 50 cells, 20 points, 2e5 grid points (profiler captures)")
+                    help="afterbody at 100 x 50 cells, 20 points, 2e5 grid points (profiler captures)")
+    ap.add_argument("--ab-cells", type=str, default="",
+                    help="afterbody cells as NXxNR (smaller only for profiler captures; all 200 points kept)")
     ap.add_argument("--cells", type=int, default=200,
                     help="cells of the stagnation line (fewer only for profiler captures)")
     ap.add_argument("--oracle-phases", action="store_true",
                     help="with --impl reference: the oracle's time per phase, all threads and one thread")
     args = ap.parse_args()
-    if args.steps is None:   # the stagnation step takes ~31 ms: 20 steps give the clock sampler a few samples
-        args.steps = 20 if (args.impl == "rapral" and args.workload == "stagnation") else 5
+    if args.steps is None:
+        args.steps = 20 if (args.impl == "rapral" and args.workload in ("afterbody", "stagnation")) else 5
     return args
 
 
@@ -84,6 +101,11 @@ LINE_SUM_TRAFFIC = {"sha1": "ee162f14b8a843d46ca76ea6702ffe0ac1880911", "cells":
 # kernel source with this digest (source_digest); a different source gives null.
 CONT_TRAFFIC = {"sha1": "5acd74ef87910912678c8d6546c788ab0f5e87b0", "cells": 200, "grid_points": 1_000_000, "levels": 100,
                 "bytes": 1_782_956_800 + 1_538_739_456}
+
+# DRAM bytes of one FP32 march launch (k_march, single-direction rays) per
+# afterbody chunk, from a one-pass ncu capture of the kernel source with this
+# digest; None until captured on the current source.
+MARCH_TRAFFIC = {"sha1": None, "cells": 80_000, "grid_points": 65_536, "bytes": None}
 
 
 def source_digest(name):
@@ -173,6 +195,84 @@ def measured_peaks():
         return {}
 
 
+# L2 gather-bandwidth probe (a roofline denominator for the march, whose
+# gathers L2 serves): warps load 256-byte rows (8 bytes a lane) at
+# pseudo-random row indices of an L2-resident table; every index is reduced
+# modulo the row count, so every access stays inside the table.
+GATHER_PROBE_SRC = r"""
+#include <cuda_runtime.h>
+extern "C" __global__ void k_gather_probe(const float2* __restrict__ tab, long long rows, int iters, float* out) {
+    const int lane = threadIdx.x & 31;
+    unsigned x = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2654435761u + 12345u;
+    float s = 0.f;
+    for (int i = 0; i < iters; i += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x = x * 1664525u + 1013904223u;
+            v[u] = tab[(long long)(x % (unsigned)rows) * 32 + lane];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s += v[u].x + v[u].y;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+extern "C" float gather_probe_ms(const void* tab, long long bytes, int blocks, int iters, float* out) {
+    const long long rows = bytes / 256;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a); cudaEventCreate(&b);
+    k_gather_probe<<<blocks, 256>>>((const float2*)tab, rows, iters, out);
+    cudaEventRecord(a);
+    k_gather_probe<<<blocks, 256>>>((const float2*)tab, rows, iters, out);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a); cudaEventDestroy(b);
+    return ms;
+}
+"""
+
+
+def l2_gather_peak(dev_index):
+    """Measured L2 gather bandwidth (GB/s): the best of a few block counts on
+    48 MB and 96 MB tables (both L2-resident), built with nvcc for sm_103a."""
+    import ctypes
+    import torch
+    from paper_2604_11856_gb300 import build as B
+    os.makedirs(B.BUILD, exist_ok=True)
+    src = os.path.join(B.BUILD, "gather_probe.cu")
+    lib = os.path.join(B.BUILD, "gather_probe.so")
+    stale = not (os.path.exists(lib) and os.path.exists(src) and open(src).read() == GATHER_PROBE_SRC)
+    if stale:
+        with open(src, "w") as f:
+            f.write(GATHER_PROBE_SRC)
+        subprocess.run([B.nvcc(), *B.ARCH, "-O3", "-shared", "-Xcompiler", "-fPIC", src, "-o", lib], check=True)
+    L = ctypes.CDLL(lib)
+    L.gather_probe_ms.restype = ctypes.c_float
+    L.gather_probe_ms.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    best = {}
+    n_sm = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    for mb in (48, 96):
+        nbytes = mb << 20
+        tab = torch.ones(nbytes // 4, dtype=torch.float32, device=f"cuda:{dev_index}")
+        for blocks in (4 * n_sm, 8 * n_sm):
+            out = torch.empty(blocks * 256, dtype=torch.float32, device=f"cuda:{dev_index}")
+            iters = 4096
+            ms = L.gather_probe_ms(tab.data_ptr(), nbytes, blocks, iters, out.data_ptr())
+            best[mb] = max(best.get(mb, 0.0), blocks * 256 * iters * 8 / (ms * 1e-3) / 1e9)
+    return {"GBps_48MB_table": best[48], "GBps_96MB_table": best[96],
+            "how": "warps loading 256-byte rows at random row indices of an L2-resident table (bench.py)"}
+
+
+def march_traffic(cells, grid_points):
+    digest = source_digest("k_rays.cu")
+    t = MARCH_TRAFFIC
+    if t["bytes"] is None or digest != t["sha1"]:
+        return None
+    return t["bytes"] * (cells / t["cells"]) * (grid_points / t["grid_points"])
+
+
 def cpu_baseline(problem, seconds, precision_note="f64"):
     """The oracle as it stands, on the host cores, on a bounded sample of the
     workload: every line, the whole grid, a few cells (one per thread), for
@@ -198,44 +298,58 @@ def cpu_baseline(problem, seconds, precision_note="f64"):
     oracle.spectral_coeffs(sub, lnp, k0, nk2)
     dt2 = time.perf_counter() - t0
     return {"value": n_cells * nk2 / dt2, "unit": "cell·λ points/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n_cells} of {len(p.cells)} cells x {nk2} of {p.grid.n} grid points, all "
-                      f"{len(p.lines)} lines, kappa and j in FP64 ({dt2:.1f} s)", "seconds": dt2}
+            "sample": f"{n_cells} of {len(p.cells)} cells spread over the domain x {nk2} of {p.grid.n} grid points, "
+                      f"all {len(p.lines)} lines, kappa and j in FP64 ({dt2:.1f} s)", "seconds": dt2}
 
 
 def served(p, args, device):
-    """Open-loop served requests (line-of-sight and slab solves, config-4
-    sizes) sharing the resident stagnation-line lists; FP32-chosen vs FP64
-    plain on the same requests (FP64 on the first few only: it is ~80x
-    slower)."""
+    """Open-loop served requests (config-4 sizes: line-of-sight and slab
+    solves, cells 10-5000, 1e5-1e6 points, 1-256 rays) sharing the resident
+    stagnation-line lists, at several offered Poisson rates.  At each rate
+    the FP32-chosen path serves the whole request stream and the FP64-plain
+    path the same stream's first requests (it is ~80x slower); the q error of
+    FP32 is taken against FP64 on the requests both served."""
     from paper_2604_11856_gb300 import rapral as R
     from paper_2604_11856_gb300 import serve, synth
     pool = (p.lines, p.species, {})
-    gen = synth.served_requests(seed=1004, n_requests=args.serve_requests, rate=args.serve_rate, pool=pool)
-    res = {"offered_rate_req_s": args.serve_rate, "slots": 4, "budget_bytes": 150 << 30}
-    q32 = {}
-    for prec, n, name in ((R.FP32, args.serve_requests, "fp32"), (R.FP64, args.serve_fp64_requests, "fp64")):
-        if n <= 0:
-            continue
-        reqs = [serve.Request(rid=i, problem=g["problem"], arrival=g["t"], precision=prec)
-                for i, g in enumerate(gen[:n])]
-        srv = serve.Server(p.lines, p.species, device=device, slots=4)
-        res[name] = serve.run_open_loop(srv, reqs)
-        if prec == R.FP32:
-            q32 = {r.rid: r.q for r in reqs if r.status == "done"}
-        else:
-            errs = [float(np.max(np.abs(q32[r.rid] / r.q - 1))) for r in reqs if r.status == "done" and r.rid in q32]
-            res["q_rel_err_fp32_vs_fp64_max"] = max(errs) if errs else None
+    rates = [float(r) for r in args.serve_rates.split(",") if r]
+    rates64 = {float(r) for r in args.serve_fp64_rates.split(",") if r}
+    res = {"slots": 4, "admission": "device free memory at start minus a 16 GiB reserve", "rates": []}
+    errs_all = []
+    for i, rate in enumerate(rates):
+        gen = synth.served_requests(seed=1004 + i, n_requests=args.serve_requests, rate=rate, pool=pool)
+        row = {"offered_rate_req_s": rate}
+        q32 = {}
+        for prec, n, name in ((R.FP32, args.serve_requests, "fp32"), (R.FP64, args.serve_fp64_requests, "fp64")):
+            if n <= 0 or (prec == R.FP64 and rate not in rates64):
+                continue
+            reqs = [serve.Request(rid=j, problem=g["problem"], arrival=g["t"], precision=prec)
+                    for j, g in enumerate(gen[:n])]
+            srv = serve.Server(p.lines, p.species, device=device, slots=4)
+            row[name] = serve.run_open_loop(srv, reqs)
+            res["budget_bytes"] = srv.budget
+            if prec == R.FP32:
+                q32 = {r.rid: r.q for r in reqs if r.status == "done"}
+            else:
+                errs = [float(np.max(np.abs(q32[r.rid] / r.q - 1))) for r in reqs
+                        if r.status == "done" and r.rid in q32]
+                row["q_rel_err_fp32_vs_fp64_max"] = max(errs) if errs else None
+                errs_all += errs
+        res["rates"].append(row)
+    res["q_rel_err_fp32_vs_fp64_max"] = max(errs_all) if errs_all else None
+    sat = [r["fp32"]["throughput_req_s"] for r in res["rates"] if "fp32" in r]
+    res["fp32_saturation_req_s"] = max(sat) if sat else None
     return res
 
 
 def run_reference(args):
     """--impl reference: the oracle on the host cores, bounded samples of the
-    bench workload per step."""
+    bench workload (the afterbody) per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from paper_2604_11856_gb300 import synth
-    p = synth.stagnation_line()
+    p = synth.afterbody()
     per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_baseline(p, per_step / 4)
@@ -246,7 +360,7 @@ def run_reference(args):
         vals.append(last["value"])
         secs.append(last.pop("seconds"))
     v = float(np.mean(vals))
-    # a step here is one bounded sample of the workload, not the whole 200-cell step
+    # a step here is one bounded sample of the workload, not a whole chunk
     line = {"metric": METRIC, "value": v, "unit": "cell·λ points/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(secs)) * 1e3, "higher_is_better": True,
             "scaling": "weak",
@@ -327,73 +441,6 @@ def oracle_phases(args):
                               "total_projected_s": sum(full.values()),
                               "cell_lambda_per_s": C * K / full["coefficients"]}))
     lib.orc_set_threads(n_all)
-    return 0
-
-
-def run_afterbody(args):
-    """The axisymmetric afterbody (80,000 cells, 1e6 points in 65,536-point
-    chunks, 102,400 rays): one FP32 solve with the two-stream chunk pipeline."""
-    import torch
-    from paper_2604_11856_gb300 import rapral as R
-    from paper_2604_11856_gb300 import solver, synth
-    if args.ab_small:
-        p = synth.afterbody(nx=100, nr=50, n_points=20, n_grid=200_000)
-    else:
-        p = synth.afterbody()
-    ctx = R.Context(0)
-    ctx2 = R.Context(0, stream=torch.cuda.Stream())
-    dp = solver.DeviceProblem(p, ctx)
-    ctx.sync()
-    bufs = [(torch.empty((dp.C, p.chunk), dtype=torch.float32, device=ctx.device),
-             torch.empty((dp.C, p.chunk), dtype=torch.float32, device=ctx.device)) for _ in range(2)]
-    for _ in range(args.warmup):
-        solver.solve(dp, ctx, R.FP32, chunk=p.chunk, ctx2=ctx2, buffers=bufs)
-    ctx.sync(); ctx2.sync()
-    ms = []
-    with ClockSampler(0) as clk:
-        for i in range(max(1, args.steps)):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(ctx.stream)
-            out = solver.solve(dp, ctx, R.FP32, chunk=p.chunk, ctx2=ctx2, buffers=bufs)
-            b.record(ctx.stream)
-            ctx.sync(); ctx2.sync()
-            ms.append(a.elapsed_time(b))
-    t = float(np.mean(ms)) * 1e-3
-    nseg = dp.rays.struct.n_segments
-    # the march alone on one full chunk (its kappa / j computed first, untimed), L2
-    # flushed before each repetition: segment-wavelengths per second and the
-    # effective gather bandwidth (8 B of kappa + j per segment-wavelength)
-    nk = min(p.chunk, p.grid.n)
-    kap, em = bufs[0]
-    R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, 0, nk, R.FP32, kap, em)
-    qlam = torch.empty((dp.P, nk), dtype=torch.float32, device=ctx.device)
-    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=ctx.device)
-    mm = []
-    for rep in range(4):
-        flush.fill_(1.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(ctx.stream)
-        R.trace_rays(ctx, dp.rays, dp.C, kap, em, p.grid, 0, nk, R.FP32, qlam)
-        b.record(ctx.stream)
-        ctx.sync()
-        if rep:
-            mm.append(a.elapsed_time(b))
-    tm = float(np.mean(mm)) * 1e-3
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    gather = nseg * nk * 8 / tm / 1e9
-    march = {"kernel": "k_march (single-direction rays)", "chunk_points": nk, "kernel_ms": tm * 1e3,
-             "ray_lambda_segments_per_s": nseg * nk / tm, "gather_GBps_effective": gather,
-             "hbm_peak_GBps": hbm, "gather_over_hbm_peak": gather / hbm,
-             "unique_kappa_j_bytes": dp.C * nk * 8,
-             "note": "kappa / j rows are gathered from L2 (one DRAM pass per chunk): bound by issue, not HBM"}
-    g = p.geometry
-    desc = (f"afterbody {len(g.xf) - 1}x{len(g.rf) - 1} cells, {len(p.lines) // 1000}k lines, {p.grid.n:.0e} points "
-            f"in {p.chunk}-point chunks, {len(g.surf_x)} points x {len(g.mu) * g.n_phi} rays")
-    print(json.dumps({"workload": desc, "warmup": args.warmup, "steps": max(1, args.steps), "ms_per_solve": t * 1e3,
-                      "cell_lambda_per_s": dp.C * p.grid.n / t, "ray_lambda_segments_per_s": nseg * p.grid.n / t,
-                      "segments": int(nseg), "q_mean_W_cm2": float(out["q"].mean().item()), "clocks": clk.summary(),
-                      "march": march}))
     return 0
 
 
@@ -643,186 +690,232 @@ def run_fibonacci(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return oracle_phases(args) if args.oracle_phases else run_reference(args)
-    if args.workload == "afterbody":
-        return run_afterbody(args)
-    if args.workload == "batch":
-        return run_batch(args)
-    if args.workload == "fibonacci":
-        return run_fibonacci(args)
-    if args.workload == "qss":
-        return run_qss(args)
-    if args.workload == "continuum":
-        return run_continuum(args)
-    if args.workload == "voigt":
-        return run_voigt(args)
+def dist_setup():
     import torch
     import torch.distributed as dist
-
-    from paper_2604_11856_gb300 import rapral as R
-    from paper_2604_11856_gb300 import solver, synth
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(dev, world):
+    import torch
+    import torch.distributed as dist
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+
+
+def afterbody_problem(args):
+    from paper_2604_11856_gb300 import synth
+    if args.ab_small:
+        return synth.afterbody(nx=100, nr=50, n_points=20, n_grid=200_000)
+    if args.ab_cells:
+        nx, nr = (int(v) for v in args.ab_cells.lower().split("x"))
+        return synth.afterbody(nx=nx, nr=nr)
+    return synth.afterbody()
+
+
+def run_headline(args):
+    """The afterbody chunk steps (module docstring).  With N ranks each rank
+    takes every N-th chunk of the solve (a spectral shard: the chunks are
+    independent, populations are replicated) and the P partial fluxes are
+    summed by one FP64 all-reduce at the end."""
+    import torch
+    import torch.distributed as dist
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver
+
+    world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
-    precision = R.FP32 if args.precision == "fp32" else R.FP64
+    p = afterbody_problem(args)
+    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ctx = R.Context(local, stream=sa)
+    ctx2 = R.Context(local, stream=sb)
+    dp = solver.DeviceProblem(p, ctx)   # ray segments: built once per geometry
+    ctx.sync()
+    C, P, n, chunk = dp.C, dp.P, p.grid.n, p.chunk
+    nseg = int(dp.rays.struct.n_segments)
+    mine = solver.shard_ranges(n, rank, world, chunk)   # this rank's spectral shard: every world-th chunk
+    pipe = solver.ChunkPipeline(dp, ctx, R.FP32, chunk, ctx2=ctx2)
+    solves = []          # (flux of each completed pass over this rank's chunks)
+    launches = [0]
 
-    p = synth.stagnation_line(n_cells=args.cells)
-    ctx = R.Context(local)
-    tuned = None
-    if args.tile:
-        ctx.set_tiling(tile_width=args.tile)
-    elif precision == R.FP32 and not args.no_tune:
-        from paper_2604_11856_gb300 import autotune
-        tw, wpb, times = autotune.tune(ctx, p)
-        tuned = {"tile_width": tw, "cells_per_block": wpb, "candidates_ms": times}
-    dp = solver.DeviceProblem(p, ctx)
-    C, K = dp.C, p.grid.n
-    n_dirs = dp.rays.n_dirs
-    seg_lambda = C * n_dirs * K          # segments x directions x wavelengths per step
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    dt = torch.float32 if precision == R.FP32 else torch.float64
-    bufs = [(torch.empty((C, K), dtype=dt, device=dev), torch.empty((C, K), dtype=dt, device=dev))]
-    stream = ctx.stream
-
-    def step(ev_pair=None):
-        if ev_pair is not None:
-            ctx.set_profile_events(*ev_pair)
-        out = solver.solve(dp, ctx, precision, buffers=bufs)
-        if ev_pair is not None:
+    def enqueue(s, kev=None, mev=None):
+        j = s % len(mine)
+        if j == 0:
+            pipe.begin()
+            launches[0] += 2                    # cell validation + populations
+        k0, nk = mine[j]
+        if kev is not None:
+            ctx.set_profile_events(*kev)
+        pipe.step(k0, nk, march_events=mev)
+        if kev is not None:
             ctx.set_profile_events(None, None)
-        return out
+        # coefficients: cell and line validation, line prep, cell prep, bin bounds, count, scan, fill,
+        # line sum; march: ray validation, three FP32 copies, march, group sum; flux: part + sum
+        launches[0] += 9 + 6 + 2
+        if j == len(mine) - 1:
+            pipe.end()
+            with torch.cuda.stream(sa):
+                solves.append(pipe.q.clone())
+        return nk
 
-    def barrier():
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-
-    for _ in range(args.warmup):
-        step()
-    # one untimed step with the work counters on (evaluations, XU terms), then
-    # the timed steps without them
-    ctx.set_counters(True)
-    ctx.reset_stats()
-    step()
-    stats = ctx.get_stats()
-    ctx.set_counters(False)
-    ctx.sync()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for a, b in k3:   # materialise the events before handing them to the library
-        a.record(stream); b.record(stream)
-    barrier()
-    t_wall = time.perf_counter()
+    for s in range(args.warmup):
+        enqueue(s)
+    pipe.end()
+    barrier(dev, world)
+    solves.clear()
+    pipe.i = 0
+    K = args.steps
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in kev:   # materialise the events before handing them to the library
+        a.record(sa); b.record(sa)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_solve = torch.cuda.Event(enable_timing=True)
+    barrier(dev, world)
+    launches[0] = 0
+    cell_lambda = 0
+    seg_lambda = 0
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))              # evict L2 between steps (outside the timed window)
-            starts[i].record(stream)
-            step(k3[i])
-            ends[i].record(stream)
-        barrier()
-    t_wall = time.perf_counter() - t_wall
-    ctx.sync()
-    step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
-    k3_ms = [k3[i][0].elapsed_time(k3[i][1]) for i in range(args.steps)]
-    total_ms = float(np.sum(step_ms))
+        t_wall = time.perf_counter()
+        t0.record(sa)
+        for s in range(K):
+            nk = enqueue(s, kev[s], mev[s])
+            cell_lambda += C * nk
+            seg_lambda += nseg * nk
+            if s == len(mine) - 1:
+                ev_solve.record(sa)   # after the join of the first whole pass
+        pipe.end()
+        qsum = pipe.q if len(solves) == 0 else solves[0]
+        if world > 1:   # the only exchange: the P partial fluxes of the shards
+            with torch.cuda.stream(sa):
+                qred = qsum.clone()
+                dist.all_reduce(qred, op=dist.ReduceOp.SUM)
+        t1.record(sa)
+        barrier(dev, world)
+        t_wall = time.perf_counter() - t_wall
+    total_ms = t0.elapsed_time(t1)
+    solve_ms = t0.elapsed_time(ev_solve) if K >= len(mine) else None
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * C * K / (ms_per_step * 1e-3)
-    evals_per_step = stats["evaluations"]
-    k3_mean = float(np.mean(k3_ms))
-
-    # roofline of the line sum: transcendental (XU / MUFU) work the FP32
-    # profile needs: rcp + 2 rsqrt per evaluation, + ex2 for the Gaussian core
-    # and + ex2 for the correction term where they do not underflow
+        w = torch.tensor([float(cell_lambda), float(seg_lambda)], dtype=torch.float64, device=dev)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        cell_lambda, seg_lambda = float(w[0].item()), float(w[1].item())
+    ms_per_step = total_ms / K
+    value = cell_lambda / (total_ms * 1e-3)
+    k_ms = [a.elapsed_time(b) for a, b in kev]
+    m_ms = [a.elapsed_time(b) for a, b in mev]
+    march_mean, lsum_mean = float(np.mean(m_ms)), float(np.mean(k_ms))
     peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    if precision == R.FP32:
-        traffic = line_sum_traffic(C, K)
-        xu_ops = 3 * stats["evaluations"] + stats["gauss_terms"] + stats["correction_terms"]
-        peak = n_sm * 16 * sm_max / 1e9               # Gop/s: 16 XU lanes per SM per clock
-        achieved = xu_ops / (k3_mean * 1e-3) / 1e9
-        roof = {"bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)", "achieved": achieved, "peak": peak,
-                "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_algorithmic_bytes": C * K * 8,   # kappa and j written once, FP32
-                "kernel": "k_line_sum_f32", "kernel_ms": k3_mean, "evaluations": evals_per_step,
-                "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"}
-    else:
-        # FP64: about 40 FP64 operations per evaluation (two exponentials, two square roots, the bracket),
-        # 2 FP64 FMA lanes per SM per clock
-        fp64_ops = 40.0 * evals_per_step
-        peak = n_sm * 2 * 2 * sm_max / 1e9
-        achieved = fp64_ops / (k3_mean * 1e-3) / 1e9
-        roof = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_line_sum_f64", "kernel_ms": k3_mean,
-                "evaluations": evals_per_step}
-
-    out = {"metric": METRIC, "value": value, "unit": "cell·λ points/s", "n_gpus": world, "steps": args.steps,
+    # march: per launch it reads each cell's kappa / j columns once from DRAM and writes q_lambda
+    steps_nk = [mine[s % len(mine)][1] for s in range(K)]
+    nk_mean = float(np.mean(steps_nk))
+    uniq = C * nk_mean * 8 + P * nk_mean * 4
+    seglam_launch = nseg * nk_mean
+    gather = seglam_launch * 8 / (march_mean * 1e-3) / 1e9
+    l2 = l2_gather_peak(local)
+    l2_peak = max(l2["GBps_48MB_table"], l2["GBps_96MB_table"])
+    march = {"kernel": "k_march1 (single-direction rays, FP32; + ray validation, FP32 copies, bundle plan, "
+                       "group sum)",
+             "kernel_ms": march_mean, "segments": nseg, "segment_lambda_per_launch": seglam_launch,
+             "ray_lambda_segments_per_s": seglam_launch / (march_mean * 1e-3),
+             "gather_bytes_per_launch": seglam_launch * 8, "gather_GBps": gather,
+             "l2_gather_peak": l2, "frac_of_l2_gather_peak": gather / l2_peak,
+             "dram_unique_bytes_per_launch": uniq,
+             "dram_traffic_bytes_per_launch": march_traffic(C, nk_mean),
+             "dram_frac_of_hbm_peak": uniq / (march_mean * 1e-3) / 1e9 / hbm,
+             "timed_inside": "the two-stream pipeline (overlaps the next chunk's line sum)"}
+    roof = {"bound": "hbm", "achieved": gather, "peak": hbm, "unit": "GB/s", "frac": gather / hbm,
+            "traffic": march_traffic(C, nk_mean),
+            "kernel": "k_march1 (single-direction rays, FP32)", "kernel_ms": march_mean,
+            "algorithmic_bytes": seglam_launch * 8,
+            "algorithmic_unit": "8 B (FP32 kappa + j of the next cell) gathered per segment-wavelength, x the "
+                                "launch's segments x columns",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
+            "served_from": "L2: DRAM sees one pass over the chunk's kappa / j (traffic); the gathers hit L2, "
+                           "whose measured gather bandwidth is in march.l2_gather_peak",
+            "frac_of_l2_gather_peak": gather / l2_peak}
+    out = {"metric": METRIC, "value": value, "unit": "cell·λ points/s", "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32" if precision == R.FP32 else "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "precision": args.precision + ("-chosen" if precision == R.FP32 else "-plain"),
-                      "cells": C, "lines": len(p.lines), "grid_points": K, "directions": n_dirs,
-                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
-                      "tiling": tuned},
-           "secondary": {"ray_lambda_segments_per_s": world * seg_lambda / (ms_per_step * 1e-3),
-                         "profile_evaluations_per_s": world * evals_per_step / (ms_per_step * 1e-3),
-                         "line_sum_ms": k3_mean, "wall_s": t_wall,
-                         "pairs_per_step": stats["pairs"],
-                         "gauss_terms_per_step": stats["gauss_terms"],
-                         "correction_terms_per_step": stats["correction_terms"]},
-           "roofline": roof, "clocks": clk.summary(), "gpu_launches": None}
-    # launches per step (checked against the ncu launch list): populations + its cell
-    # validation; line and cell validation, line prep, cell prep, bin bounds, count, scan,
-    # fill, line sum; ray validation, march, flux part + sum; FP32 adds three copies of ray
-    # data to float.  The slab rays are built once, before the timed region.
-    out["gpu_launches"] = (18 if precision == R.FP32 else 15) * args.steps
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD if not (args.ab_small or args.ab_cells) else f"reduced afterbody {C} cells",
+                      "precision": "fp32-chosen", "cells": C, "lines": len(p.lines), "grid_points": n,
+                      "chunk_points": chunk, "surface_points": P, "rays": int(dp.rays.n_dirs), "segments": nseg,
+                      "step": "one 65,536-point spectral chunk of the solve (16 steps = one solve), two-stream "
+                              "pipeline, populations at each solve's first chunk",
+                      "l2": "inputs larger than L2 (a 42 GB kappa / j table per step)",
+                      "parallelism": f"spectral shards x{world} (every {world}-th chunk a rank, one FP64 "
+                                     f"all-reduce of the wall flux)" if world > 1 else "one GPU"},
+           "secondary": {"ray_lambda_segments_per_s": seg_lambda / (total_ms * 1e-3),
+                         "solve_s": solve_ms * 1e-3 if solve_ms else None,
+                         "line_sum_ms_mean": lsum_mean, "march_ms_mean": march_mean, "wall_s": t_wall,
+                         "q_mean_W_cm2": float(qsum.mean().item()) if world == 1 else None},
+           "roofline": roof, "march": march, "clocks": clk.summary(), "gpu_launches": launches[0]}
 
-    if not args.no_fp64 and precision == R.FP32:
-        bufs64 = [(torch.empty((C, K), dtype=torch.float64, device=dev),
-                   torch.empty((C, K), dtype=torch.float64, device=dev))]
-        r64 = solver.solve(dp, ctx, R.FP64, buffers=bufs64)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(1.0)
-        e0.record(stream)
-        r64 = solver.solve(dp, ctx, R.FP64, buffers=bufs64)
-        e1.record(stream)
-        ctx.sync()
-        ms64 = e0.elapsed_time(e1)
-        r32 = step()
-        ctx.sync()
-        q32, q64 = float(r32["q"].item()), float(r64["q"].item())
-        out["fp64_plain"] = {"value": C * K / (ms64 * 1e-3), "ms_per_step": ms64, "q_W_cm2": q64,
-                             "fp32_q_W_cm2": q32, "fp32_q_rel_err": abs(q32 / q64 - 1)}
-        del bufs64
+    # the line sums of the timed chunks again, alone, with the work counters on: XU work per launch
+    ctx.set_counters(True)
+    xu, ev_total, lsum_alone = 0, 0, []
+    kap, em = pipe.buffers[0]
+    for s in range(min(K, len(mine))):
+        k0, nk = mine[s]
+        ctx.reset_stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(sa)
+        R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, k0, nk, R.FP32, kap, em)
+        b.record(sa)
+        st = ctx.get_stats()
+        xu += 3 * st["evaluations"] + st["gauss_terms"] + st["correction_terms"]
+        ev_total += st["evaluations"]
+        lsum_alone.append(a.elapsed_time(b))
+    ctx.set_counters(False)
+    n_counted = min(K, len(mine))
+    xu_peak = n_sm * 16 * sm_max / 1e9
+    out["line_sum"] = {"kernel": "k_line_sum_f32", "bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)",
+                       "evaluations_per_step": ev_total / n_counted,
+                       "in_pipeline_ms_mean": lsum_mean,
+                       "in_pipeline_xu_frac": (xu / n_counted) / (lsum_mean * 1e-3) / 1e9 / xu_peak,
+                       "alone_ms_mean": float(np.mean(lsum_alone)),
+                       "alone_xu_frac": xu / (np.sum(lsum_alone) * 1e-3) / 1e9 / xu_peak,
+                       "peak_gops": xu_peak,
+                       "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)",
+                       "note": "alone: binning + line sum of each counted chunk, not overlapped"}
 
     if not args.no_e2e:
-        # end to end through the public API: host arrays -> pinned staging -> device -> q on the host
-        ectx = R.Context(local)
-        solver.solve_host(p, precision, ctx=ectx)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        n_e2e = max(1, min(3, args.steps))
-        for _ in range(n_e2e):
-            qh, bi, bo = solver.solve_host(p, precision, ctx=ectx)
-        te = (time.perf_counter() - t0) / n_e2e
-        out["e2e"] = {"value": world * C * K / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
-                      "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3}
-        ectx.close()
-    if not args.no_serve:
-        out["served"] = served(p, args, local)
+        # end to end through the public API: host arrays -> pinned staging -> device -> q on the host,
+        # one chunk a call, the chunk cut in two halves pipelined on the two streams
+        n_e2e = max(1, min(3, K))
+        solver.solve_host(p, R.FP32, chunk // 2, ctx=ctx, ctx2=ctx2, k_start=mine[0][0], k_stop=sum(mine[0]))
+        barrier(dev, world)
+        t0w = time.perf_counter()
+        cl_e2e = 0
+        for s in range(n_e2e):
+            k0, nk = mine[s % len(mine)]
+            _qh, bi, bo = solver.solve_host(p, R.FP32, chunk // 2, ctx=ctx, ctx2=ctx2, k_start=k0, k_stop=k0 + nk)
+            cl_e2e += C * nk
+        te = time.perf_counter() - t0w
+        out["e2e"] = {"value": world * cl_e2e / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
+                      "d2h_bytes_per_step": bo, "ms_per_step": te / n_e2e * 1e3, "steps": n_e2e,
+                      "note": "each step builds the ray segments from the geometry as well"}
+    if not args.no_secondary and world == 1:
+        ctx.close(); ctx2.close()
+        del pipe, dp, solves
+        torch.cuda.empty_cache()
+        out["stagnation"] = stagnation_block(args, local, world, rank)
+        if not args.no_serve:
+            from paper_2604_11856_gb300 import synth
+            pst = synth.stagnation_line()
+            out["served"] = served(pst, args, local)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
         out["cpu_baseline"].pop("seconds")
@@ -831,6 +924,114 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def stagnation_block(args, local, world, rank, fp64=True):
+    """The stagnation-line step (200 cells, 320k lines, 1e6 points, 16-mu
+    tangent slab + normal ray, one whole solve a step): FP32-chosen with
+    autotuned tiling, the line sum's XU roofline, and one FP64-plain step."""
+    import torch
+    from paper_2604_11856_gb300 import autotune
+    from paper_2604_11856_gb300 import rapral as R
+    from paper_2604_11856_gb300 import solver, synth
+
+    dev = torch.device("cuda", local)
+    p = synth.stagnation_line(n_cells=args.cells)
+    ctx = R.Context(local)
+    tw, wpb, times = autotune.tune(ctx, p)
+    tuned = {"tile_width": tw, "cells_per_block": wpb, "candidates_ms": times}
+    dp = solver.DeviceProblem(p, ctx)
+    C, K = dp.C, p.grid.n
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    bufs = [(torch.empty((C, K), dtype=torch.float32, device=dev), torch.empty((C, K), dtype=torch.float32, device=dev))]
+    stream = ctx.stream
+    for _ in range(3):
+        solver.solve(dp, ctx, R.FP32, buffers=bufs)
+    ctx.set_counters(True)
+    ctx.reset_stats()
+    solver.solve(dp, ctx, R.FP32, buffers=bufs)
+    stats = ctx.get_stats()
+    ctx.set_counters(False)
+    ctx.sync()
+    steps = 20
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    k3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in k3:
+        a.record(stream); b.record(stream)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            ctx.set_profile_events(*k3[i])
+            r32 = solver.solve(dp, ctx, R.FP32, buffers=bufs)
+            ctx.set_profile_events(None, None)
+            ev[i][1].record(stream)
+        ctx.sync()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    kms = float(np.mean([a.elapsed_time(b) for a, b in k3]))
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    xu_ops = 3 * stats["evaluations"] + stats["gauss_terms"] + stats["correction_terms"]
+    peak = n_sm * 16 * sm_max / 1e9
+    out = {"workload": STAG_WORKLOAD, "precision": "fp32-chosen", "steps": steps, "warmup": 3, "ms_per_step": ms,
+           "value": C * K / (ms * 1e-3), "unit": "cell·λ points/s", "tiling": tuned,
+           "ray_lambda_segments_per_s": C * dp.rays.n_dirs * K / (ms * 1e-3),
+           "profile_evaluations_per_s": stats["evaluations"] / (ms * 1e-3),
+           "l2": "flushed between steps (512 MB write)",
+           "line_sum_roofline": {"bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)", "achieved": xu_ops / (kms * 1e-3) / 1e9,
+                                 "peak": peak, "unit": "Gop/s", "frac": xu_ops / (kms * 1e-3) / 1e9 / peak,
+                                 "traffic": line_sum_traffic(C, K), "traffic_algorithmic_bytes": C * K * 8,
+                                 "kernel": "k_line_sum_f32", "kernel_ms": kms, "evaluations": stats["evaluations"],
+                                 "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"},
+           "clocks": clk.summary()}
+    q32 = float(r32["q"].item())
+    if fp64:
+        bufs64 = [(torch.empty((C, K), dtype=torch.float64, device=dev),
+                   torch.empty((C, K), dtype=torch.float64, device=dev))]
+        solver.solve(dp, ctx, R.FP64, buffers=bufs64)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        r64 = solver.solve(dp, ctx, R.FP64, buffers=bufs64)
+        e1.record(stream)
+        ctx.sync()
+        ms64 = e0.elapsed_time(e1)
+        q64 = float(r64["q"].item())
+        out["fp64_plain"] = {"value": C * K / (ms64 * 1e-3), "ms_per_step": ms64, "q_W_cm2": q64,
+                             "fp32_q_W_cm2": q32, "fp32_q_rel_err": abs(q32 / q64 - 1)}
+        del bufs64
+    del bufs
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_stagnation(args):
+    """--workload stagnation: the stagnation-line block on its own."""
+    world, rank, local = dist_setup()
+    out = stagnation_block(args, local, world, rank, fp64=not args.no_fp64)
+    print(json.dumps(out))
+    return 0
+
+
+def run_serve(args):
+    """--workload serve: the served-request study on its own."""
+    from paper_2604_11856_gb300 import synth
+    world, rank, local = dist_setup()
+    print(json.dumps({"workload": "served requests", **served(synth.stagnation_line(), args, local)}))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return oracle_phases(args) if args.oracle_phases else run_reference(args)
+    runs = {"afterbody": run_headline, "stagnation": run_stagnation, "serve": run_serve, "batch": run_batch,
+            "fibonacci": run_fibonacci, "qss": run_qss, "continuum": run_continuum, "voigt": run_voigt}
+    return runs[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -465,6 +465,289 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && MAXD == 1 && V > 1)  ?
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_march1: the FP32 march of single-direction, cell-valued bundles (the
+// axisymmetric lines of sight), the hot kernel of the afterbody.
+//
+// Same work and results contract as k_march<float, 2, 1, 8>, organised for
+// fewer instructions per segment-wavelength:
+//  * lane l owns two ADJACENT columns (base + 2l, base + 2l + 1): one 8-byte
+//    load fetches both, for kappa and for j (a warp reads 256 contiguous
+//    bytes of a row);
+//  * node values are carried doubled (K = kappa_a + kappa_b, the sum of the
+//    two cells at a face), with the segment length halved to match, which
+//    removes the averaging multiplies;
+//  * optically thin steps (|dtau| < 0.5) use I' = I + s f (j_f - kappa_f I)
+//    + s p (j_n - j_f), with p = (1 - f)/dtau from one degree-6 series and
+//    f = 1 - dtau p: one polynomial instead of two and no exponential.  With
+//    e = 1 - dtau f >= 0.6 the subtraction inside costs at most a factor
+//    1/e of relative rounding, so it stays in FP32 accuracy.  Thick steps use
+//    the exponential form I' = I e + s f j_f + s p (j_n - j_f) with
+//    f = (1 - e)/dtau, p = (1 - f)/dtau;
+//  * the staged list holds, for step j, the segment's halved length and the
+//    row of the cell PF steps ahead, so each step issues the loads it will use
+//    PF steps later and no load is exposed at the 32-segment staging seams;
+//  * the bundles of a block are dealt to its eight warps longest first
+//    (k_march_plan), so the warps finish together at the block's reduction.
+// Every slice still Kahan-sums its bundles in a fixed order and the slices
+// and groups are added in fixed order: results do not depend on timing.
+// Conditions (checked by the launcher): kappa, emis and the wall row 8-byte
+// aligned, ld and nk even, nk >= 64.
+
+constexpr int M1_PF = 2;        // steps between a load and its use
+constexpr int M1_SLICES = 8;    // warps (bundle slices) per block
+
+struct M1Stage {
+    float sh;       // half the segment length (x the direction scale)
+    int row;        // cell whose values step j + M1_PF needs (its next cell); 0 past the end
+};
+
+// The thin-step series p(t) = (1 - f)/t = sum_n (-t)^n / (n + 2)!, n = 0..6
+// (truncation below 4e-8 relative at |t| = 0.5), on a packed pair.
+__device__ __forceinline__ float2 m1_series(float2 t) {
+    const auto c2 = [](float c) { return make_float2(c, c); };
+    float2 p = __ffma2_rn(t, c2(1.0f / 40320.0f), c2(-1.0f / 5040.0f));
+    p = __ffma2_rn(t, p, c2(1.0f / 720.0f));
+    p = __ffma2_rn(t, p, c2(-1.0f / 120.0f));
+    p = __ffma2_rn(t, p, c2(1.0f / 24.0f));
+    p = __ffma2_rn(t, p, c2(-1.0f / 6.0f));
+    return __ffma2_rn(t, p, c2(0.5f));
+}
+
+// One step of one column with doubled node values Kf, Jf (far), Jn (near) and
+// half length sh: the thin or the thick form by |t|.
+__device__ __forceinline__ float m1_step1(float I, float Kf, float Jf, float Jn, float sh) {
+    const float t = Kf * sh;   // kappa_far x length
+    if (fabsf(t) < (float)RAPRAL_THIN_F32) {
+        float p = fmaf(t, 1.0f / 40320.0f, -1.0f / 5040.0f);
+        p = fmaf(t, p, 1.0f / 720.0f);
+        p = fmaf(t, p, -1.0f / 120.0f);
+        p = fmaf(t, p, 1.0f / 24.0f);
+        p = fmaf(t, p, -1.0f / 6.0f);
+        p = fmaf(t, p, 0.5f);
+        const float f = fmaf(-t, p, 1.0f);
+        const float A = fmaf(-Kf, I, Jf);
+        return fmaf(sh, fmaf(f, A, p * (Jn - Jf)), I);
+    }
+    const float e = ex2f_approx(-1.44269504f * t);
+    const float r = recip(t);
+    const float f = (1.0f - e) * r;
+    const float p = (1.0f - f) * r;
+    return fmaf(sh, fmaf(f, Jf, p * (Jn - Jf)), I * e);
+}
+
+// One step of both columns: packed when both are thin.
+__device__ __forceinline__ void m1_step(float2& I, float2 Kf, float2 Jf, float2 Jn, float sh) {
+    const float2 t = __fmul2_rn(Kf, make_float2(sh, sh));
+    if (fmaxf(fabsf(t.x), fabsf(t.y)) < (float)RAPRAL_THIN_F32) {
+        const float2 p = m1_series(t);
+        const float2 f = __ffma2_rn(make_float2(-t.x, -t.y), p, make_float2(1.0f, 1.0f));
+        const float2 A = __ffma2_rn(make_float2(-Kf.x, -Kf.y), I, Jf);
+        const float2 dJ = __fadd2_rn(Jn, make_float2(-Jf.x, -Jf.y));
+        const float2 B = __ffma2_rn(f, A, __fmul2_rn(p, dJ));
+        I = __ffma2_rn(make_float2(sh, sh), B, I);
+    } else {
+        I.x = m1_step1(I.x, Kf.x, Jf.x, Jn.x, sh);
+        I.y = m1_step1(I.y, Kf.y, Jf.y, Jn.y, sh);
+    }
+}
+
+// Bundle plan: for each (point p, group g) the group's bundles (the point's
+// g-th, (g+G)-th, ... bundle) dealt to M1_SLICES slices longest first (greedy
+// to the least-loaded slice, ties to the lower slice; equal lengths in index
+// order).  plan[] lists each group's bundles slice by slice, starting at the
+// group's base; soff[(p G + g)(M1_SLICES + 1) + s] is where slice s starts.
+// Groups of more than 1024 bundles are dealt round-robin in index order.
+__global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ point_off,
+                                                    const int64_t* __restrict__ seg_off, int G,
+                                                    int32_t* __restrict__ plan, int32_t* __restrict__ soff) {
+    const int64_t p = blockIdx.x / G;
+    const int g = (int)(blockIdx.x % G);
+    const int64_t pb0 = point_off[p];
+    const int64_t nb = point_off[p + 1] - pb0;
+    const int64_t m = nb > g ? (nb - g + G - 1) / G : 0;                     // bundles of this group
+    const int64_t base = pb0 + (int64_t)g * (nb / G) + (g < nb % G ? g : nb % G);   // bundles of groups before
+    int32_t* so = soff + blockIdx.x * (M1_SLICES + 1);
+    __shared__ int64_t len[1024];
+    __shared__ int16_t order[1024];
+    __shared__ int8_t slice_of[1024];
+    __shared__ int32_t cnt[M1_SLICES + 1];
+    if (m > 1024) {   // round-robin in index order
+        for (int64_t k = threadIdx.x; k < m; k += blockDim.x) {
+            const int s = (int)(k % M1_SLICES);
+            const int64_t per = m / M1_SLICES, extra = m % M1_SLICES;
+            const int64_t start = s * per + (s < extra ? s : extra);
+            plan[base + start + k / M1_SLICES] = (int32_t)(pb0 + g + k * G);
+        }
+        if (threadIdx.x <= M1_SLICES) {
+            const int s = threadIdx.x;
+            const int64_t per = m / M1_SLICES, extra = m % M1_SLICES;
+            so[s] = (int32_t)(base + s * per + (s < extra ? s : extra));
+        }
+        return;
+    }
+    const int mm = (int)m;
+    for (int k = threadIdx.x; k < mm; k += blockDim.x) {
+        const int64_t b = pb0 + g + (int64_t)k * G;
+        len[k] = seg_off[b + 1] - seg_off[b];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < mm; k += blockDim.x) {   // rank: longer first, then lower index
+        const int64_t lk = len[k];
+        int r = 0;
+        for (int q = 0; q < mm; ++q) r += (len[q] > lk) || (len[q] == lk && q < k);
+        order[r] = (int16_t)k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t load[M1_SLICES];
+        for (int s = 0; s < M1_SLICES; ++s) { load[s] = 0; cnt[s] = 0; }
+        for (int r = 0; r < mm; ++r) {
+            const int k = order[r];
+            int best = 0;
+            for (int s = 1; s < M1_SLICES; ++s) best = load[s] < load[best] ? s : best;
+            slice_of[k] = (int8_t)best;
+            load[best] += len[k] + 1;
+            ++cnt[best];
+        }
+        int acc = 0;
+        for (int s = 0; s < M1_SLICES; ++s) { const int c = cnt[s]; cnt[s] = acc; acc += c; }
+        cnt[M1_SLICES] = acc;
+        for (int s = 0; s <= M1_SLICES; ++s) so[s] = (int32_t)(base + cnt[s]);
+        // each slice's bundles, longest first
+        int fill[M1_SLICES];
+        for (int s = 0; s < M1_SLICES; ++s) fill[s] = cnt[s];
+        for (int r = 0; r < mm; ++r) {
+            const int k = order[r];
+            plan[base + fill[slice_of[k]]++] = (int32_t)(pb0 + g + (int64_t)k * G);
+        }
+    }
+}
+
+// The lane's two columns of one row: one 8-byte load when the pair is
+// aligned (VEC), else two 4-byte loads (the second column is d1 = 0 or 1
+// after the first; 0 where a lane's second column lies past the range).
+template <bool VEC>
+__device__ __forceinline__ float2 m1_load(const float* __restrict__ p, int d1) {
+    if constexpr (VEC) return *reinterpret_cast<const float2*>(p);
+    return make_float2(p[0], p[d1]);
+}
+
+// The march of bundle b over the lane's two columns (doubled node values).
+template <bool VEC>
+__device__ __forceinline__ float2 m1_bundle(const MarchArgs& a, int64_t b, float sc, M1Stage* st, int lane,
+                                            const float* __restrict__ kb, const float* __restrict__ jb, int d1,
+                                            int ld, float2 I) {
+    const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
+    if (s1 <= s0) return I;
+    float2 kc, jc;
+    {
+        const int c0 = a.seg_cell[s0];
+        kc = m1_load<VEC>(kb + (int64_t)c0 * ld, d1);
+        jc = m1_load<VEC>(jb + (int64_t)c0 * ld, d1);
+    }
+    float2 Kf = __fadd2_rn(kc, kc), Jf = __fadd2_rn(jc, jc);
+    const float hs = 0.5f * sc;
+    // ring of loads in flight: values of the next cells of the following PF segments
+    float2 rk[M1_PF], rj[M1_PF];
+#pragma unroll
+    for (int q = 0; q < M1_PF; ++q) {
+        const int64_t i = s0 + q;   // segment i's next cell is cell i + 1
+        const int c = (i < s1 - 1) ? a.seg_cell[i + 1] : 0;
+        rk[q] = m1_load<VEC>(kb + (int64_t)c * ld, d1);
+        rj[q] = m1_load<VEC>(jb + (int64_t)c * ld, d1);
+    }
+    for (int64_t g = s0; g < s1 - 1; g += 32) {
+        const int64_t mine = g + lane;
+        __syncwarp();
+        const int64_t ahead = mine + M1_PF;   // the segment whose next cell this entry fetches
+        st[lane].sh = mine < s1 - 1 ? seg_len<float>(a, mine) * hs : 0.0f;
+        st[lane].row = ahead < s1 - 1 ? a.seg_cell[ahead + 1] : 0;
+        __syncwarp();
+        const int n = s1 - 1 - g < 32 ? (int)(s1 - 1 - g) : 32;
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const M1Stage e = st[j];
+            const float2 kx = rk[0], jx = rj[0];
+#pragma unroll
+            for (int q = 0; q + 1 < M1_PF; ++q) { rk[q] = rk[q + 1]; rj[q] = rj[q + 1]; }
+            rk[M1_PF - 1] = m1_load<VEC>(kb + (int64_t)e.row * ld, d1);
+            rj[M1_PF - 1] = m1_load<VEC>(jb + (int64_t)e.row * ld, d1);
+            const float2 Kn = __fadd2_rn(kc, kx), Jn = __fadd2_rn(jc, jx);
+            m1_step(I, Kf, Jf, Jn, e.sh);
+            Kf = Kn; Jf = Jn; kc = kx; jc = jx;
+        }
+    }
+    // last segment: its near node is its own cell's value
+    m1_step(I, Kf, Jf, __fadd2_rn(jc, jc), seg_len<float>(a, s1 - 1) * hs);
+    return I;
+}
+
+// Block (point, bundle group) x tile of 64 columns; warp w is slice w of the
+// group's plan.  The last tile is shifted back to end at nk when nk >= 64
+// (columns below the tile are computed again and not written); a range
+// shorter than 64 columns clamps the reads of lanes past it and writes
+// nothing there.
+template <bool VEC>
+__global__ void __launch_bounds__(256, RAPRAL_MARCH_MINB) k_march1(MarchArgs a, int lgG, const int32_t* __restrict__ plan,
+                                                                   const int32_t* __restrict__ soff,
+                                                                   float* __restrict__ part) {
+    if (*a.status) return;
+    constexpr int TW = 64, SLC = M1_SLICES;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nk = (int)a.nk;
+    const int tile0 = (int)blockIdx.y * TW;
+    const int base = (tile0 + TW > nk && nk >= TW) ? nk - TW : tile0;
+    const int col = base + 2 * lane;                  // the lane's columns: col, col + 1
+    const int c0 = col < nk ? col : nk - 1;           // clamped reads (VEC: never clamped)
+    const int d1 = (col + 1 < nk ? col + 1 : nk - 1) - c0;
+    const bool own0 = col >= tile0 && col < nk, own1 = col + 1 >= tile0 && col + 1 < nk;
+    const float* kb = reinterpret_cast<const float*>(a.kappa) + c0;
+    const float* jb = reinterpret_cast<const float*>(a.emis) + c0;
+    __shared__ M1Stage stage_all[SLC][32];
+    M1Stage* st = stage_all[warp];
+    float2 acc = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
+    const int32_t* so = soff + (int64_t)blockIdx.x * (SLC + 1);
+    const int k1 = so[warp + 1];
+    for (int k = so[warp]; k < k1; ++k) {
+        const int64_t b = plan[k];
+        const int64_t d0 = a.dir_off[b];
+        if (a.dir_off[b + 1] == d0) continue;
+        float2 I0 = make_float2(0.f, 0.f);
+        if (a.wall_row && a.bundle_wall[b]) I0 = m1_load<VEC>(reinterpret_cast<const float*>(a.wall_row) + c0, d1);
+        const float2 I = m1_bundle<VEC>(a, b, a.dir_scale_f[d0], st, lane, kb, jb, d1, (int)a.ld, I0);
+        if (a.I_out) {
+            float* io = reinterpret_cast<float*>(a.I_out) + d0 * a.nk + col;
+            if (VEC && own0) {
+                *reinterpret_cast<float2*>(io) = I;
+            } else {
+                if (own0) io[0] = I.x;
+                if (own1) io[1] = I.y;
+            }
+        }
+        const float w = a.dir_weight_f[d0];
+        // compensated sum over the slice's bundles
+        const float2 y = make_float2(w * I.x - comp.x, w * I.y - comp.y);
+        const float2 tt = make_float2(acc.x + y.x, acc.y + y.y);
+        comp = make_float2((tt.x - acc.x) - y.x, (tt.y - acc.y) - y.y);
+        acc = tt;
+    }
+    __shared__ float2 red[SLC][32];
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        float2 s = red[0][lane];
+        for (int q = 1; q < SLC; ++q) s = make_float2(s.x + red[q][lane].x, s.y + red[q][lane].y);
+        float* dst = (lgG == 0 ? reinterpret_cast<float*>(a.q_lambda) : part) + (int64_t)blockIdx.x * a.nk + col;
+        if (VEC && own0) {
+            *reinterpret_cast<float2*>(dst) = s;
+        } else {
+            if (own0) dst[0] = s.x;
+            if (own1) dst[1] = s.y;
+        }
+    }
+}
+
 // Planck intensity at the wall temperature for the columns of a range.
 template <class T>
 __global__ void k_planck_row(double lam_min, double h, int64_t k0, int64_t nk, double T_wall, Phys ph, T* row) {
@@ -630,6 +913,48 @@ cudaError_t march_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t
     return cudaGetLastError();
 }
 
+// k_march1 applies: FP32 cell-valued single-direction bundles, eight or more
+// a point, and the 8-byte alignment and even sizes of its paired columns.
+static bool march1_applies(const MarchArgs& a, int maxd, int maxb, bool nodes) {
+    return !nodes && maxd <= 1 && maxb >= 8 && a.ld <= 2147483647LL;
+}
+
+// Paired 8-byte loads and stores: every row of kappa / emis, q_lambda, I_out
+// and the wall row starts 8-byte aligned and the range is whole tiles or
+// ends on an even column past the first tile.
+static bool march1_vec(const MarchArgs& a, int64_t nk, const void* part) {
+    const auto al8 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; };
+    return nk >= 64 && (nk & 1) == 0 && (a.ld & 1) == 0 && al8(a.kappa) && al8(a.emis) && al8(a.q_lambda) &&
+           al8(part) && (a.I_out == nullptr || al8(a.I_out));
+}
+
+static cudaError_t march1_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int G, void* part,
+                                 int32_t* plan, int32_t* soff) {
+    int lgG = 0;
+    while ((1 << lgG) < G) ++lgG;
+    k_march_plan<<<(unsigned)(P * G), 128, 0, ctx->stream>>>(a.point_off, a.seg_off, G, plan, soff);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    MarchArgs b = a;
+    b.wall_row = nullptr;
+    if (a.T_wall > 0.0) {   // the wall row follows the group partials in the scratch
+        float* row = reinterpret_cast<float*>(part) + (G > 1 ? P * G * nk : 0);
+        k_planck_row<float><<<(unsigned)std::min<int64_t>(div_up(nk, 256), 1024), 256, 0, ctx->stream>>>(
+            a.lam_min, a.h, a.k0, nk, a.T_wall, a.ph, row);
+        b.wall_row = row;
+    }
+    dim3 g((unsigned)(P << lgG), div_up(nk, 64));
+    if (march1_vec(a, nk, part))
+        k_march1<true><<<g, 32 * M1_SLICES, 0, ctx->stream>>>(b, lgG, plan, soff, reinterpret_cast<float*>(part));
+    else
+        k_march1<false><<<g, 32 * M1_SLICES, 0, ctx->stream>>>(b, lgG, plan, soff, reinterpret_cast<float*>(part));
+    e = cudaGetLastError();
+    if (e != cudaSuccess || G == 1) return e;
+    k_group_sum<float><<<(unsigned)std::min<int64_t>(div_up(P * nk, 256), 152 * 16), 256, 0, ctx->stream>>>(
+        reinterpret_cast<const float*>(part), G, P, nk, reinterpret_cast<float*>(a.q_lambda), a.status);
+    return cudaGetLastError();
+}
+
 // Eight bundle slices for eight or more bundles a point, else one; V > 1
 // columns a lane only for one-direction bundles in FP32 and ranges of at
 // least one tile.
@@ -681,9 +1006,16 @@ static int march_groups(const rapral_rays* r) {
 
 static size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
+// FP32 scratch: the FP32 copies, then k_march1's bundle plan and slice starts.
+static size_t march_plan_bytes(const rapral_rays* r) {
+    return round256((size_t)(r->n_bundles + (int64_t)r->n_points * march_groups(r) * (M1_SLICES + 1) + 64) *
+                    sizeof(int32_t));
+}
+
 size_t march_scratch_bytes(const rapral_rays* r, int64_t nk, int precision) {
     size_t bytes = 0;
-    if (precision == RAPRAL_FP32) bytes = round256((size_t)(r->n_segments + 2 * r->n_dirs + 128) * sizeof(float));
+    if (precision == RAPRAL_FP32)
+        bytes = round256((size_t)(r->n_segments + 2 * r->n_dirs + 128) * sizeof(float)) + march_plan_bytes(r);
     const int G = march_groups(r);
     const size_t el = precision == RAPRAL_FP64 ? sizeof(double) : sizeof(float);
     if (G > 1) bytes += (size_t)r->n_points * G * nk * el;
@@ -707,8 +1039,10 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
                                r->node_values != 0);
     // FP32 copies of the path lengths, direction scales and weights, then the group partials
     float* f = reinterpret_cast<float*>(scratch);
-    void* part = reinterpret_cast<char*>(scratch) +
-                 round256((size_t)(r->n_segments + 2 * r->n_dirs + 128) * sizeof(float));
+    const size_t copies = round256((size_t)(r->n_segments + 2 * r->n_dirs + 128) * sizeof(float));
+    int32_t* plan = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(scratch) + copies);
+    int32_t* soff = plan + ((r->n_bundles + 63) / 64) * 64;
+    void* part = reinterpret_cast<char*>(scratch) + copies + march_plan_bytes(r);
     float* fd = f + ((r->n_segments + 63) / 64) * 64;
     float* fw = fd + ((r->n_dirs + 63) / 64) * 64;
     if (r->n_segments > 0)
@@ -721,6 +1055,8 @@ cudaError_t launch_march(rapral_ctx* ctx, const rapral_rays* r, const void* kapp
             r->dir_weight, r->n_dirs, fw);
     }
     a.seg_ds_f = f; a.dir_scale_f = fd; a.dir_weight_f = fw;
+    if (march1_applies(a, r->max_dirs, r->max_bundles_per_point, r->node_values != 0))
+        return march1_launch(ctx, a, r->n_points, nk, G, part, plan, soff);
     return march_t<float>(ctx, a, r->n_points, nk, r->max_dirs, r->max_bundles_per_point, G, part,
                           r->node_values != 0);
 }

@@ -59,13 +59,17 @@ def request_bytes(problem, precision, chunk=CHUNK):
 
 
 class Server:
-    """`slots` concurrent workers on one GPU, admission by a byte budget."""
+    """`slots` concurrent workers on one GPU, admission by a byte budget.
 
-    def __init__(self, lines, species, device=0, slots=4, budget_bytes=150 << 30, queue_limit=512, chunk=CHUNK):
+    The budget defaults to the device's free memory once the resident line
+    list is loaded, less `reserve_bytes`, capped at `cap_bytes` (150 GB, the
+    served configuration's HBM budget)."""
+
+    def __init__(self, lines, species, device=0, slots=4, budget_bytes=None, queue_limit=512, chunk=CHUNK,
+                 reserve_bytes=16 << 30, cap_bytes=150 * 10 ** 9):
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
         self.chunk = chunk
-        self.budget = int(budget_bytes)
         self.queue_limit = queue_limit
         boot = R.Context(device)
         # resident line list and species database, shared by every request
@@ -73,6 +77,10 @@ class Server:
         self.dspecies = R.DeviceSpecies(species, self.device)
         torch.cuda.synchronize(self.device)
         boot.close()
+        if budget_bytes is None:
+            free, _total = torch.cuda.mem_get_info(self.device)
+            budget_bytes = min(cap_bytes, max(0, free - reserve_bytes))
+        self.budget = int(budget_bytes)
         self.pending = collections.deque()
         self.cv = threading.Condition()
         self.in_use = 0

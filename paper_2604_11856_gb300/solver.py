@@ -52,6 +52,88 @@ def shard_range(n, rank, world, align=512):
     return k0, k1 - k0
 
 
+class ChunkPipeline:
+    """A problem's spectral chunks enqueued one at a time on two streams:
+    chunk i's coefficients on ctx's stream (A), its march and flux on ctx2's
+    stream (B), with two kappa / j buffers, so that the line sum of chunk
+    i + 1 overlaps the march of chunk i.  `begin` starts a pass over the
+    grid (zeroes q on B, populations on A); `step(k0, nk)` enqueues one chunk;
+    `end` joins B into A.  Nothing allocates or synchronises the host after
+    construction.  Without ctx2 every step runs on A."""
+
+    def __init__(self, dp, ctx, precision, chunk, ctx2=None, buffers=None, continuum=None, I=None):
+        self.dp, self.ctx, self.ctx2, self.precision = dp, ctx, ctx2, precision
+        self.continuum, self.I = continuum, I
+        dev = ctx.device
+        dt = _dtype(precision)
+        nbuf = 2 if ctx2 is not None else 1
+        if buffers is None:
+            buffers = [(torch.empty((dp.C, chunk), dtype=dt, device=dev),
+                        torch.empty((dp.C, chunk), dtype=dt, device=dev)) for _ in range(nbuf)]
+        self.buffers = buffers[:nbuf]
+        self.qlam = torch.empty((dp.P, chunk), dtype=dt, device=dev)
+        self.q = torch.zeros(dp.P, dtype=torch.float64, device=dev)
+        self.i = 0
+        self.used = [False] * nbuf
+        if ctx2 is not None:
+            self.free = [torch.cuda.Event() for _ in range(nbuf)]
+            self.ready = torch.cuda.Event()
+            self.ev = torch.cuda.Event()
+
+    @property
+    def march_ctx(self):
+        return self.ctx2 if self.ctx2 is not None else self.ctx
+
+    def begin(self, q=None):
+        """Starts a pass: q (default: the pipeline's own) is zeroed on the
+        march stream after its earlier uses, populations run on stream A."""
+        if q is not None:
+            self.q = q
+        dp, ctx = self.dp, self.ctx
+        if self.ctx2 is not None:   # earlier readers of q on stream A come first
+            self.ev.record(ctx.stream)
+            self.ctx2.stream.wait_event(self.ev)
+        with torch.cuda.stream(self.march_ctx.stream):
+            self.q.zero_()
+        R.populations(ctx, dp.species, dp.cells)
+        if self.ctx2 is not None:
+            self.ev.record(ctx.stream)
+            self.ctx2.stream.wait_event(self.ev)
+
+    def step(self, k0, nk, march_events=None):
+        """Enqueues grid points [k0, k0 + nk); `march_events` (a pair of
+        torch.cuda.Event) are recorded around the march on its stream."""
+        dp, ctx, prec = self.dp, self.ctx, self.precision
+        b = self.i % len(self.buffers)
+        kap, em = self.buffers[b]
+        if self.ctx2 is not None and self.used[b]:
+            ctx.stream.wait_event(self.free[b])
+        R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, prec, kap, em)
+        if self.continuum is not None:
+            R.continuum_coeffs(ctx, self.continuum, dp.species.S, dp.cells, dp.grid, k0, nk, prec, kap, em)
+        mc = self.march_ctx
+        if self.ctx2 is not None:
+            self.ready.record(ctx.stream)
+            self.ctx2.stream.wait_event(self.ready)
+        if march_events is not None:
+            march_events[0].record(mc.stream)
+        R.trace_rays(mc, dp.rays, dp.C, kap, em, dp.grid, k0, nk, prec, self.qlam, self.I)
+        if march_events is not None:
+            march_events[1].record(mc.stream)
+        R.wall_flux(mc, self.qlam, prec, dp.grid, k0, nk, dp.P, self.q)
+        if self.ctx2 is not None:
+            self.free[b].record(self.ctx2.stream)
+            self.used[b] = True
+        self.i += 1
+        return kap, em
+
+    def end(self):
+        if self.ctx2 is not None:
+            self.ev.record(self.ctx2.stream)
+            self.ctx.stream.wait_event(self.ev)
+        return self.q
+
+
 def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensity=False, ctx2=None,
           buffers=None, k_start=0, k_stop=None, continuum=None):
     """Runs the whole path on device-resident inputs over the grid points
@@ -65,85 +147,66 @@ def solve(dp, ctx, precision=R.FP64, chunk=None, keep_coeffs=False, keep_intensi
     k_stop = dp.grid.n if k_stop is None else k_stop
     n_range = k_stop - k_start
     chunk = n_range if not chunk else min(chunk, n_range)
-    dev = ctx.device
-    dt = _dtype(precision)
-    C, P = dp.C, dp.P
-    q = torch.zeros(P, dtype=torch.float64, device=dev)
-    R.populations(ctx, dp.species, dp.cells)
-    nbuf = 2 if ctx2 is not None else 1
-    if buffers is None:
-        buffers = [(torch.empty((C, chunk), dtype=dt, device=dev), torch.empty((C, chunk), dtype=dt, device=dev))
-                   for _ in range(nbuf)]
-    qlam = torch.empty((P, chunk), dtype=dt, device=dev)
-    out = {}
     I = None
     if keep_intensity:
-        I = torch.empty((dp.rays.n_dirs, chunk), dtype=dt, device=dev)
+        I = torch.empty((dp.rays.n_dirs, chunk), dtype=_dtype(precision), device=ctx.device)
+    pipe = ChunkPipeline(dp, ctx, precision, chunk, ctx2=ctx2, buffers=buffers, continuum=continuum, I=I)
     starts = list(range(k_start, k_stop, chunk))
-    if ctx2 is None:
-        for k0 in starts:
-            nk = min(chunk, k_stop - k0)
-            kap, em = buffers[0]
-            R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
-            if continuum is not None:
-                R.continuum_coeffs(ctx, continuum, dp.species.S, dp.cells, dp.grid, k0, nk, precision, kap, em)
-            R.trace_rays(ctx, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)
-            R.wall_flux(ctx, qlam, precision, dp.grid, k0, nk, P, q)
-    else:
-        # two streams: coefficients of chunk i on ctx (stream A), march + flux on ctx2 (stream B)
-        sa, sb = ctx.stream, ctx2.stream
-        ready = [torch.cuda.Event() for _ in starts]
-        free = [torch.cuda.Event() for _ in range(nbuf)]
-        used = [False] * nbuf
-        ev_pop = torch.cuda.Event()
-        ev_pop.record(sa)
-        sb.wait_event(ev_pop)
-        for i, k0 in enumerate(starts):
-            nk = min(chunk, k_stop - k0)
-            kap, em = buffers[i % nbuf]
-            if used[i % nbuf]:
-                sa.wait_event(free[i % nbuf])
-            R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, dp.grid, k0, nk, precision, kap, em)
-            if continuum is not None:
-                R.continuum_coeffs(ctx, continuum, dp.species.S, dp.cells, dp.grid, k0, nk, precision, kap, em)
-            ready[i].record(sa)
-            sb.wait_event(ready[i])
-            R.trace_rays(ctx2, dp.rays, C, kap, em, dp.grid, k0, nk, precision, qlam, I)
-            R.wall_flux(ctx2, qlam, precision, dp.grid, k0, nk, P, q)
-            free[i % nbuf].record(sb)
-            used[i % nbuf] = True
-        done = torch.cuda.Event()
-        done.record(sb)
-        sa.wait_event(done)
-    out["q"] = q
+    pipe.begin()
+    for k0 in starts:
+        kap, em = pipe.step(k0, min(chunk, k_stop - k0))
+    pipe.end()
+    out = {"q": pipe.q}
     if len(starts) == 1:
         if keep_coeffs:
-            out["kappa"], out["emis"] = buffers[0]
-        out["q_lambda"] = qlam
+            out["kappa"], out["emis"] = kap, em
+        out["q_lambda"] = pipe.qlam
         if keep_intensity:
             out["I"] = I
     return out
 
 
-def solve_sharded(dp, ctx, rank, world, precision=R.FP32, chunk=None, group=None):
-    """Spectral sharding across ranks: each rank solves its contiguous part of
-    the grid (populations are replicated, no data exchange), then one sum of
-    the P partial fluxes (FP64) over the process group finishes the job."""
-    import torch.distributed as dist
-    k0, nk = shard_range(dp.grid.n, rank, world)
-    if nk > 0:
-        q = solve(dp, ctx, precision, chunk=chunk, k_start=k0, k_stop=k0 + nk)["q"]
-    else:
-        q = torch.zeros(dp.P, dtype=torch.float64, device=ctx.device)
-    if world > 1:
-        dist.all_reduce(q, op=dist.ReduceOp.SUM, group=group)
+def shard_ranges(n, rank, world, chunk=None):
+    """Grid ranges [(k0, nk), ...] of `rank`'s spectral shard.  With `chunk`,
+    the grid is cut into chunk-point chunks dealt round-robin (chunk i to
+    rank i mod world), which spreads the heavier short-wavelength chunks over
+    the ranks; without, one contiguous tile-aligned range (shard_range)."""
+    if chunk:
+        return [(k0, min(chunk, n - k0)) for i, k0 in enumerate(range(0, n, chunk)) if i % world == rank]
+    k0, nk = shard_range(n, rank, world)
+    return [(k0, nk)] if nk > 0 else []
+
+
+def solve_sharded(dp, ctx, rank, world, precision=R.FP32, chunk=None, group=None, ctx2=None, dealt=False,
+                  reduce=True):
+    """Spectral sharding across ranks (Sec. 2.3 parallelises the spectral
+    evaluation): each rank solves its shard of the grid (shard_ranges; dealt
+    chunks with `dealt`, else one contiguous range cut into `chunk`-point
+    chunks), populations replicated, no data exchange; then one FP64 sum of
+    the P partial fluxes over the process group (skipped with reduce=False or
+    world == 1) finishes the job.  Returns q [P] (device)."""
+    ranges = shard_ranges(dp.grid.n, rank, world, chunk if dealt else None)
+    span = max((nk for _k0, nk in ranges), default=1)
+    step = min(chunk, span) if chunk else span
+    pipe = ChunkPipeline(dp, ctx, precision, step, ctx2=ctx2)
+    pipe.begin()
+    for k0, nk in ranges:
+        for c0 in range(k0, k0 + nk, step):
+            pipe.step(c0, min(step, k0 + nk - c0))
+    q = pipe.end()
+    if reduce and world > 1:
+        import torch.distributed as dist
+        with torch.cuda.stream(ctx.stream):
+            dist.all_reduce(q, op=dist.ReduceOp.SUM, group=group)
     return q
 
 
-def solve_host(problem, precision=R.FP64, chunk=None, ctx=None, device=None):
+def solve_host(problem, precision=R.FP64, chunk=None, ctx=None, device=None, ctx2=None, k_start=0, k_stop=None):
     """End-to-end: host arrays in, wall flux out.  Inputs are staged through
-    pinned host memory and copied on the context's stream; the result is
-    read back to the host.  Returns (q numpy array, bytes in, bytes out)."""
+    pinned host memory and copied on the context's stream; the result (the
+    flux of grid points [k_start, k_stop), default all) is read back to the
+    host.  With ctx2 the chunks are pipelined on two streams as in `solve`.
+    Returns (q numpy array, bytes in, bytes out)."""
     if ctx is None:
         ctx = R.Context(device)
     dev = ctx.device
@@ -180,7 +243,7 @@ def solve_host(problem, precision=R.FP64, chunk=None, ctx=None, device=None):
         geo = problem.geometry
         dp.rays = R.slab_rays(ctx, geo, dev) if isinstance(geo, synth.SlabGeometry) else R.axisym_rays(ctx, geo, dev)
         dp.C, dp.P = dp.cells.C, dp.rays.n_points
-        res = solve(dp, ctx, precision, chunk)
+        res = solve(dp, ctx, precision, chunk, ctx2=ctx2, k_start=k_start, k_stop=k_stop)
         q_host = torch.empty(res["q"].shape, dtype=torch.float64).pin_memory()
         q_host.copy_(res["q"], non_blocking=True)
     ctx.sync()

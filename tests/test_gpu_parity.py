@@ -337,18 +337,25 @@ def test_slab_many_directions_fp64(ctx):
     _close(out["q"].cpu().numpy(), [ref["q"]], [ref["q"]], TOL64, "q")
 
 
-def test_spectral_shards_sum_to_whole(ctx):
-    """The spectral sharding of the multi-GPU path, run as k partitions one
-    after another on one GPU and summed on the host, equals the unsharded
-    flux to FP64 rounding."""
-    from paper_2604_11856_gb300.solver import shard_range
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("dealt", [False, True])
+def test_spectral_shards_sum_to_whole(ctx, world, dealt):
+    """The multi-GPU path's spectral sharding (solver.solve_sharded) run for
+    every rank one after another on one GPU, its all-reduce skipped and the
+    partial fluxes summed on the host, equals the unsharded flux: contiguous
+    shards whose edges fall inside the unsharded solve's chunks, and chunks
+    dealt round-robin, each on the two-stream pipeline."""
+    import torch
     p = small_stagnation(n_cells=10, n_grid=30001)
     dp = solver.DeviceProblem(p, ctx)
-    whole = solver.solve(dp, ctx, R.FP64)["q"].cpu().numpy()
-    for world in (2, 3):
-        parts = np.zeros_like(whole)
-        for rank in range(world):
-            k0, nk = shard_range(p.grid.n, rank, world)
-            parts += solver.solve(dp, ctx, R.FP64, k_start=k0, k_stop=k0 + nk)["q"].cpu().numpy()
-        ctx.sync()
-        _close(parts, whole, whole, 1e-13, f"q over {world} shards")
+    chunk = 7000
+    whole = solver.solve(dp, ctx, R.FP64, chunk=chunk)["q"].cpu().numpy()
+    ctx2 = R.Context(0, stream=torch.cuda.Stream())
+    parts = np.zeros_like(whole)
+    for rank in range(world):
+        q = solver.solve_sharded(dp, ctx, rank, world, R.FP64, chunk=chunk, ctx2=ctx2, dealt=dealt, reduce=False)
+        parts += q.cpu().numpy()
+    ctx.sync(); ctx2.sync()
+    if not dealt:   # a shard edge inside a chunk of the unsharded solve
+        assert any(solver.shard_range(p.grid.n, r, world)[0] % chunk for r in range(1, world))
+    _close(parts, whole, whole, 1e-13, f"q over {world} shards")
