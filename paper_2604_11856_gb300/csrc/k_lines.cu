@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(128) k_line_sum_f64(LineSumArgs a) {
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
         const int64_t k = kp + i;
-        if (k < kend) { K[k] = acck[i]; J[k] = accj[i]; }
+        if (k < kend) { __stcs(K + k, acck[i]); __stcs(J + k, accj[i]); }   // streaming, as the FP32 path
     }
 }
 
@@ -970,7 +970,10 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     for (int i = 0; i < PPT; ++i) {
         const int k = kt0 + lane + 32 * i;
         const float4 v = acc[i * 32 + lane];
-        if (k <= kt1) { K[k] = v.z; J[k] = v.x; }
+        // streaming stores: the rows are read back by the march of a later
+        // chunk, long after they would have left L2, so they are marked
+        // evict-first and leave L2 to the gathers running beside them
+        if (k <= kt1) { __stcs(K + k, v.z); __stcs(J + k, v.x); }
     }
 }
 

@@ -995,10 +995,13 @@ cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t 
 // waves of resident blocks) that the tiles in flight, and so the kappa / j
 // rows they gather, stay few enough for L2; each group keeps at least 32
 // bundles, and points x groups stays below 2^31.
+#ifndef RAPRAL_MARCH_TILE_BLOCKS
+#define RAPRAL_MARCH_TILE_BLOCKS 1536
+#endif
 static int march_groups(const rapral_rays* r) {
     if (r->max_bundles_per_point < 8 || r->n_points <= 0) return 1;
     int G = 1;
-    while (G * r->n_points < 1536 && 2 * G * 32 <= r->max_bundles_per_point && G < 1024 &&
+    while (G * r->n_points < RAPRAL_MARCH_TILE_BLOCKS && 2 * G * 32 <= r->max_bundles_per_point && G < 1024 &&
            2 * G * r->n_points < (int64_t)1 << 31)
         G *= 2;
     return G;
