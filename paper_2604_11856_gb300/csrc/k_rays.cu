@@ -59,33 +59,32 @@ __device__ __forceinline__ void seg_step(double& I, double kf, double s, double 
     seg_coeffs1(kf, s, &e, &ca, &cb);
     I = I * e + ca * jf + cb * jn;
 }
+// FP32, thin (|dtau| < 0.5): with p = (1 - f)/dtau from its series
+// p = sum_n (-dtau)^n / (n + 2)!, n = 0..6 (truncation below 4e-8 relative)
+// and f = 1 - dtau p, the step I e + ca j_far + cb j_near is
+// I + s f (j_far - kappa I) + s p (j_near - j_far): one series and no
+// exponential (e = 1 - dtau f >= 0.6 keeps the subtraction within a factor
+// 1/e of FP32 rounding).  Thick: e from ex2, f from one reciprocal.
+__device__ __forceinline__ float thin_series(float t) {
+    float p = fmaf(t, 1.0f / 40320.0f, -1.0f / 5040.0f);
+    p = fmaf(t, p, 1.0f / 720.0f);
+    p = fmaf(t, p, -1.0f / 120.0f);
+    p = fmaf(t, p, 1.0f / 24.0f);
+    p = fmaf(t, p, -1.0f / 6.0f);
+    return fmaf(t, p, 0.5f);
+}
 __device__ __forceinline__ void seg_step(float& I, float kf, float s, float jf, float jn) {
     const float dtau = kf * s;
-    const float e = ex2f_approx(-1.44269504f * dtau);
-    float pa, pb, m;
     if (fabsf(dtau) < (float)RAPRAL_THIN_F32) {
-        const float t = dtau;
-        pa = fmaf(t, 1.0f / 5760.0f, -1.0f / 840.0f);
-        pa = fmaf(t, pa, 1.0f / 144.0f);
-        pa = fmaf(t, pa, -1.0f / 30.0f);
-        pa = fmaf(t, pa, 0.125f);
-        pa = fmaf(t, pa, -1.0f / 3.0f);
-        pa = fmaf(t, pa, 0.5f);
-        pb = fmaf(t, 1.0f / 40320.0f, -1.0f / 5040.0f);
-        pb = fmaf(t, pb, 1.0f / 720.0f);
-        pb = fmaf(t, pb, -1.0f / 120.0f);
-        pb = fmaf(t, pb, 1.0f / 24.0f);
-        pb = fmaf(t, pb, -1.0f / 6.0f);
-        pb = fmaf(t, pb, 0.5f);
-        m = s;
-    } else {
-        const float r = recip(dtau);
-        const float f = (1.0f - e) * r;
-        pa = f - e;
-        pb = 1.0f - f;
-        m = s * r;
+        const float p = thin_series(dtau);
+        const float f = fmaf(-dtau, p, 1.0f);
+        I = fmaf(s, fmaf(f, fmaf(-kf, I, jf), p * (jn - jf)), I);
+        return;
     }
-    I = fmaf(m, fmaf(pa, jf, pb * jn), I * e);
+    const float e = ex2f_approx(-1.44269504f * dtau);
+    const float r = recip(dtau);
+    const float f = (1.0f - e) * r;
+    I = fmaf(s * r, fmaf(f - e, jf, (1.0f - f) * jn), I * e);
 }
 
 // Two steps at once in FP32 (two wavelength columns, or two directions of a
@@ -94,24 +93,21 @@ __device__ __forceinline__ void seg_step(float& I, float kf, float s, float jf, 
 // result); otherwise each takes the scalar step.
 __device__ __forceinline__ void seg_step2(float& I0, float& I1, float k0, float k1, float s0, float s1, float jf0,
                                           float jf1, float jn0, float jn1) {
-    const float2 dt = __fmul2_rn(make_float2(k0, k1), make_float2(s0, s1));
+    const float2 k = make_float2(k0, k1), s = make_float2(s0, s1);
+    const float2 dt = __fmul2_rn(k, s);
     if (fabsf(dt.x) < (float)RAPRAL_THIN_F32 && fabsf(dt.y) < (float)RAPRAL_THIN_F32) {
-        const float e0 = ex2f_approx(-1.44269504f * dt.x), e1 = ex2f_approx(-1.44269504f * dt.y);
         const auto c2 = [](float c) { return make_float2(c, c); };
-        float2 pa = __ffma2_rn(dt, c2(1.0f / 5760.0f), c2(-1.0f / 840.0f));
-        pa = __ffma2_rn(dt, pa, c2(1.0f / 144.0f));
-        pa = __ffma2_rn(dt, pa, c2(-1.0f / 30.0f));
-        pa = __ffma2_rn(dt, pa, c2(0.125f));
-        pa = __ffma2_rn(dt, pa, c2(-1.0f / 3.0f));
-        pa = __ffma2_rn(dt, pa, c2(0.5f));
-        float2 pb = __ffma2_rn(dt, c2(1.0f / 40320.0f), c2(-1.0f / 5040.0f));
-        pb = __ffma2_rn(dt, pb, c2(1.0f / 720.0f));
-        pb = __ffma2_rn(dt, pb, c2(-1.0f / 120.0f));
-        pb = __ffma2_rn(dt, pb, c2(1.0f / 24.0f));
-        pb = __ffma2_rn(dt, pb, c2(-1.0f / 6.0f));
-        pb = __ffma2_rn(dt, pb, c2(0.5f));
-        const float2 u = __ffma2_rn(pa, make_float2(jf0, jf1), __fmul2_rn(pb, make_float2(jn0, jn1)));
-        const float2 r = __ffma2_rn(make_float2(s0, s1), u, __fmul2_rn(make_float2(I0, I1), make_float2(e0, e1)));
+        float2 p = __ffma2_rn(dt, c2(1.0f / 40320.0f), c2(-1.0f / 5040.0f));
+        p = __ffma2_rn(dt, p, c2(1.0f / 720.0f));
+        p = __ffma2_rn(dt, p, c2(-1.0f / 120.0f));
+        p = __ffma2_rn(dt, p, c2(1.0f / 24.0f));
+        p = __ffma2_rn(dt, p, c2(-1.0f / 6.0f));
+        p = __ffma2_rn(dt, p, c2(0.5f));
+        const float2 f = __ffma2_rn(make_float2(-dt.x, -dt.y), p, c2(1.0f));
+        const float2 I = make_float2(I0, I1);
+        const float2 A = __ffma2_rn(make_float2(-k0, -k1), I, make_float2(jf0, jf1));
+        const float2 dJ = make_float2(jn0 - jf0, jn1 - jf1);
+        const float2 r = __ffma2_rn(s, __ffma2_rn(f, A, __fmul2_rn(p, dJ)), I);
         I0 = r.x;
         I1 = r.y;
     } else {
