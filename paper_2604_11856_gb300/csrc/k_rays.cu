@@ -490,7 +490,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && MAXD == 1 && V > 1)  ?
 // Conditions (checked by the launcher): kappa, emis and the wall row 8-byte
 // aligned, ld and nk even, nk >= 64.
 
-constexpr int M1_PF = 2;        // steps between a load and its use
+#ifndef RAPRAL_M1_PF
+#define RAPRAL_M1_PF 2
+#endif
+#ifndef RAPRAL_M1_UNROLL
+#define RAPRAL_M1_UNROLL 4
+#endif
+constexpr int M1_PF = RAPRAL_M1_PF;            // steps between a load and its use
+constexpr int kM1Unroll = RAPRAL_M1_UNROLL;    // segment steps unrolled
 constexpr int M1_SLICES = 8;    // warps (bundle slices) per block
 
 struct M1Stage {
@@ -620,38 +627,59 @@ __global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ 
     }
 }
 
-// The lane's two columns of one row: one 8-byte load when the pair is
-// aligned (VEC), else two 4-byte loads (the second column is d1 = 0 or 1
-// after the first; 0 where a lane's second column lies past the range).
-template <bool VEC>
-__device__ __forceinline__ float2 m1_load(const float* __restrict__ p, int d1) {
-    if constexpr (VEC) return *reinterpret_cast<const float2*>(p);
-    return make_float2(p[0], p[d1]);
+// A lane's 2 NP adjacent columns of one row, as NP packed pairs.
+template <int NP> struct M1V { float2 v[NP]; };
+
+// The lane's columns of one row: one 8-byte (NP = 1) or 16-byte (NP = 2)
+// load when the columns are aligned (VEC), else one 4-byte load a column at
+// the offsets dq[] from the first (columns past the range repeat the last).
+template <int NP, bool VEC>
+__device__ __forceinline__ M1V<NP> m1_load(const float* __restrict__ p, const int (&dq)[2 * NP]) {
+    M1V<NP> r;
+    if constexpr (VEC && NP == 1) {
+        r.v[0] = *reinterpret_cast<const float2*>(p);
+    } else if constexpr (VEC) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        r.v[0] = make_float2(x.x, x.y);
+        r.v[1] = make_float2(x.z, x.w);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) r.v[q] = make_float2(p[dq[2 * q]], p[dq[2 * q + 1]]);
+    }
+    return r;
 }
 
-// The march of bundle b over the lane's two columns (doubled node values).
-template <bool VEC>
-__device__ __forceinline__ float2 m1_bundle(const MarchArgs& a, int64_t b, float sc, M1Stage* st, int lane,
-                                            const float* __restrict__ kb, const float* __restrict__ jb, int d1,
-                                            int ld, float2 I) {
+template <int NP>
+__device__ __forceinline__ M1V<NP> m1_sum(const M1V<NP>& x, const M1V<NP>& y) {
+    M1V<NP> r;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.v[q] = __fadd2_rn(x.v[q], y.v[q]);
+    return r;
+}
+
+// The march of bundle b over the lane's columns (doubled node values).
+template <int NP, bool VEC>
+__device__ __forceinline__ M1V<NP> m1_bundle(const MarchArgs& a, int64_t b, float sc, M1Stage* st, int lane,
+                                             const float* __restrict__ kb, const float* __restrict__ jb,
+                                             const int (&dq)[2 * NP], int ld, M1V<NP> I) {
     const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
     if (s1 <= s0) return I;
-    float2 kc, jc;
+    M1V<NP> kc, jc;
     {
         const int c0 = a.seg_cell[s0];
-        kc = m1_load<VEC>(kb + (int64_t)c0 * ld, d1);
-        jc = m1_load<VEC>(jb + (int64_t)c0 * ld, d1);
+        kc = m1_load<NP, VEC>(kb + (int64_t)c0 * ld, dq);
+        jc = m1_load<NP, VEC>(jb + (int64_t)c0 * ld, dq);
     }
-    float2 Kf = __fadd2_rn(kc, kc), Jf = __fadd2_rn(jc, jc);
+    M1V<NP> Kf = m1_sum(kc, kc), Jf = m1_sum(jc, jc);
     const float hs = 0.5f * sc;
     // ring of loads in flight: values of the next cells of the following PF segments
-    float2 rk[M1_PF], rj[M1_PF];
+    M1V<NP> rk[M1_PF], rj[M1_PF];
 #pragma unroll
     for (int q = 0; q < M1_PF; ++q) {
         const int64_t i = s0 + q;   // segment i's next cell is cell i + 1
         const int c = (i < s1 - 1) ? a.seg_cell[i + 1] : 0;
-        rk[q] = m1_load<VEC>(kb + (int64_t)c * ld, d1);
-        rj[q] = m1_load<VEC>(jb + (int64_t)c * ld, d1);
+        rk[q] = m1_load<NP, VEC>(kb + (int64_t)c * ld, dq);
+        rj[q] = m1_load<NP, VEC>(jb + (int64_t)c * ld, dq);
     }
     for (int64_t g = s0; g < s1 - 1; g += 32) {
         const int64_t mine = g + lane;
@@ -661,86 +689,110 @@ __device__ __forceinline__ float2 m1_bundle(const MarchArgs& a, int64_t b, float
         st[lane].row = ahead < s1 - 1 ? a.seg_cell[ahead + 1] : 0;
         __syncwarp();
         const int n = s1 - 1 - g < 32 ? (int)(s1 - 1 - g) : 32;
-#pragma unroll 4
+#pragma unroll kM1Unroll
         for (int j = 0; j < n; ++j) {
             const M1Stage e = st[j];
-            const float2 kx = rk[0], jx = rj[0];
+            const M1V<NP> kx = rk[0], jx = rj[0];
 #pragma unroll
             for (int q = 0; q + 1 < M1_PF; ++q) { rk[q] = rk[q + 1]; rj[q] = rj[q + 1]; }
-            rk[M1_PF - 1] = m1_load<VEC>(kb + (int64_t)e.row * ld, d1);
-            rj[M1_PF - 1] = m1_load<VEC>(jb + (int64_t)e.row * ld, d1);
-            const float2 Kn = __fadd2_rn(kc, kx), Jn = __fadd2_rn(jc, jx);
-            m1_step(I, Kf, Jf, Jn, e.sh);
+            rk[M1_PF - 1] = m1_load<NP, VEC>(kb + (int64_t)e.row * ld, dq);
+            rj[M1_PF - 1] = m1_load<NP, VEC>(jb + (int64_t)e.row * ld, dq);
+            const M1V<NP> Kn = m1_sum(kc, kx), Jn = m1_sum(jc, jx);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) m1_step(I.v[q], Kf.v[q], Jf.v[q], Jn.v[q], e.sh);
             Kf = Kn; Jf = Jn; kc = kx; jc = jx;
         }
     }
-    // last segment: its near node is its own cell's value
-    m1_step(I, Kf, Jf, __fadd2_rn(jc, jc), seg_len<float>(a, s1 - 1) * hs);
+    {   // last segment: its near node is its own cell's value
+        const float hl = seg_len<float>(a, s1 - 1) * hs;
+        const M1V<NP> Jn = m1_sum(jc, jc);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) m1_step(I.v[q], Kf.v[q], Jf.v[q], Jn.v[q], hl);
+    }
     return I;
 }
 
-// Block (point, bundle group) x tile of 64 columns; warp w is slice w of the
-// group's plan.  The last tile is shifted back to end at nk when nk >= 64
-// (columns below the tile are computed again and not written); a range
-// shorter than 64 columns clamps the reads of lanes past it and writes
-// nothing there.
-template <bool VEC>
+// Stores of a lane's columns: one vector store when aligned and owned, else
+// one 4-byte store a column it owns.
+template <int NP, bool VEC>
+__device__ __forceinline__ void m1_store(float* __restrict__ p, const M1V<NP>& x, const bool (&own)[2 * NP]) {
+    if constexpr (VEC && NP == 1) {
+        if (own[0]) *reinterpret_cast<float2*>(p) = x.v[0];
+    } else if constexpr (VEC) {
+        if (own[0]) *reinterpret_cast<float4*>(p) = make_float4(x.v[0].x, x.v[0].y, x.v[1].x, x.v[1].y);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            if (own[2 * q]) p[2 * q] = x.v[q].x;
+            if (own[2 * q + 1]) p[2 * q + 1] = x.v[q].y;
+        }
+    }
+}
+
+// Block (point, bundle group) x tile of 64 NP columns; warp w is slice w of
+// the group's plan; lane l owns the 2 NP adjacent columns from 2 NP l.  The
+// last tile is shifted back to end at nk when nk >= the tile (columns below
+// the tile are computed again and not written); a range shorter than a tile
+// clamps the reads of lanes past it and writes nothing there.
+template <int NP, bool VEC>
 __global__ void __launch_bounds__(256, RAPRAL_MARCH_MINB) k_march1(MarchArgs a, int lgG, const int32_t* __restrict__ plan,
                                                                    const int32_t* __restrict__ soff,
                                                                    float* __restrict__ part) {
     if (*a.status) return;
-    constexpr int TW = 64, SLC = M1_SLICES;
+    constexpr int TW = 64 * NP, SLC = M1_SLICES, NC = 2 * NP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nk = (int)a.nk;
     const int tile0 = (int)blockIdx.y * TW;
     const int base = (tile0 + TW > nk && nk >= TW) ? nk - TW : tile0;
-    const int col = base + 2 * lane;                  // the lane's columns: col, col + 1
+    const int col = base + NC * lane;                 // the lane's columns: col .. col + NC - 1
     const int c0 = col < nk ? col : nk - 1;           // clamped reads (VEC: never clamped)
-    const int d1 = (col + 1 < nk ? col + 1 : nk - 1) - c0;
-    const bool own0 = col >= tile0 && col < nk, own1 = col + 1 >= tile0 && col + 1 < nk;
+    int dq[NC];
+    bool own[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        dq[q] = (col + q < nk ? col + q : nk - 1) - c0;
+        own[q] = col + q >= tile0 && col + q < nk;
+    }
     const float* kb = reinterpret_cast<const float*>(a.kappa) + c0;
     const float* jb = reinterpret_cast<const float*>(a.emis) + c0;
     __shared__ M1Stage stage_all[SLC][32];
     M1Stage* st = stage_all[warp];
-    float2 acc = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
+    M1V<NP> acc, comp;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc.v[q] = comp.v[q] = make_float2(0.f, 0.f);
     const int32_t* so = soff + (int64_t)blockIdx.x * (SLC + 1);
     const int k1 = so[warp + 1];
     for (int k = so[warp]; k < k1; ++k) {
         const int64_t b = plan[k];
         const int64_t d0 = a.dir_off[b];
         if (a.dir_off[b + 1] == d0) continue;
-        float2 I0 = make_float2(0.f, 0.f);
-        if (a.wall_row && a.bundle_wall[b]) I0 = m1_load<VEC>(reinterpret_cast<const float*>(a.wall_row) + c0, d1);
-        const float2 I = m1_bundle<VEC>(a, b, a.dir_scale_f[d0], st, lane, kb, jb, d1, (int)a.ld, I0);
-        if (a.I_out) {
-            float* io = reinterpret_cast<float*>(a.I_out) + d0 * a.nk + col;
-            if (VEC && own0) {
-                *reinterpret_cast<float2*>(io) = I;
-            } else {
-                if (own0) io[0] = I.x;
-                if (own1) io[1] = I.y;
-            }
-        }
+        M1V<NP> I0;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) I0.v[q] = make_float2(0.f, 0.f);
+        if (a.wall_row && a.bundle_wall[b]) I0 = m1_load<NP, VEC>(reinterpret_cast<const float*>(a.wall_row) + c0, dq);
+        const M1V<NP> I = m1_bundle<NP, VEC>(a, b, a.dir_scale_f[d0], st, lane, kb, jb, dq, (int)a.ld, I0);
+        if (a.I_out) m1_store<NP, VEC>(reinterpret_cast<float*>(a.I_out) + d0 * a.nk + col, I, own);
         const float w = a.dir_weight_f[d0];
-        // compensated sum over the slice's bundles
-        const float2 y = make_float2(w * I.x - comp.x, w * I.y - comp.y);
-        const float2 tt = make_float2(acc.x + y.x, acc.y + y.y);
-        comp = make_float2((tt.x - acc.x) - y.x, (tt.y - acc.y) - y.y);
-        acc = tt;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {   // compensated sum over the slice's bundles
+            const float2 y = make_float2(w * I.v[q].x - comp.v[q].x, w * I.v[q].y - comp.v[q].y);
+            const float2 tt = make_float2(acc.v[q].x + y.x, acc.v[q].y + y.y);
+            comp.v[q] = make_float2((tt.x - acc.v[q].x) - y.x, (tt.y - acc.v[q].y) - y.y);
+            acc.v[q] = tt;
+        }
     }
-    __shared__ float2 red[SLC][32];
+    __shared__ M1V<NP> red[SLC][32];
     red[warp][lane] = acc;
     __syncthreads();
     if (warp == 0) {
-        float2 s = red[0][lane];
-        for (int q = 1; q < SLC; ++q) s = make_float2(s.x + red[q][lane].x, s.y + red[q][lane].y);
-        float* dst = (lgG == 0 ? reinterpret_cast<float*>(a.q_lambda) : part) + (int64_t)blockIdx.x * a.nk + col;
-        if (VEC && own0) {
-            *reinterpret_cast<float2*>(dst) = s;
-        } else {
-            if (own0) dst[0] = s.x;
-            if (own1) dst[1] = s.y;
+        M1V<NP> sum = red[0][lane];
+        for (int w = 1; w < SLC; ++w) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                sum.v[q] = make_float2(sum.v[q].x + red[w][lane].v[q].x, sum.v[q].y + red[w][lane].v[q].y);
         }
+        float* dst = (lgG == 0 ? reinterpret_cast<float*>(a.q_lambda) : part) + (int64_t)blockIdx.x * a.nk + col;
+        m1_store<NP, VEC>(dst, sum, own);
     }
 }
 
@@ -915,13 +967,22 @@ static bool march1_applies(const MarchArgs& a, int maxd, int maxb, bool nodes) {
     return !nodes && maxd <= 1 && maxb >= 8 && a.ld <= 2147483647LL;
 }
 
-// Paired 8-byte loads and stores: every row of kappa / emis, q_lambda, I_out
-// and the wall row starts 8-byte aligned and the range is whole tiles or
-// ends on an even column past the first tile.
+// Columns a lane owns in k_march1 (2 NP) and the tile width (64 NP).
+#ifndef RAPRAL_M1_NP
+#define RAPRAL_M1_NP 1
+#endif
+constexpr int kM1NP = RAPRAL_M1_NP;
+
+// Vector loads and stores of 2 NP floats: every row of kappa / emis,
+// q_lambda, I_out and the wall row starts aligned to 8 NP bytes, and the
+// range is whole tiles or ends on a multiple of 2 NP columns past the first
+// tile.
 static bool march1_vec(const MarchArgs& a, int64_t nk, const void* part) {
-    const auto al8 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 7u) == 0; };
-    return nk >= 64 && (nk & 1) == 0 && (a.ld & 1) == 0 && al8(a.kappa) && al8(a.emis) && al8(a.q_lambda) &&
-           al8(part) && (a.I_out == nullptr || al8(a.I_out));
+    const unsigned al = 8u * kM1NP - 1u;
+    const auto ok = [al](const void* q) { return (reinterpret_cast<uintptr_t>(q) & al) == 0; };
+    const int64_t nc = 2 * kM1NP;
+    return nk >= 64 * kM1NP && nk % nc == 0 && a.ld % nc == 0 && ok(a.kappa) && ok(a.emis) && ok(a.q_lambda) &&
+           ok(part) && (a.I_out == nullptr || ok(a.I_out));
 }
 
 static cudaError_t march1_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P, int64_t nk, int G, void* part,
@@ -939,11 +1000,11 @@ static cudaError_t march1_launch(rapral_ctx* ctx, const MarchArgs& a, int64_t P,
             a.lam_min, a.h, a.k0, nk, a.T_wall, a.ph, row);
         b.wall_row = row;
     }
-    dim3 g((unsigned)(P << lgG), div_up(nk, 64));
+    dim3 g((unsigned)(P << lgG), div_up(nk, 64 * kM1NP));
     if (march1_vec(a, nk, part))
-        k_march1<true><<<g, 32 * M1_SLICES, 0, ctx->stream>>>(b, lgG, plan, soff, reinterpret_cast<float*>(part));
+        k_march1<kM1NP, true><<<g, 32 * M1_SLICES, 0, ctx->stream>>>(b, lgG, plan, soff, reinterpret_cast<float*>(part));
     else
-        k_march1<false><<<g, 32 * M1_SLICES, 0, ctx->stream>>>(b, lgG, plan, soff, reinterpret_cast<float*>(part));
+        k_march1<kM1NP, false><<<g, 32 * M1_SLICES, 0, ctx->stream>>>(b, lgG, plan, soff, reinterpret_cast<float*>(part));
     e = cudaGetLastError();
     if (e != cudaSuccess || G == 1) return e;
     k_group_sum<float><<<(unsigned)std::min<int64_t>(div_up(P * nk, 256), 152 * 16), 256, 0, ctx->stream>>>(
