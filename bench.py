@@ -8,9 +8,10 @@ chunks, 200 surface points x 512 rays (16 mu x 32 azimuths), FP32-chosen
 arithmetic.  A step is one spectral chunk of that solve, through every step of
 the path: line binning -> line-by-line kappa / j of all 80,000 cells -> ray
 march of all 102,400 rays with the angular sum -> wall flux; populations at
-the first chunk of each solve.  Steps run back to back through the two-stream
-chunk pipeline (the line sum of chunk i + 1 overlaps the march of chunk i),
-cycling through the 16 chunks, so 16 steps are one whole solve.  The ray
+the first chunk of each solve.  Steps run back to back through the chunk
+pipeline on one stream (`--streams 2`: the line sum of chunk i + 1 beside the
+march of chunk i, which takes the same time on this workload), cycling
+through the 16 chunks, so 16 steps are one whole solve.  The ray
 segments depend on the geometry only and are built once, before timing.
 Inputs are resident in HBM when timing starts; each step's kappa / j table
 (42 GB) is far larger than L2.
@@ -73,6 +74,9 @@ def parse():
                     help="continuum workload: grid points (fewer only for profiler captures)")
     ap.add_argument("--fib-points", type=int, default=8, help="fibonacci workload: surface points")
     ap.add_argument("--fib-los", type=int, default=128, help="fibonacci workload: Fibonacci directions per point")
+    ap.add_argument("--streams", type=int, choices=[1, 2], default=1,
+                    help="afterbody: chunk pipeline on one stream, or two (line sum of the next chunk beside the "
+                         "march)")
     ap.add_argument("--ab-small", action="store_true",
                     help="afterbody at 100 x 50 cells, 20 points, 2e5 grid points (profiler captures)")
     ap.add_argument("--ab-cells", type=str, default="",
@@ -733,9 +737,9 @@ def run_headline(args):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     p = afterbody_problem(args)
-    sa, sb = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    sa = torch.cuda.Stream(dev)
     ctx = R.Context(local, stream=sa)
-    ctx2 = R.Context(local, stream=sb)
+    ctx2 = R.Context(local, stream=torch.cuda.Stream(dev)) if args.streams == 2 else None
     dp = solver.DeviceProblem(p, ctx)   # ray segments: built once per geometry
     ctx.sync()
     C, P, n, chunk = dp.C, dp.P, p.grid.n, p.chunk
@@ -835,7 +839,8 @@ def run_headline(args):
              "dram_unique_bytes_per_launch": uniq,
              "dram_traffic_bytes_per_launch": march_traffic(C, nk_mean),
              "dram_frac_of_hbm_peak": uniq / (march_mean * 1e-3) / 1e9 / hbm,
-             "timed_inside": "the two-stream pipeline (overlaps the next chunk's line sum)"}
+             "timed_inside": ("the two-stream pipeline (overlaps the next chunk's line sum)" if ctx2 is not None
+                              else "the one-stream pipeline (the kernel alone on the GPU)")}
     roof = {"bound": "hbm", "achieved": gather, "peak": hbm, "unit": "GB/s", "frac": gather / hbm,
             "traffic": march_traffic(C, nk_mean),
             "kernel": "k_march1 (single-direction rays, FP32)", "kernel_ms": march_mean,
@@ -843,8 +848,9 @@ def run_headline(args):
             "algorithmic_unit": "8 B (FP32 kappa + j of the next cell) gathered per segment-wavelength, x the "
                                 "launch's segments x columns",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
-            "served_from": "L2: DRAM sees one pass over the chunk's kappa / j (traffic); the gathers hit L2, "
-                           "whose measured gather bandwidth is in march.l2_gather_peak",
+            "served_from": "L2: the gathers hit L2, whose measured gather bandwidth is in march.l2_gather_peak; "
+                           "DRAM (traffic) sees the chunk's kappa / j once and the segment lists once per "
+                           "64-column wavelength tile",
             "frac_of_l2_gather_peak": gather / l2_peak}
     out = {"metric": METRIC, "value": value, "unit": "cell·λ points/s", "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -852,8 +858,9 @@ def run_headline(args):
            "config": {"workload": WORKLOAD if not (args.ab_small or args.ab_cells) else f"reduced afterbody {C} cells",
                       "precision": "fp32-chosen", "cells": C, "lines": len(p.lines), "grid_points": n,
                       "chunk_points": chunk, "surface_points": P, "rays": int(dp.rays.n_dirs), "segments": nseg,
-                      "step": "one 65,536-point spectral chunk of the solve (16 steps = one solve), two-stream "
-                              "pipeline, populations at each solve's first chunk",
+                      "step": f"one 65,536-point spectral chunk of the solve (16 steps = one solve), "
+                              f"{'two-stream' if ctx2 is not None else 'one-stream'} pipeline, populations at each "
+                              f"solve's first chunk",
                       "l2": "inputs larger than L2 (a 42 GB kappa / j table per step)",
                       "parallelism": f"spectral shards x{world} (every {world}-th chunk a rank, one FP64 "
                                      f"all-reduce of the wall flux)" if world > 1 else "one GPU"},
@@ -893,7 +900,7 @@ def run_headline(args):
 
     if not args.no_e2e:
         # end to end through the public API: host arrays -> pinned staging -> device -> q on the host,
-        # one chunk a call, the chunk cut in two halves pipelined on the two streams
+        # one chunk a call, the chunk cut in two halves (pipelined on two streams with --streams 2)
         n_e2e = max(1, min(3, K))
         solver.solve_host(p, R.FP32, chunk // 2, ctx=ctx, ctx2=ctx2, k_start=mine[0][0], k_stop=sum(mine[0]))
         barrier(dev, world)
@@ -908,7 +915,9 @@ def run_headline(args):
                       "d2h_bytes_per_step": bo, "ms_per_step": te / n_e2e * 1e3, "steps": n_e2e,
                       "note": "each step builds the ray segments from the geometry as well"}
     if not args.no_secondary and world == 1:
-        ctx.close(); ctx2.close()
+        ctx.close()
+        if ctx2 is not None:
+            ctx2.close()
         del pipe, dp, solves
         torch.cuda.empty_cache()
         out["stagnation"] = stagnation_block(args, local, world, rank)

@@ -480,9 +480,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && MAXD == 1 && V > 1)  ?
 //    1/e of relative rounding, so it stays in FP32 accuracy.  Thick steps use
 //    the exponential form I' = I e + s f j_f + s p (j_n - j_f) with
 //    f = (1 - e)/dtau, p = (1 - f)/dtau;
-//  * the staged list holds, for step j, the segment's halved length and the
-//    row of the cell PF steps ahead, so each step issues the loads it will use
-//    PF steps later and no load is exposed at the 32-segment staging seams;
+//  * the staged list holds, for step j, the segment's halved length (as the
+//    packed pair the step multiplies by) and the byte offset of the row of the
+//    cell PF steps ahead (row x ld, computed once by the staging lane), so a
+//    step does no address arithmetic beyond adding that offset to its lane's
+//    base; each step issues the loads it will use PF steps later and no load
+//    is exposed at the 32-segment staging seams;
 //  * the bundles of a block are dealt to its eight warps longest first
 //    (k_march_plan), so the warps finish together at the block's reduction.
 // Every slice still Kahan-sums its bundles in a fixed order and the slices
@@ -500,9 +503,9 @@ constexpr int M1_PF = RAPRAL_M1_PF;            // steps between a load and its u
 constexpr int kM1Unroll = RAPRAL_M1_UNROLL;    // segment steps unrolled
 constexpr int M1_SLICES = 8;    // warps (bundle slices) per block
 
-struct M1Stage {
-    float sh;       // half the segment length (x the direction scale)
-    int row;        // cell whose values step j + M1_PF needs (its next cell); 0 past the end
+struct __align__(16) M1Stage {
+    float2 sh;      // half the segment length (x the direction scale), twice: a packed pair
+    int64_t off;    // byte offset of the row of the cell step j + M1_PF needs (its next cell); 0 past the end
 };
 
 // The thin-step series p(t) = (1 - f)/t = sum_n (-t)^n / (n + 2)!, n = 0..6
@@ -540,15 +543,16 @@ __device__ __forceinline__ float m1_step1(float I, float Kf, float Jf, float Jn,
 }
 
 // One step of both columns: packed when both are thin.
-__device__ __forceinline__ void m1_step(float2& I, float2 Kf, float2 Jf, float2 Jn, float sh) {
-    const float2 t = __fmul2_rn(Kf, make_float2(sh, sh));
+__device__ __forceinline__ void m1_step(float2& I, float2 Kf, float2 Jf, float2 Jn, float2 sh2) {
+    const float sh = sh2.x;
+    const float2 t = __fmul2_rn(Kf, sh2);
     if (fmaxf(fabsf(t.x), fabsf(t.y)) < (float)RAPRAL_THIN_F32) {
         const float2 p = m1_series(t);
         const float2 f = __ffma2_rn(make_float2(-t.x, -t.y), p, make_float2(1.0f, 1.0f));
         const float2 A = __ffma2_rn(make_float2(-Kf.x, -Kf.y), I, Jf);
         const float2 dJ = __fadd2_rn(Jn, make_float2(-Jf.x, -Jf.y));
         const float2 B = __ffma2_rn(f, A, __fmul2_rn(p, dJ));
-        I = __ffma2_rn(make_float2(sh, sh), B, I);
+        I = __ffma2_rn(sh2, B, I);
     } else {
         I.x = m1_step1(I.x, Kf.x, Jf.x, Jn.x, sh);
         I.y = m1_step1(I.y, Kf.y, Jf.y, Jn.y, sh);
@@ -657,19 +661,24 @@ __device__ __forceinline__ M1V<NP> m1_sum(const M1V<NP>& x, const M1V<NP>& y) {
     return r;
 }
 
+// The lane's columns of one row of kappa and of emis: kb, jb point at the
+// lane's first column in row 0, off is the row's byte offset.
+template <int NP, bool VEC>
+__device__ __forceinline__ M1V<NP> m1_rowload(const char* kb, const char* jb, int64_t off, const int (&dq)[2 * NP],
+                                              M1V<NP>& j) {
+    j = m1_load<NP, VEC>(reinterpret_cast<const float*>(jb + off), dq);
+    return m1_load<NP, VEC>(reinterpret_cast<const float*>(kb + off), dq);
+}
+
 // The march of bundle b over the lane's columns (doubled node values).
 template <int NP, bool VEC>
 __device__ __forceinline__ M1V<NP> m1_bundle(const MarchArgs& a, int64_t b, float sc, M1Stage* st, int lane,
-                                             const float* __restrict__ kb, const float* __restrict__ jb,
-                                             const int (&dq)[2 * NP], int ld, M1V<NP> I) {
+                                             const char* __restrict__ kb, const char* __restrict__ jb,
+                                             const int (&dq)[2 * NP], int64_t ldb, M1V<NP> I) {
     const int64_t s0 = a.seg_off[b], s1 = a.seg_off[b + 1];
     if (s1 <= s0) return I;
     M1V<NP> kc, jc;
-    {
-        const int c0 = a.seg_cell[s0];
-        kc = m1_load<NP, VEC>(kb + (int64_t)c0 * ld, dq);
-        jc = m1_load<NP, VEC>(jb + (int64_t)c0 * ld, dq);
-    }
+    kc = m1_rowload<NP, VEC>(kb, jb, (int64_t)a.seg_cell[s0] * ldb, dq, jc);
     M1V<NP> Kf = m1_sum(kc, kc), Jf = m1_sum(jc, jc);
     const float hs = 0.5f * sc;
     // ring of loads in flight: values of the next cells of the following PF segments
@@ -678,15 +687,15 @@ __device__ __forceinline__ M1V<NP> m1_bundle(const MarchArgs& a, int64_t b, floa
     for (int q = 0; q < M1_PF; ++q) {
         const int64_t i = s0 + q;   // segment i's next cell is cell i + 1
         const int c = (i < s1 - 1) ? a.seg_cell[i + 1] : 0;
-        rk[q] = m1_load<NP, VEC>(kb + (int64_t)c * ld, dq);
-        rj[q] = m1_load<NP, VEC>(jb + (int64_t)c * ld, dq);
+        rk[q] = m1_rowload<NP, VEC>(kb, jb, (int64_t)c * ldb, dq, rj[q]);
     }
     for (int64_t g = s0; g < s1 - 1; g += 32) {
         const int64_t mine = g + lane;
         __syncwarp();
         const int64_t ahead = mine + M1_PF;   // the segment whose next cell this entry fetches
-        st[lane].sh = mine < s1 - 1 ? seg_len<float>(a, mine) * hs : 0.0f;
-        st[lane].row = ahead < s1 - 1 ? a.seg_cell[ahead + 1] : 0;
+        const float shl = mine < s1 - 1 ? seg_len<float>(a, mine) * hs : 0.0f;
+        st[lane].sh = make_float2(shl, shl);
+        st[lane].off = ahead < s1 - 1 ? (int64_t)a.seg_cell[ahead + 1] * ldb : 0;
         __syncwarp();
         const int n = s1 - 1 - g < 32 ? (int)(s1 - 1 - g) : 32;
 #pragma unroll kM1Unroll
@@ -695,8 +704,7 @@ __device__ __forceinline__ M1V<NP> m1_bundle(const MarchArgs& a, int64_t b, floa
             const M1V<NP> kx = rk[0], jx = rj[0];
 #pragma unroll
             for (int q = 0; q + 1 < M1_PF; ++q) { rk[q] = rk[q + 1]; rj[q] = rj[q + 1]; }
-            rk[M1_PF - 1] = m1_load<NP, VEC>(kb + (int64_t)e.row * ld, dq);
-            rj[M1_PF - 1] = m1_load<NP, VEC>(jb + (int64_t)e.row * ld, dq);
+            rk[M1_PF - 1] = m1_rowload<NP, VEC>(kb, jb, e.off, dq, rj[M1_PF - 1]);
             const M1V<NP> Kn = m1_sum(kc, kx), Jn = m1_sum(jc, jx);
 #pragma unroll
             for (int q = 0; q < NP; ++q) m1_step(I.v[q], Kf.v[q], Jf.v[q], Jn.v[q], e.sh);
@@ -707,7 +715,7 @@ __device__ __forceinline__ M1V<NP> m1_bundle(const MarchArgs& a, int64_t b, floa
         const float hl = seg_len<float>(a, s1 - 1) * hs;
         const M1V<NP> Jn = m1_sum(jc, jc);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) m1_step(I.v[q], Kf.v[q], Jf.v[q], Jn.v[q], hl);
+        for (int q = 0; q < NP; ++q) m1_step(I.v[q], Kf.v[q], Jf.v[q], Jn.v[q], make_float2(hl, hl));
     }
     return I;
 }
@@ -753,8 +761,8 @@ __global__ void __launch_bounds__(256, RAPRAL_MARCH_MINB) k_march1(MarchArgs a, 
         dq[q] = (col + q < nk ? col + q : nk - 1) - c0;
         own[q] = col + q >= tile0 && col + q < nk;
     }
-    const float* kb = reinterpret_cast<const float*>(a.kappa) + c0;
-    const float* jb = reinterpret_cast<const float*>(a.emis) + c0;
+    const char* kb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(a.kappa) + c0);
+    const char* jb = reinterpret_cast<const char*>(reinterpret_cast<const float*>(a.emis) + c0);
     __shared__ M1Stage stage_all[SLC][32];
     M1Stage* st = stage_all[warp];
     M1V<NP> acc, comp;
@@ -770,7 +778,7 @@ __global__ void __launch_bounds__(256, RAPRAL_MARCH_MINB) k_march1(MarchArgs a, 
 #pragma unroll
         for (int q = 0; q < NP; ++q) I0.v[q] = make_float2(0.f, 0.f);
         if (a.wall_row && a.bundle_wall[b]) I0 = m1_load<NP, VEC>(reinterpret_cast<const float*>(a.wall_row) + c0, dq);
-        const M1V<NP> I = m1_bundle<NP, VEC>(a, b, a.dir_scale_f[d0], st, lane, kb, jb, dq, (int)a.ld, I0);
+        const M1V<NP> I = m1_bundle<NP, VEC>(a, b, a.dir_scale_f[d0], st, lane, kb, jb, dq, a.ld * 4, I0);
         if (a.I_out) m1_store<NP, VEC>(reinterpret_cast<float*>(a.I_out) + d0 * a.nk + col, I, own);
         const float w = a.dir_weight_f[d0];
 #pragma unroll
