@@ -96,8 +96,8 @@ def parse():
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
 # with this digest (source_digest).  Other cell / point counts scale in proportion (the bytes are
 # the kappa / j rows written); a different source (comments aside) gives null.
-LINE_SUM_TRAFFIC = {"sha1": "ee162f14b8a843d46ca76ea6702ffe0ac1880911", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 55_467_776 + 1_546_483_712}
+LINE_SUM_TRAFFIC = {"sha1": "7fab173bb0d4922c72abfe911a4abe30f0932817", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 50_309_888 + 1_540_463_872}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
