@@ -106,10 +106,12 @@ LINE_SUM_TRAFFIC = {"sha1": "7fab173bb0d4922c72abfe911a4abe30f0932817", "cells":
 CONT_TRAFFIC = {"sha1": "5acd74ef87910912678c8d6546c788ab0f5e87b0", "cells": 200, "grid_points": 1_000_000, "levels": 100,
                 "bytes": 1_782_956_800 + 1_538_739_456}
 
-# DRAM bytes of one FP32 march launch (k_march, single-direction rays) per
-# afterbody chunk, from a one-pass ncu capture of the kernel source with this
-# digest; None until captured on the current source.
-MARCH_TRAFFIC = {"sha1": None, "cells": 80_000, "grid_points": 65_536, "bytes": None}
+# DRAM bytes (read + write) of one FP32 march launch (k_march1) on a full
+# 65,536-point afterbody chunk (80,000 cells, 26,697,080 ray segments), from a
+# one-pass ncu capture of the kernel source with this digest (source_digest);
+# another source or ray set gives null.
+MARCH_TRAFFIC = {"sha1": "7fb91849ff64b0e603c2b712e6a298e2c220c1fe", "cells": 80_000, "segments": 26_697_080,
+                 "grid_points": 65_536, "bytes": 334_466_940_672 + 472_968_704}
 
 
 def source_digest(name):
@@ -269,12 +271,15 @@ def l2_gather_peak(dev_index):
             "how": "warps loading 256-byte rows at random row indices of an L2-resident table (bench.py)"}
 
 
-def march_traffic(cells, grid_points):
+def march_traffic(cells, segments, grid_points):
+    """The stored DRAM bytes of one march launch, scaled to the launch's columns
+    (the segment lists are read once per wavelength tile); None for another ray
+    set or another kernel source."""
     digest = source_digest("k_rays.cu")
     t = MARCH_TRAFFIC
-    if t["bytes"] is None or digest != t["sha1"]:
+    if t["bytes"] is None or digest != t["sha1"] or cells != t["cells"] or segments != t["segments"]:
         return None
-    return t["bytes"] * (cells / t["cells"]) * (grid_points / t["grid_points"])
+    return t["bytes"] * (grid_points / t["grid_points"])
 
 
 def cpu_baseline(problem, seconds, precision_note="f64"):
@@ -837,12 +842,12 @@ def run_headline(args):
              "gather_bytes_per_launch": seglam_launch * 8, "gather_GBps": gather,
              "l2_gather_peak": l2, "frac_of_l2_gather_peak": gather / l2_peak,
              "dram_unique_bytes_per_launch": uniq,
-             "dram_traffic_bytes_per_launch": march_traffic(C, nk_mean),
+             "dram_traffic_bytes_per_launch": march_traffic(C, nseg, nk_mean),
              "dram_frac_of_hbm_peak": uniq / (march_mean * 1e-3) / 1e9 / hbm,
              "timed_inside": ("the two-stream pipeline (overlaps the next chunk's line sum)" if ctx2 is not None
                               else "the one-stream pipeline (the kernel alone on the GPU)")}
     roof = {"bound": "hbm", "achieved": gather, "peak": hbm, "unit": "GB/s", "frac": gather / hbm,
-            "traffic": march_traffic(C, nk_mean),
+            "traffic": march_traffic(C, nseg, nk_mean),
             "kernel": "k_march1 (single-direction rays, FP32)", "kernel_ms": march_mean,
             "algorithmic_bytes": seglam_launch * 8,
             "algorithmic_unit": "8 B (FP32 kappa + j of the next cell) gathered per segment-wavelength, x the "
@@ -870,45 +875,48 @@ def run_headline(args):
                          "q_mean_W_cm2": float(qsum.mean().item()) if world == 1 else None},
            "roofline": roof, "march": march, "clocks": clk.summary(), "gpu_launches": launches[0]}
 
-    # the line sums of the timed chunks again, alone, with the work counters on: XU work per launch
+    # XU work of the timed steps: each distinct chunk of the timed sequence once more, untimed, with the
+    # library's work counters on (they cost time, so the timed steps run without them)
     ctx.set_counters(True)
-    xu, ev_total, lsum_alone = 0, 0, []
     kap, em = pipe.buffers[0]
-    for s in range(min(K, len(mine))):
-        k0, nk = mine[s]
+    per_chunk = {}
+    for s in range(K):
+        j = s % len(mine)
+        if j in per_chunk:
+            continue
+        k0, nk = mine[j]
         ctx.reset_stats()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(sa)
         R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, k0, nk, R.FP32, kap, em)
-        b.record(sa)
         st = ctx.get_stats()
-        xu += 3 * st["evaluations"] + st["gauss_terms"] + st["correction_terms"]
-        ev_total += st["evaluations"]
-        lsum_alone.append(a.elapsed_time(b))
+        per_chunk[j] = (3 * st["evaluations"] + st["gauss_terms"] + st["correction_terms"], st["evaluations"])
     ctx.set_counters(False)
-    n_counted = min(K, len(mine))
+    xu = sum(per_chunk[s % len(mine)][0] for s in range(K))
+    ev_total = sum(per_chunk[s % len(mine)][1] for s in range(K))
     xu_peak = n_sm * 16 * sm_max / 1e9
     out["line_sum"] = {"kernel": "k_line_sum_f32", "bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)",
-                       "evaluations_per_step": ev_total / n_counted,
-                       "in_pipeline_ms_mean": lsum_mean,
-                       "in_pipeline_xu_frac": (xu / n_counted) / (lsum_mean * 1e-3) / 1e9 / xu_peak,
-                       "alone_ms_mean": float(np.mean(lsum_alone)),
-                       "alone_xu_frac": xu / (np.sum(lsum_alone) * 1e-3) / 1e9 / xu_peak,
+                       "evaluations_per_step": ev_total / K,
+                       "ms_mean": lsum_mean,
+                       "xu_frac": xu / (float(np.sum(k_ms)) * 1e-3) / 1e9 / xu_peak,
                        "peak_gops": xu_peak,
                        "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)",
-                       "note": "alone: binning + line sum of each counted chunk, not overlapped"}
+                       "timed_inside": march["timed_inside"].replace("(the kernel alone on the GPU)", "(alone)"),
+                       "note": "time: the line-sum kernel of each timed step (CUDA events the library records "
+                               "around the launch, on its stream); XU "
+                               "operations: 3 per evaluation + one per Gaussian and correction term, from the "
+                               "library's work counters in an untimed pass over the same chunks"}
 
     if not args.no_e2e:
         # end to end through the public API: host arrays -> pinned staging -> device -> q on the host,
-        # one chunk a call, the chunk cut in two halves (pipelined on two streams with --streams 2)
+        # one chunk a call (with --streams 2 cut in two halves, pipelined on the two streams)
         n_e2e = max(1, min(3, K))
-        solver.solve_host(p, R.FP32, chunk // 2, ctx=ctx, ctx2=ctx2, k_start=mine[0][0], k_stop=sum(mine[0]))
+        sub = chunk if ctx2 is None else chunk // 2
+        solver.solve_host(p, R.FP32, sub, ctx=ctx, ctx2=ctx2, k_start=mine[0][0], k_stop=sum(mine[0]))
         barrier(dev, world)
         t0w = time.perf_counter()
         cl_e2e = 0
         for s in range(n_e2e):
             k0, nk = mine[s % len(mine)]
-            _qh, bi, bo = solver.solve_host(p, R.FP32, chunk // 2, ctx=ctx, ctx2=ctx2, k_start=k0, k_stop=k0 + nk)
+            _qh, bi, bo = solver.solve_host(p, R.FP32, sub, ctx=ctx, ctx2=ctx2, k_start=k0, k_stop=k0 + nk)
             cl_e2e += C * nk
         te = time.perf_counter() - t0w
         out["e2e"] = {"value": world * cl_e2e / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
