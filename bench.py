@@ -357,8 +357,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from paper_2604_11856_gb300 import synth
-    p = synth.afterbody()
+    p = afterbody_problem(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_baseline(p, per_step / 4)
@@ -374,7 +374,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": float(np.mean(secs)) * 1e3, "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": last["sample"]},
+            "config": headline_config(args, p, world),
             "cpu_baseline": {**last, "value": v},
             "e2e": {"value": v, "unit": "cell·λ points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -729,6 +729,22 @@ def afterbody_problem(args):
     return synth.afterbody()
 
 
+def headline_config(args, p, world):
+    """The bench line's `config`: the afterbody workload as the arguments
+    select it (both arms print the same one)."""
+    geo = p.geometry
+    C, P = len(p.cells), len(geo.surf_x)
+    return {"workload": WORKLOAD if not (args.ab_small or args.ab_cells) else f"reduced afterbody {C} cells",
+            "precision": "fp32-chosen", "cells": C, "lines": len(p.lines), "grid_points": p.grid.n,
+            "chunk_points": p.chunk, "surface_points": P, "rays": P * len(geo.mu) * int(geo.n_phi),
+            "step": f"one {p.chunk:,}-point spectral chunk of the solve ({-(-p.grid.n // p.chunk)} steps = one "
+                    f"solve), {'two-stream' if args.streams == 2 else 'one-stream'} pipeline, populations at each "
+                    f"solve's first chunk",
+            "l2": "inputs larger than L2 (a 42 GB kappa / j table per step)",
+            "parallelism": f"spectral shards x{world} (every {world}-th chunk a rank, one FP64 "
+                           f"all-reduce of the wall flux)" if world > 1 else "one GPU"}
+
+
 def run_headline(args):
     """The afterbody chunk steps (module docstring).  With N ranks each rank
     takes every N-th chunk of the solve (a spectral shard: the chunks are
@@ -860,16 +876,8 @@ def run_headline(args):
     out = {"metric": METRIC, "value": value, "unit": "cell·λ points/s", "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD if not (args.ab_small or args.ab_cells) else f"reduced afterbody {C} cells",
-                      "precision": "fp32-chosen", "cells": C, "lines": len(p.lines), "grid_points": n,
-                      "chunk_points": chunk, "surface_points": P, "rays": int(dp.rays.n_dirs), "segments": nseg,
-                      "step": f"one 65,536-point spectral chunk of the solve (16 steps = one solve), "
-                              f"{'two-stream' if ctx2 is not None else 'one-stream'} pipeline, populations at each "
-                              f"solve's first chunk",
-                      "l2": "inputs larger than L2 (a 42 GB kappa / j table per step)",
-                      "parallelism": f"spectral shards x{world} (every {world}-th chunk a rank, one FP64 "
-                                     f"all-reduce of the wall flux)" if world > 1 else "one GPU"},
-           "secondary": {"ray_lambda_segments_per_s": seg_lambda / (total_ms * 1e-3),
+           "config": headline_config(args, p, world),
+           "secondary": {"segments": nseg, "ray_lambda_segments_per_s": seg_lambda / (total_ms * 1e-3),
                          "solve_s": solve_ms * 1e-3 if solve_ms else None,
                          "line_sum_ms_mean": lsum_mean, "march_ms_mean": march_mean, "wall_s": t_wall,
                          "q_mean_W_cm2": float(qsum.mean().item()) if world == 1 else None},
@@ -907,21 +915,33 @@ def run_headline(args):
 
     if not args.no_e2e:
         # end to end through the public API: host arrays -> pinned staging -> device -> q on the host,
-        # one chunk a call (with --streams 2 cut in two halves, pipelined on the two streams)
-        n_e2e = max(1, min(3, K))
+        # one chunk a call (with --streams 2 cut in two halves, pipelined on the two streams), over one
+        # whole pass of this rank's chunks, so that its chunk mix is the solve's (the chunks' line-sum
+        # costs differ 60-fold)
+        n_e2e = len(mine)
         sub = chunk if ctx2 is None else chunk // 2
-        solver.solve_host(p, R.FP32, sub, ctx=ctx, ctx2=ctx2, k_start=mine[0][0], k_stop=sum(mine[0]))
+        k0, nk = mine[-1]
+        solver.solve_host(p, R.FP32, sub, ctx=ctx, ctx2=ctx2, k_start=k0, k_stop=k0 + nk)
         barrier(dev, world)
         t0w = time.perf_counter()
         cl_e2e = 0
         for s in range(n_e2e):
-            k0, nk = mine[s % len(mine)]
+            k0, nk = mine[s]
             _qh, bi, bo = solver.solve_host(p, R.FP32, sub, ctx=ctx, ctx2=ctx2, k_start=k0, k_stop=k0 + nk)
             cl_e2e += C * nk
+        barrier(dev, world)
         te = time.perf_counter() - t0w
-        out["e2e"] = {"value": world * cl_e2e / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
+        if world > 1:
+            t = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+            w = torch.tensor([float(cl_e2e)], dtype=torch.float64, device=dev)
+            dist.all_reduce(w, op=dist.ReduceOp.SUM)
+            cl_e2e = float(w.item())
+        out["e2e"] = {"value": cl_e2e / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
                       "d2h_bytes_per_step": bo, "ms_per_step": te / n_e2e * 1e3, "steps": n_e2e,
-                      "note": "each step builds the ray segments from the geometry as well"}
+                      "note": "one whole pass over the chunks (the solve's chunk mix), one chunk a call; each "
+                              "call also builds the ray segments from the geometry"}
     if not args.no_secondary and world == 1:
         ctx.close()
         if ctx2 is not None:
