@@ -940,6 +940,7 @@ def run_headline(args):
             cl_e2e = float(w.item())
         out["e2e"] = {"value": cl_e2e / te, "unit": "cell·λ points/s", "h2d_bytes_per_step": bi,
                       "d2h_bytes_per_step": bo, "ms_per_step": te / n_e2e * 1e3, "steps": n_e2e,
+                      "device_ms_per_step_same_chunks": solve_ms / len(mine) if solve_ms else None,
                       "note": "one whole pass over the chunks (the solve's chunk mix), one chunk a call; each "
                               "call also builds the ray segments from the geometry"}
     if not args.no_secondary and world == 1:

@@ -39,7 +39,8 @@ LAM_H = 91.1267   # nm, hydrogen's bound-free edge (Sec. 2.2.1)
 def planck(lam_nm, T):
     """Planck function, W/cm^2/sr/um (the form of Sec. 2.2)."""
     lcm = np.asarray(lam_nm) * 1e-7
-    return 1e-7 * 2.0 * H * CL * CL / (1e4 * lcm ** 5 * np.expm1(H * CL / (lcm * KB * T)))
+    with np.errstate(over="ignore"):   # cold gas: expm1 overflows to inf and B to 0, as it should
+        return 1e-7 * 2.0 * H * CL * CL / (1e4 * lcm ** 5 * np.expm1(H * CL / (lcm * KB * T)))
 
 
 def ln_planck(lam_nm, T):
