@@ -92,12 +92,12 @@ def parse():
 
 
 # DRAM bytes (read + write) of one timed FP32 line-sum launch on the stagnation line
-# at full size (200 cells x 1e6 points, tiling 128 x 2), from a one-pass ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source
-# with this digest (source_digest).  Other cell / point counts scale in proportion (the bytes are
-# the kappa / j rows written); a different source (comments aside) gives null.
-LINE_SUM_TRAFFIC = {"sha1": "7fab173bb0d4922c72abfe911a4abe30f0932817", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 50_309_888 + 1_540_463_872}
+# at full size (200 cells x 1e6 points, tiling 128 x 2, the persistent launch), from a
+# one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel
+# source with this digest (source_digest).  Other cell / point counts scale in proportion (the
+# bytes are the kappa / j rows written); a different source (comments aside) gives null.
+LINE_SUM_TRAFFIC = {"sha1": "26fefb50e0990e7161ec63be2cdc334d30889191", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 53_938_944 + 1_543_512_064}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
@@ -901,7 +901,7 @@ def run_headline(args):
     xu = sum(per_chunk[s % len(mine)][0] for s in range(K))
     ev_total = sum(per_chunk[s % len(mine)][1] for s in range(K))
     xu_peak = n_sm * 16 * sm_max / 1e9
-    out["line_sum"] = {"kernel": "k_line_sum_f32", "bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)",
+    out["line_sum"] = {"kernel": "k_line_sum_f32_persist", "bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)",
                        "evaluations_per_step": ev_total / K,
                        "ms_mean": lsum_mean,
                        "xu_frac": xu / (float(np.sum(k_ms)) * 1e-3) / 1e9 / xu_peak,
@@ -1021,7 +1021,7 @@ def stagnation_block(args, local, world, rank, fp64=True):
            "line_sum_roofline": {"bound": "alu", "pipe": "xu (MUFU ex2/rsqrt/rcp)", "achieved": xu_ops / (kms * 1e-3) / 1e9,
                                  "peak": peak, "unit": "Gop/s", "frac": xu_ops / (kms * 1e-3) / 1e9 / peak,
                                  "traffic": line_sum_traffic(C, K), "traffic_algorithmic_bytes": C * K * 8,
-                                 "kernel": "k_line_sum_f32", "kernel_ms": kms, "evaluations": stats["evaluations"],
+                                 "kernel": "k_line_sum_f32_persist", "kernel_ms": kms, "evaluations": stats["evaluations"],
                                  "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"},
            "clocks": clk.summary()}
     q32 = float(r32["q"].item())

@@ -199,6 +199,18 @@ RAPRAL_API int rapral_set_constants(rapral_ctx* ctx, int codata);
  * default.  Used by the autotuner. */
 RAPRAL_API int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block);
 
+/* How the FP32 line sum (Sec. 2.2.1: the sum over lines of strength times
+ * profile at every cell and grid point) is launched, for the default line
+ * shape without the optional Lorentz terms or departure coefficients.  Its
+ * work units are (spectral tile, group of cells_per_block cells).
+ * blocks_per_sm = -1 (the default): a persistent launch of as many blocks
+ * as fit on every SM, which take the units in tile order from an atomic
+ * counter (cleared on the context's stream before each launch); n in
+ * 1 .. 32: the same with n blocks a SM; 0: one block per unit.  Every unit
+ * is computed the same way in all three, so the results are bitwise the
+ * same.  Errors: EINVAL (blocks_per_sm outside -1 .. 32). */
+RAPRAL_API int rapral_set_line_sum_blocks(rapral_ctx* ctx, int blocks_per_sm);
+
 /* Work counters of the line sum, accumulated over rapral_spectral_coeffs
  * calls since the last reset: in-window (line, cell, grid point) profile
  * evaluations, how many of them needed the Gaussian core term and the

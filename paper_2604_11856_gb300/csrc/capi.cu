@@ -89,8 +89,9 @@ int rapral_create(rapral_ctx** out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 16 * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stats, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) ctx->d_unit = ctx->d_stats + 4;
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
@@ -187,6 +188,14 @@ int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block) {
             return set_error(ctx, RAPRAL_EINVAL, "cells per block %d not 2, 4 or 8", cells_per_block);
         ctx->cells_per_block = cells_per_block;
     }
+    return RAPRAL_OK;
+}
+
+int rapral_set_line_sum_blocks(rapral_ctx* ctx, int blocks_per_sm) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (blocks_per_sm < -1 || blocks_per_sm > 32)
+        return set_error(ctx, RAPRAL_EINVAL, "line-sum blocks per SM %d not in -1 .. 32", blocks_per_sm);
+    ctx->ls_persist = blocks_per_sm;
     return RAPRAL_OK;
 }
 

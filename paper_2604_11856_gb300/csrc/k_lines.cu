@@ -1000,6 +1000,56 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
     if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
+// The same line sum as a persistent launch: a fixed number of blocks pull
+// the units (tile, group of WPB cells) of k_line_sum_f32's grid, in its
+// order (tile by tile), from an atomic counter; each warp does the same
+// work as there, so the sums are bitwise the same.
+template <int PPT, int WPB>
+__global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f32_persist(LineSumArgs a, int64_t n_groups,
+                                                                            int64_t total,
+                                                                            unsigned long long* counter) {
+    if (*a.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ float4 sm0[WPB][32];
+    __shared__ float4 sm1[WPB][32];
+    __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
+    __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
+    __shared__ float4 acc[WPB][32 * PPT];
+    __shared__ long long unit_s;
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (;;) {
+        if (threadIdx.x == 0) unit_s = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const int64_t u = unit_s;
+        __syncthreads();
+        if (u >= total) break;
+        const int t = (int)(u / n_groups);
+        const int64_t c = (u - (int64_t)t * n_groups) * WPB + warp;
+        if (c < a.C) warp_tile_f32<PPT, 0>(a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
+        __syncwarp();
+    }
+    if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
+}
+
+// Launches k_line_sum_f32_persist over the units of grid g: ctx->ls_persist
+// blocks a SM, or as many as fit (-1); the unit counter (ctx->d_unit) is
+// cleared on the stream first.
+template <int PPT, int WPB>
+static cudaError_t launch_persist(rapral_ctx* ctx, const LineSumArgs& a, dim3 g) {
+    int dev = 0, sms = 0, per_sm = ctx->ls_persist;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && per_sm < 0)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_f32_persist<PPT, WPB>, 32 * WPB, 0);
+    unsigned long long* counter = ctx->d_unit;
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)g.x * g.y;
+    const int64_t blocks = std::min<int64_t>(total, (int64_t)sms * std::max(1, per_sm));
+    k_line_sum_f32_persist<PPT, WPB><<<(unsigned)blocks, 32 * WPB, 0, ctx->stream>>>(a, (int64_t)g.x, total, counter);
+    return cudaGetLastError();
+}
+
 // Persistent line sum over many independent requests: blocks pull work
 // units (request, tile, group of WPB cells) from one atomic counter until the
 // list is exhausted; units of a request are ordered tile by tile so blocks
@@ -1153,7 +1203,11 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
     }
     const int wpb = a.tile_w == 512 ? 4 : ctx->cells_per_block;
     dim3 g32(div_up(a.C, wpb), grid.y);
-#define RAPRAL_LS32(PPT, WPB) k_line_sum_f32<PPT, WPB><<<g32, 32 * WPB, 0, ctx->stream>>>(a)
+#define RAPRAL_LS32(PPT, WPB)                                                  \
+    do {                                                                       \
+        if (ctx->ls_persist != 0 && ctx->d_unit) return launch_persist<PPT, WPB>(ctx, a, g32); \
+        k_line_sum_f32<PPT, WPB><<<g32, 32 * WPB, 0, ctx->stream>>>(a);        \
+    } while (0)
     if (a.tile_w == 128 && wpb == 2) RAPRAL_LS32(4, 2);
     else if (a.tile_w == 128 && wpb == 4) RAPRAL_LS32(4, 4);
     else if (a.tile_w == 128 && wpb == 8) RAPRAL_LS32(4, 8);

@@ -5,7 +5,9 @@
 // the allocator (an allocation can block on the driver for an unbounded
 // time), and plug-ins running inside a host program that owns all device
 // memory through its own pool, which must not be fragmented or exceeded.  This entry point
-// runs the same kernels as rapral_spectral_coeffs, but every scratch buffer
+// runs the same kernels as rapral_spectral_coeffs (its FP32 line sum as one
+// block per work unit, which gives bitwise the same sums as the regular
+// entry point's persistent launch), but every scratch buffer
 // (per-line and per-cell records, the tile ranges, the tile lists, the
 // status and counter words) lives in one file-scope __device__ array of
 // SCRATCH_BYTES.  The caller passes inputs and outputs; nothing is allocated

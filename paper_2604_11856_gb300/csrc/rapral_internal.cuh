@@ -140,6 +140,7 @@ struct rapral_ctx {
     int codata = 0;
     int tile_w = 0;            // grid points per line-sum tile (0: 512 for FP64, 128 for FP32)
     int cells_per_block = 4;   // warps (cells) per FP32 line-sum block
+    int ls_persist = -1;       // FP32 line sum: persistent with this many blocks a SM (-1: as many as fit; 0: a block a unit)
     // workspace arena (grown on demand; all users are stream-ordered)
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -147,6 +148,7 @@ struct rapral_ctx {
     int* d_status = nullptr;
     int* h_pinned = nullptr;    // [16] pinned scratch for small read-backs
     unsigned long long* d_stats = nullptr;   // [4] line-sum work counters
+    unsigned long long* d_unit = nullptr;    // the persistent line sum's unit counter (null: no persistent launch)
     int count_work = 1;                      // counters on (rapral_set_counters)
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing events
     BroadArgs broad = {};                    // optional Lorentz terms (flags 0: off)

@@ -125,6 +125,7 @@ def load(build_if_missing=True):
             "rapral_clear_status": (i, [vp]),
             "rapral_set_constants": (i, [vp, i]),
             "rapral_set_tiling": (i, [vp, i, i]),
+            "rapral_set_line_sum_blocks": (i, [vp, i]),
             "rapral_workspace_bytes": (i, [i64, i64, i64, P(ct.c_size_t)]),
             "rapral_get_stats": (i, [vp, P(Stats)]),
             "rapral_reset_stats": (i, [vp]),
@@ -225,6 +226,11 @@ class Context:
 
     def set_tiling(self, tile_width=0, cells_per_block=0):
         self.check(self.lib.rapral_set_tiling(self.h, tile_width, cells_per_block))
+
+    def set_line_sum_blocks(self, blocks_per_sm=-1):
+        """FP32 line-sum launch: -1 persistent at full occupancy (default),
+        n > 0 persistent with n blocks a SM, 0 one block per work unit."""
+        self.check(self.lib.rapral_set_line_sum_blocks(self.h, blocks_per_sm))
 
     def get_stats(self):
         st = Stats()

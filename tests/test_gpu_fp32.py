@@ -65,6 +65,43 @@ def test_coeffs_fp32_stagnation(ctx):
     assert point_error(kap, rk, ra, what="kappa") <= TOL_POINT
 
 
+@pytest.mark.parametrize("tile,cpb", [(128, 2), (128, 4), (128, 8), (256, 4), (512, 4)])
+def test_line_sum_launch_forms_are_bitwise_equal(ctx, tile, cpb):
+    """The FP32 line sum launched persistently (as many blocks as fit, or one
+    block a SM, taking the units from a counter) and as one block per unit:
+    the same coefficients to the bit and the same work counts, on a ragged
+    cell count and a range that starts and ends inside a tile."""
+    p = synth.stagnation_line(n_cells=19, n_atomic=3000, n_molecular=40000, n_grid=60001)
+    dp = solver.DeviceProblem(p, ctx)
+    k0, nk = 1234, 50000
+    out = {}
+    ctx.set_tiling(tile_width=tile, cells_per_block=cpb)
+    try:
+        for blocks in (-1, 1, 0):
+            ctx.set_line_sum_blocks(blocks)
+            R.populations(ctx, dp.species, dp.cells)
+            kap = torch.empty((dp.C, nk), dtype=torch.float32, device=ctx.device)
+            em = torch.empty_like(kap)
+            ctx.reset_stats()
+            R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, p.grid, k0, nk, R.FP32, kap, em)
+            ctx.sync()
+            out[blocks] = (kap.cpu().numpy(), em.cpu().numpy(), ctx.get_stats())
+    finally:
+        ctx.set_line_sum_blocks(-1)
+        ctx.set_tiling(tile_width=-1, cells_per_block=4)
+    for blocks in (1, 0):
+        assert np.array_equal(out[blocks][0], out[-1][0]) and np.array_equal(out[blocks][1], out[-1][1]), blocks
+        assert out[blocks][2] == out[-1][2]
+    assert np.isfinite(out[-1][0]).all() and out[-1][2]["evaluations"] > 0
+
+
+def test_line_sum_blocks_checked(ctx):
+    for bad in (-2, 33):
+        with pytest.raises(R.RapralError):
+            ctx.set_line_sum_blocks(bad)
+    ctx.set_line_sum_blocks(-1)
+
+
 @pytest.mark.parametrize("tile", [None, 256])
 def test_fp32_window_decisions_match_fp64(ctx, tile):
     """The FP32 path includes exactly the (line, point) pairs the FP64 path
