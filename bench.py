@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["rapral", "reference"], default="rapral")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="seconds of oracle work in the cpu_baseline sample (and at most per reference-arm step)")
     ap.add_argument("--no-secondary", action="store_true", help="headline only: skip the stagnation and served blocks")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-requests block")
     ap.add_argument("--serve-requests", type=int, default=100, help="FP32 requests per offered rate")
@@ -359,7 +360,7 @@ def run_reference(args):
         return 0
     p = afterbody_problem(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_baseline(p, per_step / 4)
     vals, secs = [], []
