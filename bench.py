@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--serve-rates", type=str, default="4,50,2000",
                     help=f"offered rates, req/s (the whole study: {','.join(str(int(r)) for r in SERVE_RATES)})")
     ap.add_argument("--serve-fp64-rates", type=str, default="2000")
+    ap.add_argument("--serve-slots", type=int, default=4, help="served block: concurrent request slots")
+    ap.add_argument("--serve-solo", action="store_true",
+                    help="served block: also run each rate's FP32 requests back to back on one stream (no "
+                         "arrival gaps, one at a time), the capacity the served loop compares with")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default tiling)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32", help="stagnation workload only")
@@ -324,7 +328,7 @@ def served(p, args, device):
     pool = (p.lines, p.species, {})
     rates = [float(r) for r in args.serve_rates.split(",") if r]
     rates64 = {float(r) for r in args.serve_fp64_rates.split(",") if r}
-    res = {"slots": 4, "admission": "device free memory at start minus a 16 GiB reserve", "rates": []}
+    res = {"slots": args.serve_slots, "admission": "device free memory at start minus a 16 GiB reserve", "rates": []}
     errs_all = []
     for i, rate in enumerate(rates):
         gen = synth.served_requests(seed=1004 + i, n_requests=args.serve_requests, rate=rate, pool=pool)
@@ -335,11 +339,18 @@ def served(p, args, device):
                 continue
             reqs = [serve.Request(rid=j, problem=g["problem"], arrival=g["t"], precision=prec)
                     for j, g in enumerate(gen[:n])]
-            srv = serve.Server(p.lines, p.species, device=device, slots=4)
+            srv = serve.Server(p.lines, p.species, device=device, slots=args.serve_slots)
             row[name] = serve.run_open_loop(srv, reqs)
             res["budget_bytes"] = srv.budget
             if prec == R.FP32:
                 q32 = {r.rid: r.q for r in reqs if r.status == "done"}
+                if args.serve_solo:
+                    t0 = time.perf_counter()
+                    solo = serve.solo(reqs, p.lines, p.species, device=device)
+                    dt = time.perf_counter() - t0
+                    row["fp32_back_to_back"] = {"requests": len(solo), "seconds": dt, "req_s": len(solo) / dt,
+                                                "max_q_rel_diff_vs_served": float(max(
+                                                    np.max(np.abs(q32[k] / solo[k] - 1)) for k in q32))}
             else:
                 errs = [float(np.max(np.abs(q32[r.rid] / r.q - 1))) for r in reqs
                         if r.status == "done" and r.rid in q32]

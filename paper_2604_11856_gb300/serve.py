@@ -116,16 +116,18 @@ class Server:
             self.cv.notify_all()
         return True
 
+    def _admissible(self):
+        return bool(self.pending) and self.free_slots > 0 and self.in_use + self.pending[0].nbytes <= self.budget
+
     def _scheduler(self):
         while True:
             with self.cv:
-                while not self.stop and not (self.pending and self.free_slots > 0 and
-                                             self.in_use + self.pending[0].nbytes <= self.budget):
+                # wait (never spin) until the head of the queue fits, or the
+                # server is closing with nothing left to admit
+                while not self._admissible() and not (self.stop and not self.pending):
                     self.cv.wait(0.05)
-                if self.stop and not self.pending:
+                if not self._admissible():   # closing and the queue is empty
                     break
-                if not (self.pending and self.free_slots > 0 and self.in_use + self.pending[0].nbytes <= self.budget):
-                    continue
                 req = self.pending.popleft()
                 self.in_use += req.nbytes
                 self.high_water = max(self.high_water, self.in_use)
