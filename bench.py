@@ -62,6 +62,8 @@ def parse():
                     help=f"offered rates, req/s (the whole study: {','.join(str(int(r)) for r in SERVE_RATES)})")
     ap.add_argument("--serve-fp64-rates", type=str, default="2000")
     ap.add_argument("--serve-slots", type=int, default=4, help="served block: concurrent request slots")
+    ap.add_argument("--pairs-per-pass", type=int, choices=[32, 64], default=32,
+                    help="afterbody: (line, cell) pairs a warp of the FP32 line sum stages per sweep pass")
     ap.add_argument("--serve-solo", action="store_true",
                     help="served block: also run each rate's FP32 requests back to back on one stream (no "
                          "arrival gaps, one at a time), the capacity the served loop compares with")
@@ -473,7 +475,7 @@ def run_batch(args):
     from paper_2604_11856_gb300 import autotune, batch, rapral as R, solver, synth
     probs = synth.batch_slabs()
     ctx = R.Context(0)
-    tw, wpb, times = autotune.tune(ctx, max(probs, key=lambda q: len(q.lines)))
+    tw, wpb, pb, times = autotune.tune(ctx, max(probs, key=lambda q: len(q.lines)))
     bs = batch.BatchSolver(probs, ctx, chunk=65536)
     bs.run(); ctx.sync()
     bs.capture()
@@ -496,7 +498,7 @@ def run_batch(args):
     ctx.sync()
     t_seq = a.elapsed_time(b) * 1e-3
     print(json.dumps({"workload": "64 uneven slab solves (cells 20-2000, 1e5-2e6 points, 1e3-5e4 atomic + "
-                                  "0-3e5 molecular lines)", "tiling": [tw, wpb], "graph_ms": t * 1e3,
+                                  "0-3e5 molecular lines)", "tiling": [tw, wpb, pb], "graph_ms": t * 1e3,
                       "cell_lambda_per_s": cl / t, "sequential_ms": t_seq * 1e3,
                       "sequential_cell_lambda_per_s": cl / t_seq, "rounds": len(bs.handles),
                       "units": bs.units()[:3]}))
@@ -773,6 +775,7 @@ def run_headline(args):
     sa = torch.cuda.Stream(dev)
     ctx = R.Context(local, stream=sa)
     ctx2 = R.Context(local, stream=torch.cuda.Stream(dev)) if args.streams == 2 else None
+    ctx.set_line_batch(args.pairs_per_pass)
     dp = solver.DeviceProblem(p, ctx)   # ray segments: built once per geometry
     ctx.sync()
     C, P, n, chunk = dp.C, dp.P, p.grid.n, p.chunk
@@ -988,8 +991,8 @@ def stagnation_block(args, local, world, rank, fp64=True):
     dev = torch.device("cuda", local)
     p = synth.stagnation_line(n_cells=args.cells)
     ctx = R.Context(local)
-    tw, wpb, times = autotune.tune(ctx, p)
-    tuned = {"tile_width": tw, "cells_per_block": wpb, "candidates_ms": times}
+    tw, wpb, pb, times = autotune.tune(ctx, p)
+    tuned = {"tile_width": tw, "cells_per_block": wpb, "pairs_per_pass": pb, "candidates_ms": times}
     dp = solver.DeviceProblem(p, ctx)
     C, K = dp.C, p.grid.n
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

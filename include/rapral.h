@@ -211,6 +211,18 @@ RAPRAL_API int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_
  * same.  Errors: EINVAL (blocks_per_sm outside -1 .. 32). */
 RAPRAL_API int rapral_set_line_sum_blocks(rapral_ctx* ctx, int blocks_per_sm);
 
+/* Lines a warp of the FP32 line sum stages per sweep pass (Sec. 2.2.1: a
+ * cell's coefficients over a spectral tile are the sum over the tile's line
+ * list): 32 (the default, one (line, cell) pair set up by each lane) or 64
+ * (two passes of set-up, then one sweep over all 64).  Terms are added
+ * plainly inside a pass and with compensation across passes, so the plain
+ * part's error bound is (pairs - 1) u of a point's term magnitudes
+ * (u = 2^-24).  Used by the autotuner with rapral_set_tiling; batches take
+ * the value current at rapral_batch_create (32 with the optional Lorentz
+ * terms); the exact Voigt shape and the optional terms use 32.
+ * Errors: EINVAL (not 32 or 64). */
+RAPRAL_API int rapral_set_line_batch(rapral_ctx* ctx, int pairs);
+
 /* Work counters of the line sum, accumulated over rapral_spectral_coeffs
  * calls since the last reset: in-window (line, cell, grid point) profile
  * evaluations, how many of them needed the Gaussian core term and the

@@ -1,5 +1,5 @@
-"""Autotuner of the FP32 line sum: spectral tile width and cells (warps) per
-block.
+"""Autotuner of the FP32 line sum: spectral tile width, cells (warps) per
+block and lines (line, cell pairs) a warp stages per sweep pass.
 
 For a workload class (GPU, line count, grid spacing) it times the
 coefficient step of a representative sample -- a chunk from the middle of
@@ -20,7 +20,7 @@ from . import build as _build
 from . import rapral as R
 from . import solver, synth
 
-CANDIDATES = [(128, 2), (128, 4), (128, 8), (256, 2), (256, 4), (256, 8)]
+CANDIDATES = [(tw, wpb, pb) for pb in (32, 64) for tw in (128, 256) for wpb in (2, 4, 8)]
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 
 
@@ -58,14 +58,15 @@ def sample_problem(problem, n_cells=48):
 
 
 def tune(ctx, problem, precision=R.FP32, nk=65536, reps=3, use_cache=True, candidates=CANDIDATES):
-    """Returns (tile_width, cells_per_block, timings) and applies the choice
-    to `ctx`."""
+    """Returns (tile_width, cells_per_block, pairs_per_pass, timings) and
+    applies the choice to `ctx`."""
     key = _key(problem, precision)
     cache = _load() if use_cache else {}
-    if use_cache and key in cache:
-        tw, wpb = cache[key]["choice"]
+    if use_cache and key in cache and len(cache[key]["choice"]) == 3:
+        tw, wpb, pb = cache[key]["choice"]
         ctx.set_tiling(tw, wpb)
-        return tw, wpb, cache[key]["ms"]
+        ctx.set_line_batch(pb)
+        return tw, wpb, pb, cache[key]["ms"]
     sp = sample_problem(problem)
     dp = solver.DeviceProblem(sp, ctx)
     R.populations(ctx, dp.species, dp.cells)
@@ -74,8 +75,9 @@ def tune(ctx, problem, precision=R.FP32, nk=65536, reps=3, use_cache=True, candi
     kap = torch.empty((dp.C, nk), dtype=torch.float32, device=ctx.device)
     em = torch.empty_like(kap)
     times = {}
-    for tw, wpb in candidates:
+    for tw, wpb, pb in candidates:
         ctx.set_tiling(tw, wpb)
+        ctx.set_line_batch(pb)
         R.spectral_coeffs(ctx, dp.species, dp.lines, dp.cells, sp.grid, k0, nk, precision, kap, em)   # warm
         ctx.sync()
         ms = []
@@ -87,12 +89,13 @@ def tune(ctx, problem, precision=R.FP32, nk=65536, reps=3, use_cache=True, candi
             ctx.set_profile_events(None, None)
             ctx.sync()
             ms.append(a.elapsed_time(b))
-        times[f"{tw}x{wpb}"] = float(np.median(ms))
+        times[f"{tw}x{wpb}x{pb}"] = float(np.median(ms))
     best = min(times, key=times.get)
-    tw, wpb = (int(x) for x in best.split("x"))
+    tw, wpb, pb = (int(x) for x in best.split("x"))
     ctx.set_tiling(tw, wpb)
+    ctx.set_line_batch(pb)
     if use_cache:
         cache = _load()
-        cache[key] = {"choice": [tw, wpb], "ms": times}
+        cache[key] = {"choice": [tw, wpb, pb], "ms": times}
         _store(cache)
-    return tw, wpb, times
+    return tw, wpb, pb, times

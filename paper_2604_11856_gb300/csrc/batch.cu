@@ -28,7 +28,7 @@ struct BatchReq {
 
 struct rapral_batch {
     int n = 0;
-    int tile_w = 128, wpb = 4;
+    int tile_w = 128, wpb = 4, pb = 32;   // tiling, cells a block, pairs a sweep pass
     bool broad = false;           // the optional Lorentz terms were planned in
     std::vector<BatchReq> req;
     char* ws = nullptr;           // records, tile ranges, offsets of every request
@@ -76,6 +76,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
     B->tile_w = ctx->tile_w ? ctx->tile_w : 128;
     B->wpb = (B->tile_w == 512 || broad_terms(&ctx->broad)) ? 4 : ctx->cells_per_block;
     B->broad = broad_terms(&ctx->broad);
+    B->pb = B->broad ? 32 : ctx->pairs_per_batch;
     const int W = B->tile_w;
     B->req.resize(n_items);
     // phase 1 sizes
@@ -206,7 +207,7 @@ int rapral_batch_create(rapral_ctx* ctx, int n_items, const rapral_batch_item* i
         e = cudaMemcpyAsync(B->d_items, hitems.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice,
                             ctx->stream);
     if (e == cudaSuccess)
-        e = launch_line_sum_batch(ctx, W, B->wpb, nullptr, 0, 0, nullptr, &B->blocks, false, B->broad);
+        e = launch_line_sum_batch(ctx, W, B->wpb, B->pb, nullptr, 0, 0, nullptr, &B->blocks, false, B->broad);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (h_tot) cudaFreeHost(h_tot);
     if (e != cudaSuccess) {
@@ -230,7 +231,7 @@ int rapral_batch_run(rapral_ctx* ctx, rapral_batch* B) {
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), ctx->stream);
     if (ctx->ev_before && e == cudaSuccess) e = cudaEventRecord(ctx->ev_before, ctx->stream);
     if (e == cudaSuccess)
-        e = launch_line_sum_batch(ctx, B->tile_w, B->wpb, B->d_items, B->n, B->total_units, B->d_counter, nullptr,
+        e = launch_line_sum_batch(ctx, B->tile_w, B->wpb, B->pb, B->d_items, B->n, B->total_units, B->d_counter, nullptr,
                                   true, B->broad);
     if (ctx->ev_after && e == cudaSuccess) e = cudaEventRecord(ctx->ev_after, ctx->stream);
     for (int i = 0; i < B->n && e == cudaSuccess; ++i) {

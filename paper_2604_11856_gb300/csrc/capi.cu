@@ -191,6 +191,14 @@ int rapral_set_tiling(rapral_ctx* ctx, int tile_width, int cells_per_block) {
     return RAPRAL_OK;
 }
 
+int rapral_set_line_batch(rapral_ctx* ctx, int pairs) {
+    if (!ctx) return RAPRAL_EINVAL;
+    if (pairs != 32 && pairs != 64)
+        return set_error(ctx, RAPRAL_EINVAL, "line-sum pairs per pass %d not 32 or 64", pairs);
+    ctx->pairs_per_batch = pairs;
+    return RAPRAL_OK;
+}
+
 int rapral_set_line_sum_blocks(rapral_ctx* ctx, int blocks_per_sm) {
     if (!ctx) return RAPRAL_EINVAL;
     if (blocks_per_sm < -1 || blocks_per_sm > 32)

@@ -878,7 +878,7 @@ __device__ __forceinline__ void sweep_pair_voigt(const VoigtCoef& vc, float lo, 
 // The staged pairs are grouped by class (bracket mode, and whether the
 // window covers the whole tile, where two points go per packed FP32
 // instruction), one loop per class.  Warps never wait for each other.
-template <int PPT, int FL>
+template <int PPT, int FL, int PB = 32>
 __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64_t c, float4* sm0, float4* sm1,
                                               float2* smlp, float2* smcb, float4* acc, int lane, int64_t* cnt) {
     constexpr int TW = 32 * PPT;
@@ -888,7 +888,7 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     const float lanef = (float)lane;       // lane's first point, relative to kt0
     // compensated sums (Kahan) of the per-batch partial sums, kept in shared
     // memory (acc[i * 32 + lane] = (s_j, c_j, s_k, c_k)); inside a batch of at
-    // most 32 lines the terms are added plainly in registers (error <= 31 u
+    // most PB lines the terms are added plainly in registers (error <= (PB - 1) u
     // of the batch's magnitude, u = 2^-24)
     float bk[PPT], bj[PPT];
 #pragma unroll
@@ -907,52 +907,59 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
     }
     __syncwarp();
     const int beg = a.tile_off[t], end = a.tile_off[t + 1];
-    for (int b = beg; b < end; b += 32) {
-        const int nb = min(32, end - b);
-        PairF32 P;
-        bool valid = false;
-        if (lane < nb) {
-            const int l = a.tile_lines[b + lane];
-            const LineF32 L = a.lf[l];
-            valid = setup_pair_f32<FL>(a, L, cp, smlp[L.species], (FL & 1) ? smcb[L.species] : make_float2(0.f, 0.f), l,
-                                       c, hf, inv_hf, kt0, kt0f, kt1f,
-                                   count, &P, cnt);
-        }
+    constexpr int NH = PB / 32;   // staged halves of 32 pairs (one pair a lane each)
+    constexpr int NCLS = (FL & 4) ? 1 : 6;
+    for (int b = beg; b < end; b += PB) {
         // stage the pairs that reach the tile grouped by class (bracket mode,
         // plus 3 where the window covers the whole tile; one class with the
         // exact Voigt shape), in lane order within a class, so the sweeps
-        // below run one loop per class with no test per pair
-        constexpr int NCLS = (FL & 4) ? 1 : 6;
-        int cls = -1;
-        if (valid) cls = (FL & 4) ? 0 : P.mode + ((P.lo <= 0.0f && P.hi >= (float)(TW - 1)) ? 3 : 0);
-        const unsigned lt = (1u << lane) - 1u;
-        int base[NCLS + 1];
-        int pos = 0;
-        base[0] = 0;
+        // below run one loop per class with no test per pair; with PB = 64
+        // the second 32 pairs are staged in their own half the same way
+        int base[NH][NCLS + 1];
 #pragma unroll
-        for (int k = 0; k < NCLS; ++k) {
-            const unsigned m = __ballot_sync(0xffffffffu, cls == k);
-            if (cls == k) pos = base[k] + __popc(m & lt);
-            base[k + 1] = base[k] + __popc(m);
-        }
-        if (cls >= 0) {
-            sm0[pos] = make_float4(P.lo, P.hi, P.ub, P.s);
-            sm1[pos] = make_float4(P.r, P.ub_lo, P.aj, P.ak);
+        for (int hh = 0; hh < NH; ++hh) {
+            const int nb = min(32, end - (b + 32 * hh));
+            PairF32 P;
+            bool valid = false;
+            if (lane < nb) {
+                const int l = a.tile_lines[b + 32 * hh + lane];
+                const LineF32 L = a.lf[l];
+                valid = setup_pair_f32<FL>(a, L, cp, smlp[L.species], (FL & 1) ? smcb[L.species] : make_float2(0.f, 0.f),
+                                           l, c, hf, inv_hf, kt0, kt0f, kt1f, count, &P, cnt);
+            }
+            int cls = -1;
+            if (valid) cls = (FL & 4) ? 0 : P.mode + ((P.lo <= 0.0f && P.hi >= (float)(TW - 1)) ? 3 : 0);
+            const unsigned lt = (1u << lane) - 1u;
+            int pos = 0;
+            base[hh][0] = 32 * hh;
+#pragma unroll
+            for (int k = 0; k < NCLS; ++k) {
+                const unsigned m = __ballot_sync(0xffffffffu, cls == k);
+                if (cls == k) pos = base[hh][k] + __popc(m & lt);
+                base[hh][k + 1] = base[hh][k] + __popc(m);
+            }
+            if (cls >= 0) {
+                sm0[pos] = make_float4(P.lo, P.hi, P.ub, P.s);
+                sm1[pos] = make_float4(P.r, P.ub_lo, P.aj, P.ak);
+            }
         }
         __syncwarp();
-        if (FL & 4) {
-            for (int q = 0; q < base[NCLS]; ++q) {
-                const float4 A = sm0[q];
-                const float4 B = sm1[q];
-                sweep_pair_voigt<PPT>(c_voigt, A.x, A.y, lanef, A.w, A.z, B.y, B.x, B.z, B.w, bj, bk);
+#pragma unroll
+        for (int hh = 0; hh < NH; ++hh) {
+            if (FL & 4) {
+                for (int q = base[hh][0]; q < base[hh][NCLS]; ++q) {
+                    const float4 A = sm0[q];
+                    const float4 B = sm1[q];
+                    sweep_pair_voigt<PPT>(c_voigt, A.x, A.y, lanef, A.w, A.z, B.y, B.x, B.z, B.w, bj, bk);
+                }
+            } else {
+                sweep_class<PPT, BR_NEAR, false>(sm0, sm1, base[hh][0], base[hh][1], lanef, bj, bk);
+                sweep_class<PPT, BR_MID, false>(sm0, sm1, base[hh][1], base[hh][2], lanef, bj, bk);
+                sweep_class<PPT, BR_FAR, false>(sm0, sm1, base[hh][2], base[hh][3], lanef, bj, bk);
+                sweep_class<PPT, BR_NEAR, true>(sm0, sm1, base[hh][3], base[hh][4], lanef, bj, bk);
+                sweep_class<PPT, BR_MID, true>(sm0, sm1, base[hh][4], base[hh][5], lanef, bj, bk);
+                sweep_class<PPT, BR_FAR, true>(sm0, sm1, base[hh][5], base[hh][6], lanef, bj, bk);
             }
-        } else {
-            sweep_class<PPT, BR_NEAR, false>(sm0, sm1, base[0], base[1], lanef, bj, bk);
-            sweep_class<PPT, BR_MID, false>(sm0, sm1, base[1], base[2], lanef, bj, bk);
-            sweep_class<PPT, BR_FAR, false>(sm0, sm1, base[2], base[3], lanef, bj, bk);
-            sweep_class<PPT, BR_NEAR, true>(sm0, sm1, base[3], base[4], lanef, bj, bk);
-            sweep_class<PPT, BR_MID, true>(sm0, sm1, base[4], base[5], lanef, bj, bk);
-            sweep_class<PPT, BR_FAR, true>(sm0, sm1, base[5], base[6], lanef, bj, bk);
         }
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
@@ -984,19 +991,19 @@ __device__ __forceinline__ void warp_tile_f32(const LineSumArgs& a, int t, int64
 #endif
 #define RAPRAL_LS_BLOCKS(WPB) (RAPRAL_LS_WARPS / (WPB))
 
-template <int PPT, int WPB, int FL = 0>
+template <int PPT, int WPB, int FL = 0, int PB = 32>
 __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f32(LineSumArgs a) {
     if (*a.status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * WPB + warp;
     if (c >= a.C) return;
-    __shared__ float4 sm0[WPB][32];   // klo, khi, kc (int bits), s
-    __shared__ float4 sm1[WPB][32];   // u0, r, aj, ak
+    __shared__ float4 sm0[WPB][PB];   // lo, hi, ub, s of each staged pair
+    __shared__ float4 sm1[WPB][PB];   // r, ub_lo, aj, ak
     __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float4 acc[WPB][32 * PPT];
     int64_t cnt[4] = {0, 0, 0, 0};
-    warp_tile_f32<PPT, FL>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
+    warp_tile_f32<PPT, FL, PB>(a, blockIdx.y, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
     if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
 }
 
@@ -1004,14 +1011,14 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
 // the units (tile, group of WPB cells) of k_line_sum_f32's grid, in its
 // order (tile by tile), from an atomic counter; each warp does the same
 // work as there, so the sums are bitwise the same.
-template <int PPT, int WPB>
+template <int PPT, int WPB, int PB = 32>
 __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f32_persist(LineSumArgs a, int64_t n_groups,
                                                                             int64_t total,
                                                                             unsigned long long* counter) {
     if (*a.status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ float4 sm0[WPB][32];
-    __shared__ float4 sm1[WPB][32];
+    __shared__ float4 sm0[WPB][PB];
+    __shared__ float4 sm1[WPB][PB];
     __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float4 acc[WPB][32 * PPT];
@@ -1025,7 +1032,7 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
         if (u >= total) break;
         const int t = (int)(u / n_groups);
         const int64_t c = (u - (int64_t)t * n_groups) * WPB + warp;
-        if (c < a.C) warp_tile_f32<PPT, 0>(a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
+        if (c < a.C) warp_tile_f32<PPT, 0, PB>(a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane, cnt);
         __syncwarp();
     }
     if (a.count) block_count(a.stats, cnt[0], cnt[1], cnt[2], cnt[3]);
@@ -1034,19 +1041,19 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_f3
 // Launches k_line_sum_f32_persist over the units of grid g: ctx->ls_persist
 // blocks a SM, or as many as fit (-1); the unit counter (ctx->d_unit) is
 // cleared on the stream first.
-template <int PPT, int WPB>
+template <int PPT, int WPB, int PB>
 static cudaError_t launch_persist(rapral_ctx* ctx, const LineSumArgs& a, dim3 g) {
     int dev = 0, sms = 0, per_sm = ctx->ls_persist;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess && per_sm < 0)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_f32_persist<PPT, WPB>, 32 * WPB, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_f32_persist<PPT, WPB, PB>, 32 * WPB, 0);
     unsigned long long* counter = ctx->d_unit;
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)g.x * g.y;
     const int64_t blocks = std::min<int64_t>(total, (int64_t)sms * std::max(1, per_sm));
-    k_line_sum_f32_persist<PPT, WPB><<<(unsigned)blocks, 32 * WPB, 0, ctx->stream>>>(a, (int64_t)g.x, total, counter);
+    k_line_sum_f32_persist<PPT, WPB, PB><<<(unsigned)blocks, 32 * WPB, 0, ctx->stream>>>(a, (int64_t)g.x, total, counter);
     return cudaGetLastError();
 }
 
@@ -1054,15 +1061,15 @@ static cudaError_t launch_persist(rapral_ctx* ctx, const LineSumArgs& a, dim3 g)
 // units (request, tile, group of WPB cells) from one atomic counter until the
 // list is exhausted; units of a request are ordered tile by tile so blocks
 // working at the same time share a tile's line list in L2.
-template <int PPT, int WPB, bool BR = false>
+template <int PPT, int WPB, bool BR = false, int PB = 32>
 __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_batch(const BatchItem* __restrict__ items,
                                                                        int n_items, int64_t total,
                                                                        unsigned long long* counter,
                                                                        unsigned long long* stats, const int* status) {
     if (*status) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ float4 sm0[WPB][32];
-    __shared__ float4 sm1[WPB][32];
+    __shared__ float4 sm0[WPB][PB];
+    __shared__ float4 sm1[WPB][PB];
     __shared__ float2 smlp[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float2 smcb[WPB][RAPRAL_MAX_SPECIES];
     __shared__ float4 acc[WPB][32 * PPT];
@@ -1084,8 +1091,8 @@ __global__ void __launch_bounds__(32 * WPB, RAPRAL_LS_BLOCKS(WPB)) k_line_sum_ba
         const int t = (int)(local / it.n_groups);
         const int64_t c = (local - (int64_t)t * it.n_groups) * WPB + warp;
         if (c < it.a.C)
-            warp_tile_f32<PPT, BR ? 1 : 0>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp], lane,
-                                           cnt);
+            warp_tile_f32<PPT, BR ? 1 : 0, PB>(it.a, t, c, sm0[warp], sm1[warp], smlp[warp], smcb[warp], acc[warp],
+                                               lane, cnt);
         __syncwarp();
     }
     if (items[0].a.count) block_count(stats, cnt[0], cnt[1], cnt[2], cnt[3]);
@@ -1203,10 +1210,15 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
     }
     const int wpb = a.tile_w == 512 ? 4 : ctx->cells_per_block;
     dim3 g32(div_up(a.C, wpb), grid.y);
-#define RAPRAL_LS32(PPT, WPB)                                                  \
-    do {                                                                       \
-        if (ctx->ls_persist != 0 && ctx->d_unit) return launch_persist<PPT, WPB>(ctx, a, g32); \
-        k_line_sum_f32<PPT, WPB><<<g32, 32 * WPB, 0, ctx->stream>>>(a);        \
+#define RAPRAL_LS32_PB(PPT, WPB, PB)                                                          \
+    do {                                                                                      \
+        if (ctx->ls_persist != 0 && ctx->d_unit) return launch_persist<PPT, WPB, PB>(ctx, a, g32); \
+        k_line_sum_f32<PPT, WPB, 0, PB><<<g32, 32 * WPB, 0, ctx->stream>>>(a);                 \
+    } while (0)
+#define RAPRAL_LS32(PPT, WPB)                                  \
+    do {                                                       \
+        if (ctx->pairs_per_batch == 64) RAPRAL_LS32_PB(PPT, WPB, 64); \
+        else RAPRAL_LS32_PB(PPT, WPB, 32);                     \
     } while (0)
     if (a.tile_w == 128 && wpb == 2) RAPRAL_LS32(4, 2);
     else if (a.tile_w == 128 && wpb == 4) RAPRAL_LS32(4, 4);
@@ -1217,42 +1229,48 @@ static cudaError_t launch_line_sum_grid(rapral_ctx* ctx, const LineSumArgs& a, i
     else if (a.tile_w == 512) RAPRAL_LS32(16, 4);
     else return cudaErrorInvalidValue;
 #undef RAPRAL_LS32
+#undef RAPRAL_LS32_PB
     return cudaGetLastError();
 }
 
-template <int PPT, int WPB, bool BR = false>
+template <int PPT, int WPB, bool BR = false, int PB = 32>
 static cudaError_t batch_launch(rapral_ctx* ctx, const BatchItem* items, int n, int64_t total,
                                 unsigned long long* counter, int* blocks_out, bool launch) {
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_batch<PPT, WPB, BR>, 32 * WPB, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_sum_batch<PPT, WPB, BR, PB>, 32 * WPB, 0);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int blocks = max(1, per_sm) * sms;
     if (blocks_out) *blocks_out = blocks;
     if (!launch) return cudaSuccess;
-    k_line_sum_batch<PPT, WPB, BR><<<blocks, 32 * WPB, 0, ctx->stream>>>(items, n, total, counter, ctx->d_stats,
-                                                                         ctx->d_status);
+    k_line_sum_batch<PPT, WPB, BR, PB><<<blocks, 32 * WPB, 0, ctx->stream>>>(items, n, total, counter, ctx->d_stats,
+                                                                             ctx->d_status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const BatchItem* items, int n, int64_t total,
-                                  unsigned long long* counter, int* blocks_out, bool launch, bool broad) {
-    if (broad) {   // the optional Lorentz terms: four cells a block (the plan's group size)
-        if (wpb != 4) return cudaErrorInvalidValue;
+cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, int pb, const BatchItem* items, int n,
+                                  int64_t total, unsigned long long* counter, int* blocks_out, bool launch, bool broad) {
+    if (broad) {   // the optional Lorentz terms: four cells a block (the plan's group size), 32 pairs a pass
+        if (wpb != 4 || pb != 32) return cudaErrorInvalidValue;
         if (tile_w == 128) return batch_launch<4, 4, true>(ctx, items, n, total, counter, blocks_out, launch);
         if (tile_w == 256) return batch_launch<8, 4, true>(ctx, items, n, total, counter, blocks_out, launch);
         if (tile_w == 512) return batch_launch<16, 4, true>(ctx, items, n, total, counter, blocks_out, launch);
         return cudaErrorInvalidValue;
     }
-    if (tile_w == 128 && wpb == 2) return batch_launch<4, 2>(ctx, items, n, total, counter, blocks_out, launch);
-    if (tile_w == 128 && wpb == 4) return batch_launch<4, 4>(ctx, items, n, total, counter, blocks_out, launch);
-    if (tile_w == 128 && wpb == 8) return batch_launch<4, 8>(ctx, items, n, total, counter, blocks_out, launch);
-    if (tile_w == 256 && wpb == 2) return batch_launch<8, 2>(ctx, items, n, total, counter, blocks_out, launch);
-    if (tile_w == 256 && wpb == 4) return batch_launch<8, 4>(ctx, items, n, total, counter, blocks_out, launch);
-    if (tile_w == 256 && wpb == 8) return batch_launch<8, 8>(ctx, items, n, total, counter, blocks_out, launch);
-    if (tile_w == 512) return batch_launch<16, 4>(ctx, items, n, total, counter, blocks_out, launch);
+#define RAPRAL_BL(PPT, WPB)                                                                          \
+    return pb == 64 ? batch_launch<PPT, WPB, false, 64>(ctx, items, n, total, counter, blocks_out, launch) \
+                    : batch_launch<PPT, WPB, false, 32>(ctx, items, n, total, counter, blocks_out, launch)
+    if (pb != 32 && pb != 64) return cudaErrorInvalidValue;
+    if (tile_w == 128 && wpb == 2) RAPRAL_BL(4, 2);
+    if (tile_w == 128 && wpb == 4) RAPRAL_BL(4, 4);
+    if (tile_w == 128 && wpb == 8) RAPRAL_BL(4, 8);
+    if (tile_w == 256 && wpb == 2) RAPRAL_BL(8, 2);
+    if (tile_w == 256 && wpb == 4) RAPRAL_BL(8, 4);
+    if (tile_w == 256 && wpb == 8) RAPRAL_BL(8, 8);
+    if (tile_w == 512) RAPRAL_BL(16, 4);
+#undef RAPRAL_BL
     return cudaErrorInvalidValue;
 }
 

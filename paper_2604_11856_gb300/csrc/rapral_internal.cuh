@@ -140,6 +140,7 @@ struct rapral_ctx {
     int codata = 0;
     int tile_w = 0;            // grid points per line-sum tile (0: 512 for FP64, 128 for FP32)
     int cells_per_block = 4;   // warps (cells) per FP32 line-sum block
+    int pairs_per_batch = 32;  // (line, cell) pairs a warp of the FP32 line sum stages per sweep pass (32 or 64)
     int ls_persist = -1;       // FP32 line sum: persistent with this many blocks a SM (-1: as many as fit; 0: a block a unit)
     // workspace arena (grown on demand; all users are stream-ordered)
     char* ws = nullptr;
@@ -315,8 +316,8 @@ struct BatchItem {
 };
 // Launches the persistent FP32 line sum over all units (or only reports the
 // grid size when `launch` is false).
-cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, const BatchItem* items, int n, int64_t total,
-                                  unsigned long long* counter, int* blocks_out, bool launch, bool broad);
+cudaError_t launch_line_sum_batch(rapral_ctx* ctx, int tile_w, int wpb, int pb, const BatchItem* items, int n,
+                                  int64_t total, unsigned long long* counter, int* blocks_out, bool launch, bool broad);
 
 // Rays
 cudaError_t launch_validate_rays(rapral_ctx* ctx, const rapral_rays* r, int64_t n_cells);

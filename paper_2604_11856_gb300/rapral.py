@@ -126,6 +126,7 @@ def load(build_if_missing=True):
             "rapral_set_constants": (i, [vp, i]),
             "rapral_set_tiling": (i, [vp, i, i]),
             "rapral_set_line_sum_blocks": (i, [vp, i]),
+            "rapral_set_line_batch": (i, [vp, i]),
             "rapral_workspace_bytes": (i, [i64, i64, i64, P(ct.c_size_t)]),
             "rapral_get_stats": (i, [vp, P(Stats)]),
             "rapral_reset_stats": (i, [vp]),
@@ -231,6 +232,10 @@ class Context:
         """FP32 line-sum launch: -1 persistent at full occupancy (default),
         n > 0 persistent with n blocks a SM, 0 one block per work unit."""
         self.check(self.lib.rapral_set_line_sum_blocks(self.h, blocks_per_sm))
+
+    def set_line_batch(self, pairs=32):
+        """FP32 line sum: (line, cell) pairs a warp stages per sweep pass, 32 or 64."""
+        self.check(self.lib.rapral_set_line_batch(self.h, pairs))
 
     def get_stats(self):
         st = Stats()

@@ -20,8 +20,10 @@ def problems():
     return probs
 
 
-def test_batch_equals_solo_and_graph_replays(problems):
+@pytest.mark.parametrize("pb", [32, 64])
+def test_batch_equals_solo_and_graph_replays(problems, pb):
     ctx = R.Context(0)
+    ctx.set_line_batch(pb)   # lines staged per sweep pass, in the batch and in the solo runs
     chunk = 3000
     bs = batch.BatchSolver(problems, ctx, chunk=chunk)
     assert len(bs.handles) >= 2   # several spectral rounds

@@ -65,8 +65,9 @@ def test_coeffs_fp32_stagnation(ctx):
     assert point_error(kap, rk, ra, what="kappa") <= TOL_POINT
 
 
-@pytest.mark.parametrize("tile,cpb", [(128, 2), (128, 4), (128, 8), (256, 4), (512, 4)])
-def test_line_sum_launch_forms_are_bitwise_equal(ctx, tile, cpb):
+@pytest.mark.parametrize("tile,cpb,pb", [(128, 2, 32), (128, 4, 32), (128, 8, 32), (256, 4, 32), (512, 4, 32),
+                                         (128, 4, 64), (256, 2, 64)])
+def test_line_sum_launch_forms_are_bitwise_equal(ctx, tile, cpb, pb):
     """The FP32 line sum launched persistently (as many blocks as fit, or one
     block a SM, taking the units from a counter) and as one block per unit:
     the same coefficients to the bit and the same work counts, on a ragged
@@ -76,6 +77,7 @@ def test_line_sum_launch_forms_are_bitwise_equal(ctx, tile, cpb):
     k0, nk = 1234, 50000
     out = {}
     ctx.set_tiling(tile_width=tile, cells_per_block=cpb)
+    ctx.set_line_batch(pb)
     try:
         for blocks in (-1, 1, 0):
             ctx.set_line_sum_blocks(blocks)
@@ -88,6 +90,7 @@ def test_line_sum_launch_forms_are_bitwise_equal(ctx, tile, cpb):
             out[blocks] = (kap.cpu().numpy(), em.cpu().numpy(), ctx.get_stats())
     finally:
         ctx.set_line_sum_blocks(-1)
+        ctx.set_line_batch(32)
         ctx.set_tiling(tile_width=-1, cells_per_block=4)
     for blocks in (1, 0):
         assert np.array_equal(out[blocks][0], out[-1][0]) and np.array_equal(out[blocks][1], out[-1][1]), blocks
@@ -100,6 +103,27 @@ def test_line_sum_blocks_checked(ctx):
         with pytest.raises(R.RapralError):
             ctx.set_line_sum_blocks(bad)
     ctx.set_line_sum_blocks(-1)
+    for bad in (0, 16, 48, 128):
+        with pytest.raises(R.RapralError):
+            ctx.set_line_batch(bad)
+    ctx.set_line_batch(32)
+
+
+@pytest.mark.parametrize("pb", [32, 64])
+def test_coeffs_fp32_pairs_per_pass(ctx, pb):
+    """64 pairs a sweep pass against the oracle at the FP32 tolerance, on the
+    two-temperature case with atoms and diatomics, and the same to the
+    tolerance as 32 a pass (only the order of the terms in a point's sum
+    differs)."""
+    p = synth.stagnation_line(n_cells=8, n_atomic=3000, n_molecular=40000, n_grid=60001)
+    ctx.set_line_batch(pb)
+    try:
+        kap, em = _coeffs(ctx, p, R.FP32)
+    finally:
+        ctx.set_line_batch(32)
+    rk, re, ra = oracle.spectral_coeffs(p, with_abs=True)
+    assert point_error(em, re, what=f"j, {pb} a pass") <= TOL_POINT
+    assert point_error(kap, rk, ra, what=f"kappa, {pb} a pass") <= TOL_POINT
 
 
 @pytest.mark.parametrize("tile", [None, 256])
