@@ -117,8 +117,8 @@ CONT_TRAFFIC = {"sha1": "5acd74ef87910912678c8d6546c788ab0f5e87b0", "cells": 200
 # 65,536-point afterbody chunk (80,000 cells, 26,697,080 ray segments), from a
 # one-pass ncu capture of the kernel source with this digest (source_digest);
 # another source or ray set gives null.
-MARCH_TRAFFIC = {"sha1": "7fb91849ff64b0e603c2b712e6a298e2c220c1fe", "cells": 80_000, "segments": 26_697_080,
-                 "grid_points": 65_536, "bytes": 334_466_940_672 + 472_968_704}
+MARCH_TRAFFIC = {"sha1": "156f11f3f01ceca0c87329b7dcd4e547185c0877", "cells": 80_000, "segments": 26_697_080,
+                 "grid_points": 65_536, "bytes": 356_842_381_824 + 468_259_328}
 
 
 def source_digest(name):

@@ -559,10 +559,11 @@ __device__ __forceinline__ void m1_step(float2& I, float2 Kf, float2 Jf, float2 
     }
 }
 
-// Bundle plan: for each (point p, group g) the group's bundles (the point's
-// g-th, (g+G)-th, ... bundle) dealt to M1_SLICES slices longest first (greedy
-// to the least-loaded slice, ties to the lower slice; equal lengths in index
-// order).  plan[] lists each group's bundles slice by slice, starting at the
+// Bundle plan: for each (point p, group g) the group's bundles (a contiguous
+// run of the point's bundles: with the rays of a point in angular order, the
+// neighbours a block marches cross the same cells near the point, which L1
+// then serves) dealt to M1_SLICES slices longest first (greedy to the
+// least-loaded slice, ties to the lower slice; equal lengths in index order).  plan[] lists each group's bundles slice by slice, starting at the
 // group's base; soff[(p G + g)(M1_SLICES + 1) + s] is where slice s starts.
 // Groups of more than 1024 bundles are dealt round-robin in index order.
 __global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ point_off,
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ 
     const int64_t pb0 = point_off[p];
     const int64_t nb = point_off[p + 1] - pb0;
     const int64_t m = nb > g ? (nb - g + G - 1) / G : 0;                     // bundles of this group
-    const int64_t base = pb0 + (int64_t)g * (nb / G) + (g < nb % G ? g : nb % G);   // bundles of groups before
+    const int64_t base = pb0 + (int64_t)g * (nb / G) + (g < nb % G ? g : nb % G);   // the group's first bundle
     int32_t* so = soff + blockIdx.x * (M1_SLICES + 1);
     __shared__ int64_t len[1024];
     __shared__ int16_t order[1024];
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ 
             const int s = (int)(k % M1_SLICES);
             const int64_t per = m / M1_SLICES, extra = m % M1_SLICES;
             const int64_t start = s * per + (s < extra ? s : extra);
-            plan[base + start + k / M1_SLICES] = (int32_t)(pb0 + g + k * G);
+            plan[base + start + k / M1_SLICES] = (int32_t)(base + k);
         }
         if (threadIdx.x <= M1_SLICES) {
             const int s = threadIdx.x;
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ 
     }
     const int mm = (int)m;
     for (int k = threadIdx.x; k < mm; k += blockDim.x) {
-        const int64_t b = pb0 + g + (int64_t)k * G;
+        const int64_t b = base + k;
         len[k] = seg_off[b + 1] - seg_off[b];
     }
     __syncthreads();
@@ -626,7 +627,7 @@ __global__ void __launch_bounds__(128) k_march_plan(const int64_t* __restrict__ 
         for (int s = 0; s < M1_SLICES; ++s) fill[s] = cnt[s];
         for (int r = 0; r < mm; ++r) {
             const int k = order[r];
-            plan[base + fill[slice_of[k]]++] = (int32_t)(pb0 + g + (int64_t)k * G);
+            plan[base + fill[slice_of[k]]++] = (int32_t)(base + k);
         }
     }
 }
