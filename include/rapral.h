@@ -219,7 +219,8 @@ RAPRAL_API int rapral_set_line_sum_blocks(rapral_ctx* ctx, int blocks_per_sm);
  * part's error bound is (pairs - 1) u of a point's term magnitudes
  * (u = 2^-24).  Used by the autotuner with rapral_set_tiling; batches take
  * the value current at rapral_batch_create (32 with the optional Lorentz
- * terms); the exact Voigt shape and the optional terms use 32.
+ * terms); the exact Voigt shape, the optional terms and the allocation-free
+ * entry point use 32.
  * Errors: EINVAL (not 32 or 64). */
 RAPRAL_API int rapral_set_line_batch(rapral_ctx* ctx, int pairs);
 
