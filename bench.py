@@ -103,8 +103,8 @@ def parse():
 # one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel
 # source with this digest (source_digest).  Other cell / point counts scale in proportion (the
 # bytes are the kappa / j rows written); a different source (comments aside) gives null.
-LINE_SUM_TRAFFIC = {"sha1": "26fefb50e0990e7161ec63be2cdc334d30889191", "cells": 200, "grid_points": 1_000_000,
-                    "bytes": 53_938_944 + 1_543_512_064}
+LINE_SUM_TRAFFIC = {"sha1": "9cb401bd4549a6eaf0a40186c4f84d5e3c0dda4c", "cells": 200, "grid_points": 1_000_000,
+                    "bytes": 53_932_288 + 1_543_667_712}
 
 
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
