@@ -991,8 +991,11 @@ def stagnation_block(args, local, world, rank, fp64=True):
     dev = torch.device("cuda", local)
     p = synth.stagnation_line(n_cells=args.cells)
     ctx = R.Context(local)
-    tw, wpb, pb, times = autotune.tune(ctx, p)
-    tuned = {"tile_width": tw, "cells_per_block": wpb, "pairs_per_pass": pb, "candidates_ms": times}
+    if args.no_tune:   # the library's default tiling (128-point tiles, 4 cells a block, 32 lines a pass)
+        tuned = {"tile_width": 128, "cells_per_block": 4, "pairs_per_pass": 32, "candidates_ms": None}
+    else:
+        tw, wpb, pb, times = autotune.tune(ctx, p)
+        tuned = {"tile_width": tw, "cells_per_block": wpb, "pairs_per_pass": pb, "candidates_ms": times}
     dp = solver.DeviceProblem(p, ctx)
     C, K = dp.C, p.grid.n
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
