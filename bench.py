@@ -110,8 +110,8 @@ LINE_SUM_TRAFFIC = {"sha1": "9cb401bd4549a6eaf0a40186c4f84d5e3c0dda4c", "cells":
 # DRAM bytes of one FP32 continuum level-sum launch at full size (200 cells x
 # 1e6 points, N and O with 100 levels each), from a one-pass ncu capture of the
 # kernel source with this digest (source_digest); a different source gives null.
-CONT_TRAFFIC = {"sha1": "5acd74ef87910912678c8d6546c788ab0f5e87b0", "cells": 200, "grid_points": 1_000_000, "levels": 100,
-                "bytes": 1_782_956_800 + 1_538_739_456}
+CONT_TRAFFIC = {"sha1": "b20ff15bc5d2a99674fcbc6991e7a0c6b0701352", "cells": 200, "grid_points": 1_000_000, "levels": 100,
+                "bytes": 1_782_987_520 + 1_539_120_640}
 
 # DRAM bytes (read + write) of one FP32 march launch (k_march1) on a full
 # 65,536-point afterbody chunk (80,000 cells, 26,697,080 ray segments), from a
