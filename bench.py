@@ -62,6 +62,8 @@ def parse():
                     help=f"offered rates, req/s (the whole study: {','.join(str(int(r)) for r in SERVE_RATES)})")
     ap.add_argument("--serve-fp64-rates", type=str, default="2000")
     ap.add_argument("--serve-slots", type=int, default=4, help="served block: concurrent request slots")
+    ap.add_argument("--stag-chunks", type=str, default="",
+                    help="stagnation block: also time the FP32 step in spectral chunks of these sizes (comma list)")
     ap.add_argument("--pairs-per-pass", type=int, choices=[32, 64], default=32,
                     help="afterbody: (line, cell) pairs a warp of the FP32 line sum stages per sweep pass")
     ap.add_argument("--serve-solo", action="store_true",
@@ -1043,6 +1045,25 @@ def stagnation_block(args, local, world, rank, fp64=True):
                                  "peak_source": f"{n_sm} SMs x 16 XU lanes x {sm_max / 1e6:.0f} MHz (max SM clock)"},
            "clocks": clk.summary()}
     q32 = float(r32["q"].item())
+    chunked = {}
+    for ch in (int(v) for v in args.stag_chunks.split(",") if v):
+        # the same step through the chunk pipeline: per-chunk buffers, planning and flux per chunk
+        cb = [(torch.empty((C, ch), dtype=torch.float32, device=dev), torch.empty((C, ch), dtype=torch.float32, device=dev))]
+        solver.solve(dp, ctx, R.FP32, chunk=ch, buffers=cb)
+        ctx.sync()
+        cms = []
+        for i in range(5):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc = solver.solve(dp, ctx, R.FP32, chunk=ch, buffers=cb)
+            b.record(stream)
+            ctx.sync()
+            cms.append(a.elapsed_time(b))
+        chunked[str(ch)] = {"ms_per_step": float(np.mean(cms)), "q_rel_diff_vs_whole": abs(float(rc["q"].item()) / q32 - 1)}
+        del cb
+    if chunked:
+        out["chunked"] = chunked
     if fp64:
         bufs64 = [(torch.empty((C, K), dtype=torch.float64, device=dev),
                    torch.empty((C, K), dtype=torch.float64, device=dev))]
